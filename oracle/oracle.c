@@ -1,0 +1,377 @@
+/*
+ * oracle.c -- plain, slow, obviously correct FP64 CPU oracle for the PARS3
+ * hot path (Yildirim & Manguoglu, "PARS3: Parallel Sparse Skew-Symmetric
+ * Matrix-Vector Multiplication with Reverse Cuthill-McKee Reordering").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this file.  It shares no code,
+ * header, table or helper with the CUDA library; the product path never
+ * calls it.
+ *
+ * Everything here is single-threaded and written for clarity, not speed.
+ * Inputs are the strict lower triangle L of S = L - L^T in CSR form (the
+ * half storage of Sec. 3): row pointers rp[n+1], sorted unique column
+ * indices ci[nnz] with ci < row, values v[nnz].  All arithmetic is FP64.
+ *
+ * Functions:
+ *   orc_validate     input checks (strict lower, sorted, unique, in range)
+ *   orc_full_csr     full storage of S = L - L^T           (Sec. 1, Eq. 1)
+ *   orc_spmv_full    y = (alpha I + S) x by plain row sums   (Sec. 1)
+ *   orc_spmv_sss     the serial SSS skew SpMV baseline       (Sec. 3.1.1)
+ *   orc_rcm          reverse Cuthill-McKee ordering          (Sec. 1, 3.1.2)
+ *   orc_bandwidth    max |p^-1(i) - p^-1(j)| over stored pairs (Table 1)
+ *   orc_split        3-way band split, canonical form        (Sec. 3.1.2)
+ *   orc_auto_cut     default cut point W (and tile T)        (Sec. 3.1.2, Fig. 8)
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOTSKEW -2
+#define ORC_ENOMEM -3
+
+/* ------------------------------------------------------------------------ */
+/* input validation                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Returns ORC_OK when rp/ci describe a strict lower triangle with sorted,
+ * unique, in-range column indices (the SSS half storage of Sec. 3). */
+int orc_validate(int32_t n, const int32_t *rp, const int32_t *ci)
+{
+    if (n < 0) return ORC_EINVAL;
+    if (rp[0] != 0) return ORC_EINVAL;
+    for (int32_t i = 0; i < n; i++) {
+        if (rp[i + 1] < rp[i]) return ORC_EINVAL;
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+            if (ci[k] < 0 || ci[k] >= i) return ORC_ENOTSKEW;
+            if (k > rp[i] && ci[k] <= ci[k - 1]) return ORC_ENOTSKEW;
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O1: the operator y = (alpha I + S) x                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Full-storage CSR of S = L - L^T (Eq. 1: A = -A^T; Sec. 1: CRS stores every
+ * nonzero).  Row i holds s_ij = l_ij for j < i and s_ij = -l_ji for j > i,
+ * columns ascending.  frp has n+1 entries, fci/fv have 2*nnz entries. */
+int orc_full_csr(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
+                 int64_t *frp, int32_t *fci, double *fv)
+{
+    int64_t *fill = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!fill) return ORC_ENOMEM;
+    /* count: each stored (i, j) appears in row i and in row j */
+    for (int64_t i = 0; i <= n; i++) frp[i] = 0;
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+            frp[i + 1]++;
+            frp[ci[k] + 1]++;
+        }
+    for (int32_t i = 0; i < n; i++) frp[i + 1] += frp[i];
+    /* lower part of row i first (columns < i, ascending) */
+    for (int32_t i = 0; i < n; i++) {
+        fill[i] = frp[i];
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+            fci[fill[i]] = ci[k];
+            fv[fill[i]] = v[k];
+            fill[i]++;
+        }
+    }
+    /* then the mirrored upper part: row j receives (j, i, -l_ij); visiting i
+     * in increasing order keeps the columns of row j ascending */
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+            int32_t j = ci[k];
+            fci[fill[j]] = i;
+            fv[fill[j]] = -v[k];
+            fill[j]++;
+        }
+    free(fill);
+    return ORC_OK;
+}
+
+/* y_i = alpha x_i + sum_j s_ij x_j, one row at a time (the plain definition
+ * of the shifted skew-symmetric operator A = alpha I + S, Sec. 1). */
+void orc_spmv_full(int32_t n, double alpha, const int64_t *frp, const int32_t *fci,
+                   const double *fv, const double *x, double *y)
+{
+    for (int32_t i = 0; i < n; i++) {
+        double s = alpha * x[i];
+        for (int64_t k = frp[i]; k < frp[i + 1]; k++) s += fv[k] * x[fci[k]];
+        y[i] = s;
+    }
+}
+
+/* Same operator applied to k right-hand sides stored row-major (X[i*k + c]). */
+void orc_spmm_full(int32_t n, int32_t k, double alpha, const int64_t *frp, const int32_t *fci,
+                   const double *fv, const double *X, double *Y)
+{
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t c = 0; c < k; c++) {
+            double s = alpha * X[(int64_t)i * k + c];
+            for (int64_t q = frp[i]; q < frp[i + 1]; q++)
+                s += fv[q] * X[(int64_t)fci[q] * k + c];
+            Y[(int64_t)i * k + c] = s;
+        }
+}
+
+/* The paper's serial baseline (Sec. 3.1.1, adapted to skew symmetry, with the
+ * pair update of Eqs. 2-6): every stored l_ij is read once and used twice,
+ * y_i += l_ij x_j and y_j += (-l_ij) x_i. */
+void orc_spmv_sss(int32_t n, double alpha, const int32_t *rp, const int32_t *ci,
+                  const double *v, const double *x, double *y)
+{
+    for (int32_t i = 0; i < n; i++) y[i] = alpha * x[i];
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+            int32_t j = ci[k];
+            double a = v[k];
+            y[i] += a * x[j];          /* Eq. 3 and Eq. 5 */
+            y[j] += (-a) * x[i];       /* Eq. 2, Eq. 4 and Eq. 6 */
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* O2: reverse Cuthill-McKee (Sec. 1 and Sec. 3.1.2; tie rule: degree, then   */
+/* index; start vertex: unvisited vertex of minimum degree, then index)       */
+/* ------------------------------------------------------------------------ */
+
+static const int32_t *g_deg; /* comparator context (the oracle is single-threaded) */
+
+static int cmp_deg_idx(const void *pa, const void *pb)
+{
+    int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
+    if (g_deg[a] != g_deg[b]) return g_deg[a] < g_deg[b] ? -1 : 1;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* Bandwidth of the ordering perm (new -> old): the largest |p^-1(i) - p^-1(j)|
+ * over stored pairs; 0 without nonzeros.  perm == NULL means identity. */
+int64_t orc_bandwidth(int32_t n, const int32_t *rp, const int32_t *ci, const int32_t *perm)
+{
+    int32_t *pinv = NULL;
+    if (perm) {
+        pinv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        for (int32_t k = 0; k < n; k++) pinv[perm[k]] = k;
+    }
+    int64_t bw = 0;
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+            int64_t a = pinv ? pinv[i] : i, b = pinv ? pinv[ci[k]] : ci[k];
+            int64_t d = a > b ? a - b : b - a;
+            if (d > bw) bw = d;
+        }
+    free(pinv);
+    return bw;
+}
+
+/* perm[k] = old index of the vertex placed at new position k.
+ * Steps: (1) graph with an edge {i, j} per stored (i, j); (2) while vertices
+ * remain unvisited, start a breadth-first search at the unvisited vertex of
+ * least degree (lowest index on ties); (3) on dequeuing a vertex, append its
+ * unvisited neighbours in (degree, index) order, marking them visited when
+ * they are enqueued; (4) the concatenated visit order is the Cuthill-McKee
+ * order, reversed as a whole it is RCM; (5) with guard != 0, when the RCM
+ * bandwidth exceeds the original one, the identity is returned instead. */
+int orc_rcm(int32_t n, const int32_t *rp, const int32_t *ci, int32_t guard,
+            int32_t *perm, int64_t *bw_before, int64_t *bw_after)
+{
+    if (n < 0) return ORC_EINVAL;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    int64_t nnz = rp[n];
+    int64_t *arp = (int64_t *)calloc(nn + 1, sizeof(int64_t));
+    int32_t *adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * nnz + 1));
+    int32_t *deg = (int32_t *)calloc(nn, sizeof(int32_t));
+    int32_t *by_deg = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *cm = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * nn);
+    char *seen = (char *)calloc(nn, 1);
+    int64_t *fill = (int64_t *)calloc(nn, sizeof(int64_t));
+    if (!arp || !adj || !deg || !by_deg || !cm || !tmp || !seen || !fill) {
+        free(arp); free(adj); free(deg); free(by_deg); free(cm); free(tmp); free(seen); free(fill);
+        return ORC_ENOMEM;
+    }
+    /* (1) adjacency lists of the symmetric pattern */
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) { deg[i]++; deg[ci[k]]++; }
+    for (int32_t i = 0; i < n; i++) arp[i + 1] = arp[i] + deg[i];
+    for (int32_t i = 0; i < n; i++) fill[i] = arp[i];
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+            adj[fill[i]++] = ci[k];
+            adj[fill[ci[k]]++] = i;
+        }
+    /* (2) all vertices in (degree, index) order: the first unvisited one in
+     * this list is the next start vertex */
+    for (int32_t i = 0; i < n; i++) by_deg[i] = i;
+    g_deg = deg;
+    qsort(by_deg, (size_t)n, sizeof(int32_t), cmp_deg_idx);
+
+    int32_t count = 0, head = 0, next_start = 0;
+    while (count < n) {
+        while (seen[by_deg[next_start]]) next_start++;
+        int32_t s = by_deg[next_start];
+        seen[s] = 1;
+        cm[count++] = s;
+        /* (3) breadth-first search, the cm array doubles as the FIFO queue */
+        while (head < count) {
+            int32_t v = cm[head++];
+            int32_t m = 0;
+            for (int64_t k = arp[v]; k < arp[v + 1]; k++)
+                if (!seen[adj[k]]) tmp[m++] = adj[k];
+            g_deg = deg;
+            qsort(tmp, (size_t)m, sizeof(int32_t), cmp_deg_idx);
+            for (int32_t q = 0; q < m; q++) {
+                seen[tmp[q]] = 1;
+                cm[count++] = tmp[q];
+            }
+        }
+    }
+    /* (4) reverse */
+    for (int32_t k = 0; k < n; k++) perm[k] = cm[n - 1 - k];
+
+    int64_t b0 = orc_bandwidth(n, rp, ci, NULL);
+    int64_t b1 = orc_bandwidth(n, rp, ci, perm);
+    /* (5) guard: a matrix that is already banded gains nothing (Sec. 4.1) */
+    if (guard && b1 > b0) {
+        for (int32_t k = 0; k < n; k++) perm[k] = k;
+        b1 = b0;
+    }
+    if (bw_before) *bw_before = b0;
+    if (bw_after) *bw_after = b1;
+    free(arp); free(adj); free(deg); free(by_deg); free(cm); free(tmp); free(seen); free(fill);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O3: the 3-way band split in canonical form (Sec. 3.1.2, Figs. 7-8)        */
+/* ------------------------------------------------------------------------ */
+
+/* class codes of a stored entry of the reordered lower triangle */
+#define ORC_MID_LOCAL 0  /* 1 <= i-j <= W and j in the same row tile as i */
+#define ORC_MID_HALO 1   /* 1 <= i-j <= W and j in an earlier tile (the one before) */
+#define ORC_OUTER 2      /* i-j > W */
+
+typedef struct { int32_t r, c; double v; } orc_trip;
+
+static int cmp_trip_rc(const void *pa, const void *pb)
+{
+    const orc_trip *a = (const orc_trip *)pa, *b = (const orc_trip *)pb;
+    if (a->r != b->r) return a->r < b->r ? -1 : 1;
+    if (a->c != b->c) return a->c < b->c ? -1 : 1;
+    return 0;
+}
+
+static const int32_t *g_row_of, *g_col_of; /* comparator context */
+
+static int cmp_entry_cr(const void *pa, const void *pb)
+{
+    int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
+    if (g_col_of[a] != g_col_of[b]) return g_col_of[a] < g_col_of[b] ? -1 : 1;
+    if (g_row_of[a] != g_row_of[b]) return g_row_of[a] < g_row_of[b] ? -1 : 1;
+    return 0;
+}
+
+/* Canonical split of P S P^T for the ordering perm (new -> old), row tile T
+ * and middle bandwidth W (1 <= W <= T):
+ *  - brp/bci/bv: strict lower CSR of P S P^T.  An entry (i, j, a) moves to
+ *    (p^-1(i), p^-1(j)); when that lands above the diagonal it is stored
+ *    transposed with its sign flipped (a_ji = -a_ij, Eq. 2).
+ *  - cls[e]: ORC_MID_LOCAL / ORC_MID_HALO / ORC_OUTER for entry e (rows are
+ *    split in tiles of T rows: tile t holds rows [tT, tT+T)).
+ *  - tile_ptr[ntiles+1] / tile_list: for each tile, the indices e of its
+ *    middle entries (local and halo) sorted by (column, row): the order in
+ *    which the mirrored products y_j -= a_ij x_i are summed.
+ *  - outer_csr: indices of the outer entries in (row, column) order;
+ *    outer_csc: the same indices in (column, row) order.
+ *  - counts[0..2]: number of entries of each class.
+ * Arrays are caller-allocated: brp[n+1], bci/bv/cls[nnz], tile_ptr[ntiles+1],
+ * tile_list[nnz], outer_csr/outer_csc[nnz]. */
+int orc_split(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
+              const int32_t *perm, int32_t T, int32_t W,
+              int32_t *brp, int32_t *bci, double *bv, uint8_t *cls,
+              int32_t *tile_ptr, int32_t *tile_list, int32_t *outer_csr, int32_t *outer_csc,
+              int64_t *counts)
+{
+    if (n < 0 || T < 1 || W < 1 || W > T) return ORC_EINVAL;
+    int64_t nnz = rp[n];
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t ntiles = (n + T - 1) / T;
+    int32_t *pinv = (int32_t *)malloc(sizeof(int32_t) * nn);
+    orc_trip *tr = (orc_trip *)malloc(sizeof(orc_trip) * (size_t)(nnz > 0 ? nnz : 1));
+    int32_t *row_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!pinv || !tr || !row_of) { free(pinv); free(tr); free(row_of); return ORC_ENOMEM; }
+    for (int32_t k = 0; k < n; k++) pinv[perm[k]] = k;
+
+    /* re-triangularize */
+    int64_t m = 0;
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+            int32_t a = pinv[i], b = pinv[ci[k]];
+            if (a > b) { tr[m].r = a; tr[m].c = b; tr[m].v = v[k]; }
+            else       { tr[m].r = b; tr[m].c = a; tr[m].v = -v[k]; }
+            m++;
+        }
+    qsort(tr, (size_t)nnz, sizeof(orc_trip), cmp_trip_rc);
+    for (int32_t i = 0; i <= n; i++) brp[i] = 0;
+    for (int64_t e = 0; e < nnz; e++) {
+        brp[tr[e].r + 1]++;
+        bci[e] = tr[e].c;
+        bv[e] = tr[e].v;
+        row_of[e] = tr[e].r;
+    }
+    for (int32_t i = 0; i < n; i++) brp[i + 1] += brp[i];
+
+    /* classify */
+    counts[0] = counts[1] = counts[2] = 0;
+    for (int64_t e = 0; e < nnz; e++) {
+        int32_t i = row_of[e], j = bci[e];
+        int32_t r0 = (i / T) * T;
+        if (i - j <= W) cls[e] = (j >= r0) ? ORC_MID_LOCAL : ORC_MID_HALO;
+        else cls[e] = ORC_OUTER;
+        counts[cls[e]]++;
+    }
+
+    /* per-tile middle lists in (column, row) order */
+    g_row_of = row_of;
+    g_col_of = bci;
+    int32_t q = 0;
+    for (int32_t t = 0; t < ntiles; t++) {
+        tile_ptr[t] = q;
+        int32_t r0 = t * T, r1 = (t + 1) * T < n ? (t + 1) * T : n;
+        int32_t start = q;
+        for (int32_t i = r0; i < r1; i++)
+            for (int32_t e = brp[i]; e < brp[i + 1]; e++)
+                if (cls[e] != ORC_OUTER) tile_list[q++] = e;
+        qsort(tile_list + start, (size_t)(q - start), sizeof(int32_t), cmp_entry_cr);
+    }
+    tile_ptr[ntiles] = q;
+
+    /* outer entries in row order and in column order */
+    int32_t o = 0;
+    for (int64_t e = 0; e < nnz; e++)
+        if (cls[e] == ORC_OUTER) { outer_csr[o] = (int32_t)e; outer_csc[o] = (int32_t)e; o++; }
+    qsort(outer_csc, (size_t)o, sizeof(int32_t), cmp_entry_cr);
+
+    free(pinv); free(tr); free(row_of);
+    return ORC_OK;
+}
+
+/* Default cut point (Fig. 8: the distance from the diagonal to the outer
+ * split is a bandwidth parameter).  Rule of this implementation: W is the
+ * smallest power of two >= the reordered bandwidth, clamped to
+ * [w_min, w_cap]; the row tile is T = max(W, t_min).  w_min, w_cap and t_min
+ * are powers of two supplied by the caller. */
+void orc_auto_cut(int64_t bw, int32_t w_min, int32_t w_cap, int32_t t_min,
+                  int32_t *T_out, int32_t *W_out)
+{
+    int64_t W = w_min;
+    while (W < bw && W < w_cap) W *= 2;
+    if (W > w_cap) W = w_cap;
+    *W_out = (int32_t)W;
+    *T_out = (int32_t)(W > t_min ? W : t_min);
+}
