@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 skew SpMV (and the MRS solver) -- one JSON line.
+
+Workload (default): the 3D 7-point grid 128^3 with 1% random long-range
+edges (n = 2,097,152, 6,304,727 stored lower entries), values N(0,1),
+alpha = 0.5, x ~ U(-1,1); one reorder + split, then a step = 200 repeated
+y = (alpha I + S) x through pars3_spmv, inputs resident in HBM.  Metric:
+effective skew-SpMV GB/s = algorithmic bytes (half storage:
+nnz*(value+4) + (n+1)*4 + 2*n*vector bytes) per product / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the method
+has no exchange step on one matrix per GPU); value = products of all ranks /
+max time.  --impl reference times the FP64 CPU oracle (the plain full-storage
+row-sum SpMV) on rank 0 on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "skew-SpMV GB/s (% HBM peak); mixed-prec MRS time-to-1e-10 vs FP64 MRS"
+REPEATS = 200
+L2_FLUSH_BYTES = 512 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def alg_bytes(n: int, nnz: int, sv: int, sx: int, k: int = 1) -> int:
+    """Half-storage algorithmic bytes of one product: every stored lower entry
+    once (value + 4-byte column), the row pointers, x read once, y written once."""
+    return nnz * (sv + 4) + (n + 1) * 4 + 2 * n * sx * k
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(name: str):
+    import workloads as W
+    if name == "cfg1":
+        A, alpha, x = W.config1()
+        desc = "grid3d 128^3 + 1% random long-range edges, N(0,1) values, alpha=0.5, 200 repeated SpMVs"
+    elif name == "cfg2":
+        A, alpha, x = W.config2()
+        desc = "R-MAT scale 22 (a,b,c,d=.57,.19,.19,.05), 20M stored, U(-1,1) values, alpha=0"
+    elif name == "cfg0":
+        A, alpha, x = W.config0()
+        desc = "grid2d 200x100, U(-1,1) values, alpha=0"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return A, alpha, x, desc
+
+
+# cut points used for each workload (chosen by pars3_autotune on a GB300)
+TUNED = {"cfg0": (1024, 128), "cfg1": (0, 0), "cfg2": (0, 0)}
+
+
+def run_reference(args, ws, rank):
+    """Oracle arm: FP64 full-storage row-sum SpMV (plain C, one thread)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    A, alpha, x, desc = workload(args.workload)
+    F = O.Full(A)
+    unit_bytes = alg_bytes(A.n, A.nnz, 8, 8)
+    F.apply(alpha, x)
+    per_step = max(1, args.ref_spmvs)
+    for _ in range(args.warmup):
+        F.apply(alpha, x)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            F.apply(alpha, x)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    gbs = unit_bytes * per_step * args.steps / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {desc}", "n": A.n, "nnz_stored": A.nnz,
+                       "sample": f"{per_step} SpMVs per step (of the {REPEATS}-product step)"},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step * args.steps} full-storage SpMVs of the whole matrix"},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(A, alpha, x, budget_s: float):
+    import oracle as O
+    F = O.Full(A)
+    F.apply(alpha, x)
+    t0 = time.perf_counter()
+    cnt = 0
+    while True:
+        F.apply(alpha, x)
+        cnt += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or cnt >= REPEATS:
+            break
+    gbs = alg_bytes(A.n, A.nnz, 8, 8) * cnt / el / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{cnt} full-storage fp64 SpMVs of the whole matrix ({el:.1f} s, single thread)"}
+
+
+def traffic_from_profile(kernel_hash: str, launch_units: float):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get("tile_kernel_f64_cfg1")
+    if not ent or ent.get("source_hash") != kernel_hash:
+        return None
+    return float(ent["dram_bytes_per_launch"])
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("spmv.cu", "devcommon.cuh", "smem_layout.h"):
+        h.update(open(os.path.join(ROOT, "paper_2407_17651_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg1")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--T", type=int, default=-1)
+    ap.add_argument("--W", type=int, default=-1)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-spmvs", type=int, default=10)
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2407_17651_gb300 import _build
+    from paper_2407_17651_gb300 import pars3 as P
+
+    if rank == 0 or ws == 1:
+        _build.build()
+    barrier(ws)
+    torch.cuda.set_device(local)
+    dt = {"f64": P.F64, "f32": P.F32, "bf16": P.BF16}[args.dtype]
+    vt = torch.float64 if dt == P.F64 else torch.float32
+    sv = {P.F64: 8, P.F32: 4, P.BF16: 2}[dt]
+    sx = 8 if dt == P.F64 else 4
+
+    A, alpha, x, desc = workload(args.workload)
+    T, Wc = TUNED.get(args.workload, (0, 0))
+    if args.T >= 0:
+        T, Wc = args.T, args.W
+    t0 = time.perf_counter()
+    perm, bw0, bw1 = P.pars3_reorder(A.n, A.rowptr, A.col)
+    t_rcm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=Wc, dtypes=P.dtype_bit(dt))
+    t_split = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P.pars3_upload(h)
+    t_up = time.perf_counter() - t0
+    info = P.pars3_info_get(h)
+
+    xp = torch.from_numpy(x[perm]).to("cuda", vt)
+    y = torch.empty_like(xp)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        for r in range(REPEATS):
+            if evs is not None:
+                evs[r].record(stream)
+            P.pars3_spmv(h, dt, alpha, xp, y, stream)
+        if evs is not None:
+            evs[REPEATS].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    P.pars3_check(h)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(REPEATS + 1)] for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.zero_()
+        step(evs[s])
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    P.pars3_check(h)
+    step_ms = [evs[s][0].elapsed_time(evs[s][REPEATS]) for s in range(args.steps)]
+    spmv_ms = [evs[s][r].elapsed_time(evs[s][r + 1]) for s in range(args.steps) for r in range(REPEATS)]
+    tot_s = sum(step_ms) / 1e3
+    tot_s = max_over_ranks(ws, tot_s)
+    ub = alg_bytes(A.n, A.nnz, sv, sx)
+    value = ub * REPEATS * args.steps * ws / tot_s / 1e9
+    peak, peak_kind = measured_peaks()
+    avg_spmv_s = statistics.mean(spmv_ms) / 1e3
+    achieved = ub / avg_spmv_s / 1e9
+    khash = kernel_source_hash()
+    traffic = traffic_from_profile(khash, 1.0) if (dt == P.F64 and args.workload == "cfg1") else None
+
+    # end to end through the host-buffer entry point (original numbering)
+    e2e = None
+    if args.e2e_steps > 0:
+        xh = torch.from_numpy(x.astype(np.float64 if dt == P.F64 else np.float32)).pin_memory().numpy()
+        yh = torch.empty(A.n, dtype=vt).pin_memory().numpy()
+        P.pars3_spmv_host(h, dt, alpha, xh, yh)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for _ in range(REPEATS):
+                P.pars3_spmv_host(h, dt, alpha, xh, yh)
+        el = time.perf_counter() - t0
+        el = max_over_ranks(ws, el)
+        e2e = {"value": ub * REPEATS * args.e2e_steps * ws / el / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": REPEATS * A.n * sx, "d2h_bytes_per_step": REPEATS * A.n * sx,
+               "api": "pars3_spmv_host (H2D, permute, SpMV, unpermute, D2H, sync per product)"}
+
+    cpu = cpu_baseline(A, alpha, x, args.cpu_budget) if (rank == 0 and ws == 1) else None
+    launches_per_spmv = 1 + (1 if info["halo_targets"] + info["long_rows"] > 0 else 0)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "pct_hbm_peak": value / ws / peak,
+            "config": {"workload": f"{args.workload}: {desc}", "n": A.n, "nnz_stored": A.nnz, "alpha": alpha,
+                       "repeats_per_step": REPEATS, "T": info["T"], "W": info["W"],
+                       "rcm_bandwidth": bw1, "original_bandwidth": bw0,
+                       "half_entries": info["half_entries"], "full_entries": info["full_entries"],
+                       "long_rows": info["long_rows"], "halo_targets": info["halo_targets"],
+                       "l2": "L2 (126 MB) flushed by a 512 MB write before every step; the matrix "
+                             f"({info['bytes_per_spmv'][dt] / 1e6:.0f} MB per product as laid out) exceeds L2; "
+                             "x and y stay device-resident across the 200 products as in a Krylov loop",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                         "kernel": "pars3_spmv (tile kernel + fold kernel), CUDA events per product",
+                         "algorithmic_bytes_per_launch": ub,
+                         "layout_bytes_per_launch": info["bytes_per_spmv"][dt]},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_spmv * REPEATS * args.steps,
+            "clocks": clk,
+            "preprocess_s": {"rcm": t_rcm, "split": t_split, "upload": t_up},
+            "spmv_us": {"mean": 1e6 * avg_spmv_s, "median": 1e6 * statistics.median(spmv_ms) / 1e3,
+                        "min": 1e3 * min(spmv_ms)},
+            "kernel_source_hash": khash,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
+if __name__ == "__main__":
+    main()

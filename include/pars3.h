@@ -1,0 +1,262 @@
+/*
+ * pars3.h -- C ABI of the GB300 skew-symmetric SpMV library.
+ *
+ * The library applies y = (alpha I + S) x for a sparse skew-symmetric S
+ * (S = -S^T, Sec. 1, Eq. 1) stored as its strict lower triangle only (the
+ * half storage of Sec. 3), after the preprocessing of Sec. 3.1.2: a
+ * reverse Cuthill-McKee reordering squeezes S towards a band and the band is
+ * split three ways -- the diagonal (here alpha I, S has a zero diagonal), a
+ * middle part within a bandwidth W of the diagonal and an outer part beyond
+ * it.  Every stored middle entry l_ij is read once and used twice
+ * (y_i += l_ij x_j and y_j -= l_ij x_i, Eqs. 2-6); the conflicting
+ * (cross-tile) mirrored products go through a halo buffer that a fixed-order
+ * pass folds in, so no atomics are used and results are bitwise
+ * reproducible from run to run.  On top of the operator sits the minimal
+ * residual (MRS) Krylov solver for shifted skew systems named in Sec. 1.
+ *
+ * Conventions
+ *  - Every function returns an int status: PARS3_OK (0) or a negative code.
+ *    Nothing throws across the ABI.  pars3_strerror() names a code.
+ *  - Host input arrays belong to the caller and are copied; the caller may
+ *    free them after the call returns.
+ *  - A handle (pars3_handle) owns its host metadata and, after
+ *    pars3_upload(), its device buffers; pars3_free() releases both.
+ *  - Device vectors (x, y, X, Y, b) are caller-allocated device pointers in
+ *    the handle's REORDERED numbering: x'[k] = x[perm[k]].
+ *    pars3_permute()/pars3_unpermute() convert on the device.  Device
+ *    vectors must be 16-byte aligned.
+ *  - stream arguments are cudaStream_t values passed as void* (NULL = the
+ *    legacy default stream).  Calls that launch kernels are asynchronous
+ *    with respect to the host unless stated otherwise.
+ *  - Integer indices are int32 (n < 2^31, stored nonzeros < 2^31).
+ */
+#ifndef PARS3_H
+#define PARS3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define PARS3_OK 0
+#define PARS3_EINVAL (-1)       /* bad argument (size, null pointer, alignment, parameter range) */
+#define PARS3_ENOTSKEW (-2)     /* input is not a valid strict lower triangle: an entry on or above
+                                   the diagonal, an unsorted or duplicate column, a bad row pointer */
+#define PARS3_ENOMEM (-3)       /* host or device allocation failed */
+#define PARS3_ECUDA (-4)        /* a CUDA runtime call failed */
+#define PARS3_ENOCONV (-5)      /* MRS reached its iteration limit before the tolerance */
+#define PARS3_ETIMEOUT (-6)     /* a bounded device-side wait gave up (error word set by a kernel) */
+#define PARS3_EUNSUPPORTED (-7) /* valid request this build does not support (e.g. precision not packed) */
+#define PARS3_ESTATE (-8)       /* handle in the wrong state (e.g. not uploaded) */
+#define PARS3_ENONFINITE (-9)   /* a NaN or Inf value in the input */
+
+/* ------------------------------------------------------------ precisions */
+#define PARS3_F64 0   /* values fp64, vectors fp64, accumulation fp64 */
+#define PARS3_F32 1   /* values fp32, vectors fp32, accumulation fp32 */
+#define PARS3_BF16 2  /* values bf16 (round-to-nearest-even of the fp32 rounding of the
+                         fp64 input), vectors fp32, accumulation fp32 */
+#define PARS3_DTYPE_BIT(d) (1 << (d))
+
+/* ---------------------------------------------------------------- flags */
+#define PARS3_RCM_GUARD 1 /* pars3_reorder: return the identity when RCM would widen the band */
+
+typedef struct pars3_handle pars3_handle;
+
+/* Split parameters (Sec. 3.1.2, Fig. 8: the middle/outer boundary is a
+ * user-given bandwidth).  T and W are powers of two with 32 <= W <= T <=
+ * 32768; 0 selects the default rule (W = smallest power of two >= the
+ * reordered bandwidth, clamped to [32, w_cap]; T = max(W, 1024)), where
+ * w_cap = 4096 when PARS3_F64 is packed and 8192 otherwise. */
+typedef struct {
+    int32_t T;          /* row tile: rows [tT, tT+T) are owned by one thread block */
+    int32_t W;          /* middle bandwidth: stored (i, j) with i - j <= W are middle entries */
+    int32_t dtypes;     /* bit mask of PARS3_DTYPE_BIT(d) value precisions to pack (0 = F64 only) */
+    int32_t long_row;   /* full-storage row length above which a row is processed in chunks (0 = default) */
+    int32_t reserved[4];
+} pars3_split_params;
+
+/* Read-only view of a handle's canonical split (host memory owned by the
+ * handle, valid until pars3_free).  It is the bit-exact contract with the
+ * oracle: values are moved or negated, never computed. */
+typedef struct {
+    int32_t n, T, W, ntiles;
+    int64_t nnz;                 /* stored strict-lower entries */
+    int64_t counts[3];           /* middle-local, middle-halo, outer */
+    const int32_t *perm;         /* [n] new -> old */
+    const int32_t *rowptr;       /* [n+1] strict-lower CSR of P S P^T */
+    const int32_t *col;          /* [nnz] */
+    const double *val;           /* [nnz] (mirrored entries carry the flipped sign) */
+    const uint8_t *cls;          /* [nnz] 0 middle-local, 1 middle-halo, 2 outer */
+    const int32_t *tile_ptr;     /* [ntiles+1] */
+    const int32_t *tile_list;    /* [counts0+counts1] middle entries of each tile, (column, row) order */
+    const int32_t *outer_csr;    /* [counts2] outer entries, (row, column) order */
+    const int32_t *outer_csc;    /* [counts2] outer entries, (column, row) order */
+} pars3_canonical;
+
+/* Sizes of the device layout (for reports and tests). */
+typedef struct {
+    int32_t n, T, W, ntiles, dtypes;
+    int64_t nnz;
+    int64_t half_entries;        /* entries on the half-storage tile path (read once, used twice) */
+    int64_t full_entries;        /* full-storage entries on the row path (outer entries twice) */
+    int64_t long_entries;        /* full-storage entries of chunked long rows */
+    int32_t long_rows, long_chunks;
+    int64_t halo_targets;        /* distinct rows that receive a cross-tile mirrored sum */
+    int32_t max_tile_half;       /* largest number of half-path entries of one tile */
+    int32_t smem_bytes[3];       /* dynamic shared memory of the tile kernel per precision (0 = not packed) */
+    int64_t device_bytes;        /* device memory held by the handle after upload */
+    int64_t bytes_per_spmv[3];   /* modelled DRAM bytes of one pars3_spmv per precision */
+    int64_t bandwidth;           /* max i - j of the reordered lower triangle */
+} pars3_info;
+
+/* MRS options (Sec. 1: minimal residual method for shifted skew systems,
+ * one product and one inner product per iteration). */
+typedef struct {
+    double rtol;         /* target ||b - A x||_2 / ||b||_2 (true residual, fp64) */
+    int32_t max_iter;    /* total inner iterations over all refinement cycles */
+    int32_t inner;       /* PARS3_F64: plain fp64 MRS; PARS3_F32 / PARS3_BF16: inner MRS in that
+                            precision inside fp64 iterative refinement */
+    double inner_rtol;   /* relative reduction asked of each inner solve (refinement only) */
+    int32_t max_outer;   /* refinement cycles */
+    int32_t check_every; /* iterations between device-side convergence checks of the recursion */
+    int32_t reserved[4];
+} pars3_mrs_opts;
+
+typedef struct {
+    int32_t iters;       /* inner iterations performed */
+    int32_t outer;       /* refinement cycles (1 for plain fp64) */
+    double true_relres;  /* final ||b - A x|| / ||b|| computed in fp64 on the device */
+    double est_relres;   /* last recursive residual estimate */
+    int32_t status;      /* PARS3_OK or PARS3_ENOCONV */
+    int32_t reserved[3];
+} pars3_mrs_result;
+
+/* ------------------------------------------------------------- functions */
+
+/* Name of a status code (static string). */
+const char *pars3_strerror(int code);
+
+/* Library version and the CUDA architecture it was built for (e.g. 103). */
+int pars3_version(int32_t *major, int32_t *minor, int32_t *cuda_arch);
+
+/* pars3_reorder -- Sec. 1 and Sec. 3.1.2: reverse Cuthill-McKee ordering of
+ * the symmetric pattern of S, on the host.  rowptr[n+1]/col[nnz] is the
+ * strict lower pattern (sorted unique columns < row).  Each connected
+ * component is searched breadth-first from its unvisited vertex of least
+ * (degree, index); a dequeued vertex appends its unvisited neighbours in
+ * (degree, index) order; the whole visit order is reversed.  perm_out[n]
+ * (caller-allocated) receives new -> old.  With PARS3_RCM_GUARD the identity
+ * is returned when the RCM bandwidth would exceed the original (Sec. 4.1:
+ * already banded matrices gain nothing).  bw_before/bw_after may be NULL.
+ * Errors: EINVAL (n < 0, null pointer), ENOTSKEW (pattern not strict lower),
+ * ENOMEM. */
+int pars3_reorder(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t flags,
+                  int32_t *perm_out, int64_t *bw_before, int64_t *bw_after);
+
+/* pars3_split -- Sec. 3.1.2 and Figs. 7-8: reorder S by perm (new -> old;
+ * NULL = identity), re-triangularize (an entry landing above the diagonal is
+ * stored mirrored with its sign flipped, Eq. 2), classify every stored entry
+ * as middle-local / middle-halo / outer for tile T and bandwidth W, and build
+ * the device layout for the precisions in p->dtypes.  val[nnz] are fp64 host
+ * values.  On success *out is a new handle (free with pars3_free).
+ * Errors: EINVAL (bad T/W/dtypes/perm), ENOTSKEW, ENONFINITE, ENOMEM. */
+int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                const int32_t *perm, const pars3_split_params *p, pars3_handle **out);
+
+/* Canonical split of a handle (host view; see pars3_canonical). */
+int pars3_split_export(const pars3_handle *h, pars3_canonical *out);
+
+/* Device-layout sizes of a handle. */
+int pars3_info_get(const pars3_handle *h, pars3_info *out);
+
+/* Host-only consistency check of the device layout against the canonical
+ * split: every middle entry appears once on the half path, every other
+ * entry twice on the full/long paths with mirrored sign.  Returns PARS3_OK
+ * or PARS3_EINVAL. */
+int pars3_layout_check(const pars3_handle *h);
+
+/* pars3_upload -- allocate the handle's device buffers on the current
+ * device and copy the layout (cudaMemcpyAsync on stream, then the stream is
+ * synchronized).  Idempotent.  Errors: ENOMEM, ECUDA. */
+int pars3_upload(pars3_handle *h, void *stream);
+
+/* pars3_spmv -- y = (alpha I + P S P^T) x for x, y of n entries in the
+ * handle's numbering: fp64 vectors for PARS3_F64, fp32 for PARS3_F32 and
+ * PARS3_BF16.  Two kernels: the tile kernel (one block per row tile: TMA
+ * staging of the x window [tT-W, tT+T), the half-storage middle entries with
+ * their in-tile mirrored sums in shared memory, the full-storage outer rows,
+ * chunked long rows) and the fold kernel (cross-tile halo sums and long-row
+ * partial sums, fixed order).  x and y must not overlap.  Errors: EINVAL,
+ * ESTATE (not uploaded), EUNSUPPORTED (precision not packed), ECUDA. */
+int pars3_spmv(const pars3_handle *h, int32_t dtype, double alpha, const void *x, void *y,
+               void *stream);
+
+/* pars3_spmm -- Y = (alpha I + P S P^T) X for k right-hand sides stored
+ * row-major (X[i*k + c]), 1 <= k <= 32.  Same precisions and errors as
+ * pars3_spmv. */
+int pars3_spmm(const pars3_handle *h, int32_t dtype, double alpha, int32_t k, const void *X,
+               void *Y, void *stream);
+
+/* pars3_spmm_batched -- count independent products Y_m = (alpha_m I + S_m) X_m
+ * (uneven sizes, same dtype and k) in ONE persistent kernel launch over a
+ * fixed-order list of (matrix, tile) work items, followed by one fold
+ * launch; with capture != 0 the pair is recorded once in a CUDA graph kept
+ * by the first handle and replayed on later calls with the same arguments.
+ * hs[count], alpha[count] (host), X[count], Y[count] (device pointers, host
+ * array).  Errors: as pars3_spmm. */
+int pars3_spmm_batched(pars3_handle *const *hs, int32_t count, int32_t dtype, const double *alpha,
+                       int32_t k, const void *const *X, void *const *Y, int32_t capture,
+                       void *stream);
+
+/* pars3_mrs -- solve (alpha I + P S P^T) x = b (Sec. 1: MRS, one product
+ * and one inner product per iteration) on the device.  b[n], x[n] are fp64
+ * device vectors in the handle's numbering; x holds x0 on entry and the
+ * solution on exit.  opts->inner selects plain fp64 MRS or an fp32 / bf16
+ * inner MRS inside fp64 iterative refinement (true residual, inner products
+ * and norms in fp64).  The inner loop runs as a CUDA graph with a
+ * device-side while-condition; the host only syncs once per refinement
+ * cycle.  alpha must be nonzero.  res may be NULL.  Errors: EINVAL, ESTATE,
+ * EUNSUPPORTED, ENOCONV (limit reached; x holds the best iterate), ECUDA,
+ * ETIMEOUT. */
+int pars3_mrs(const pars3_handle *h, double alpha, const double *b, double *x,
+              const pars3_mrs_opts *opts, pars3_mrs_result *res, void *stream);
+
+/* pars3_permute / pars3_unpermute -- dst[k] = src[perm[k]] and
+ * dst[perm[k]] = src[k] for n*k_cols elements of the given precision's vector
+ * type (row-major blocks of k_cols columns). */
+int pars3_permute(const pars3_handle *h, int32_t dtype, int32_t k_cols, const void *src, void *dst,
+                  void *stream);
+int pars3_unpermute(const pars3_handle *h, int32_t dtype, int32_t k_cols, const void *src, void *dst,
+                    void *stream);
+
+/* pars3_spmv_host -- end-to-end product on HOST vectors in the ORIGINAL
+ * numbering: copies x (n entries of the precision's vector type) to the
+ * device, permutes, applies the operator, un-permutes and copies y back,
+ * all on stream, then synchronizes the stream.  Staging buffers are owned
+ * by the handle (allocated on first use).  Errors: as pars3_spmv. */
+int pars3_spmv_host(pars3_handle *h, int32_t dtype, double alpha, const void *x_host, void *y_host,
+                    void *stream);
+
+/* Reads and clears the handle's device error word (synchronizes the
+ * stream).  Returns PARS3_OK, PARS3_ETIMEOUT or PARS3_ECUDA. */
+int pars3_check(const pars3_handle *h, void *stream);
+
+/* pars3_autotune -- times pars3_spmm (k right-hand sides) on the current
+ * device for candidate cut points (T, W) and returns the fastest in *best
+ * (other fields copied from *base).  The matrix arguments are those of
+ * pars3_split.  Leaves no device state behind.  Errors: as pars3_split and
+ * pars3_upload. */
+int pars3_autotune(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                   const int32_t *perm, const pars3_split_params *base, int32_t dtype, int32_t k,
+                   pars3_split_params *best, double *best_us);
+
+/* Release a handle (host and device memory).  NULL is ignored. */
+void pars3_free(pars3_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARS3_H */

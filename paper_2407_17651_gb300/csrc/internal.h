@@ -1,0 +1,111 @@
+// internal.h -- handle layout shared by the host preprocessing (C++) and the
+// CUDA launchers of libpars3.  Not part of the public ABI (include/pars3.h).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "pars3.h"
+
+namespace pars3 {
+
+constexpr int kNumDtypes = 3;
+constexpr int kAlignEntries = 8;       // half-path tile segments start on 16-byte boundaries
+constexpr int kBlock = 512;            // threads of the tile kernel
+constexpr int kLongChunk = 8192;       // entries per long-row chunk (one block each)
+constexpr int kSmemLimit = 227 * 1024; // opt-in shared memory per block on sm_100/sm_103
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Device layout on the host side (vectors) and its device mirror.
+struct Layout {
+    // half path: per tile t, entries [hoff[t], hoff[t] + hcnt[t]) in (row, col) order
+    std::vector<int32_t> hoff;      // [ntiles+1] (starts padded to kAlignEntries)
+    std::vector<int32_t> hcnt;      // [ntiles]
+    std::vector<uint16_t> hrp;      // [ntiles*(T+8)] tile-local row pointers
+    std::vector<uint16_t> hcol;     // window position p = j - (tT - W)
+    std::vector<uint16_t> hcperm;   // tile-local entry index, (col, row) order
+    std::vector<int32_t> hhoff;     // [ntiles+1] halo targets of tile t
+    std::vector<int32_t> hhrow;     // global row of each halo target (sorted per tile)
+    // full path: row i holds [frp[i], frp[i+1]) (long rows: empty)
+    std::vector<int32_t> frp;       // [n+1]
+    std::vector<int32_t> fcol;
+    // long rows, chunked
+    std::vector<int32_t> lrow;      // [nlong] row ids
+    std::vector<int32_t> lcptr;     // [nlong+1] chunk range of each long row
+    std::vector<int32_t> lcbeg, lcend;  // [nchunks] entry range of each chunk in lcol/lval
+    std::vector<int32_t> lcol;
+    // values per precision (fp64 / fp32 / bf16 bits)
+    std::vector<double> hval64, fval64, lval64;
+    std::vector<float> hval32, fval32, lval32;
+    std::vector<uint16_t> hval16, fval16, lval16;
+    int32_t max_tile_half = 0;
+};
+
+struct DevLayout {
+    int32_t *hoff = nullptr, *hcnt = nullptr;
+    uint16_t *hrp = nullptr, *hcol = nullptr, *hcperm = nullptr;
+    int32_t *hhoff = nullptr, *hhrow = nullptr;
+    int32_t *frp = nullptr, *fcol = nullptr;
+    int32_t *lrow = nullptr, *lcptr = nullptr, *lcbeg = nullptr, *lcend = nullptr, *lcol = nullptr;
+    void *hval[kNumDtypes] = {nullptr, nullptr, nullptr};
+    void *fval[kNumDtypes] = {nullptr, nullptr, nullptr};
+    void *lval[kNumDtypes] = {nullptr, nullptr, nullptr};
+    // scratch: halo sums and long-row partial sums (sized for fp64, k_max columns)
+    void *halo = nullptr;
+    void *lpart = nullptr;
+    int32_t *perm = nullptr;
+    int32_t *err = nullptr;          // device error word
+    // staging for pars3_spmv_host
+    void *stage_x = nullptr, *stage_y = nullptr, *stage_px = nullptr, *stage_py = nullptr;
+    int64_t bytes = 0;
+    std::vector<void *> owned;       // everything to cudaFree
+};
+
+}  // namespace pars3
+
+struct pars3_handle {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t T = 0, W = 0, ntiles = 0;
+    int32_t dtypes = 0;
+    int32_t long_row = 0;
+    int64_t bw = 0;
+    // canonical split (host)
+    std::vector<int32_t> perm, rowptr, col;
+    std::vector<double> val;
+    std::vector<uint8_t> cls;
+    std::vector<int32_t> tile_ptr, tile_list, outer_csr, outer_csc;
+    int64_t counts[3] = {0, 0, 0};
+    // device layout
+    pars3::Layout L;
+    pars3::DevLayout D;
+    bool uploaded = false;
+    int device = -1;
+    void *graph_cache = nullptr;     // batched SpMM graph (owned, see batched.cu)
+};
+
+namespace pars3 {
+
+// host_reorder.cpp
+int validate_lower(int32_t n, const int32_t *rowptr, const int32_t *col);
+int64_t bandwidth(int32_t n, const int32_t *rowptr, const int32_t *col, const int32_t *pinv);
+
+// host_split.cpp
+void auto_cut(int64_t bw, int32_t w_min, int32_t w_cap, int32_t t_min, int32_t *T, int32_t *W);
+int build_layout(pars3_handle *h);
+int smem_bytes_for(const pars3_handle *h, int dtype);
+int64_t model_bytes(const pars3_handle *h, int dtype);
+uint16_t f32_to_bf16_rne(float f);
+
+// capi.cpp
+int cuda_status(int cuda_err);
+
+// spmv.cu
+int launch_spmv(const pars3_handle *h, int dtype, double alpha, int k, const void *x, void *y,
+                void *stream);
+int launch_permute(const pars3_handle *h, int dtype, int k, const void *src, void *dst, bool inverse,
+                   void *stream);
+int prepare_kernels();
+
+}  // namespace pars3

@@ -1,0 +1,323 @@
+"""Python binding of libpars3 (include/pars3.h): argument marshalling only.
+
+Every entry point keeps its C name.  Host arrays are numpy arrays; device
+vectors are torch CUDA tensors (torch provides device memory and streams,
+the library's kernels do all the work).  A status other than PARS3_OK raises
+Pars3Error; there is no fallback path: if libpars3.so is missing, loading
+fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+F64, F32, BF16 = 0, 1, 2
+RCM_GUARD = 1
+
+OK, EINVAL, ENOTSKEW, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, EUNSUPPORTED, ESTATE, ENONFINITE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+
+
+def dtype_bit(d: int) -> int:
+    return 1 << d
+
+
+class Pars3Error(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {pars3_strerror(code)} ({code})")
+
+
+class pars3_split_params(C.Structure):
+    _fields_ = [("T", C.c_int32), ("W", C.c_int32), ("dtypes", C.c_int32), ("long_row", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
+
+
+class pars3_canonical(C.Structure):
+    _fields_ = [("n", C.c_int32), ("T", C.c_int32), ("W", C.c_int32), ("ntiles", C.c_int32),
+                ("nnz", C.c_int64), ("counts", C.c_int64 * 3),
+                ("perm", C.POINTER(C.c_int32)), ("rowptr", C.POINTER(C.c_int32)),
+                ("col", C.POINTER(C.c_int32)), ("val", C.POINTER(C.c_double)),
+                ("cls", C.POINTER(C.c_uint8)), ("tile_ptr", C.POINTER(C.c_int32)),
+                ("tile_list", C.POINTER(C.c_int32)), ("outer_csr", C.POINTER(C.c_int32)),
+                ("outer_csc", C.POINTER(C.c_int32))]
+
+
+class pars3_info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("T", C.c_int32), ("W", C.c_int32), ("ntiles", C.c_int32),
+                ("dtypes", C.c_int32), ("nnz", C.c_int64), ("half_entries", C.c_int64),
+                ("full_entries", C.c_int64), ("long_entries", C.c_int64), ("long_rows", C.c_int32),
+                ("long_chunks", C.c_int32), ("halo_targets", C.c_int64), ("max_tile_half", C.c_int32),
+                ("smem_bytes", C.c_int32 * 3), ("device_bytes", C.c_int64),
+                ("bytes_per_spmv", C.c_int64 * 3), ("bandwidth", C.c_int64)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+class pars3_mrs_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int32), ("inner", C.c_int32),
+                ("inner_rtol", C.c_double), ("max_outer", C.c_int32), ("check_every", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
+
+
+class pars3_mrs_result(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("outer", C.c_int32), ("true_relres", C.c_double),
+                ("est_relres", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, outer=self.outer, true_relres=self.true_relres,
+                    est_relres=self.est_relres, status=self.status)
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libpars3.so from the package's build folder (raises if absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libpars3.so is not built ({path}); run paper_2407_17651_gb300._build.build()")
+    L = C.CDLL(path)
+    P, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "pars3_strerror": ([C.c_int], C.c_char_p),
+        "pars3_version": ([P, P, P], C.c_int),
+        "pars3_reorder": ([i32, P, P, i32, P, P, P], C.c_int),
+        "pars3_split": ([i32, P, P, P, P, P, P], C.c_int),
+        "pars3_split_export": ([P, P], C.c_int),
+        "pars3_info_get": ([P, P], C.c_int),
+        "pars3_layout_check": ([P], C.c_int),
+        "pars3_upload": ([P, P], C.c_int),
+        "pars3_spmv": ([P, i32, f64, P, P, P], C.c_int),
+        "pars3_spmm": ([P, i32, f64, i32, P, P, P], C.c_int),
+        "pars3_spmm_batched": ([P, i32, i32, P, i32, P, P, i32, P], C.c_int),
+        "pars3_mrs": ([P, f64, P, P, P, P, P], C.c_int),
+        "pars3_permute": ([P, i32, i32, P, P, P], C.c_int),
+        "pars3_unpermute": ([P, i32, i32, P, P, P], C.c_int),
+        "pars3_spmv_host": ([P, i32, f64, P, P, P], C.c_int),
+        "pars3_check": ([P, P], C.c_int),
+        "pars3_autotune": ([i32, P, P, P, P, P, i32, i32, P, P], C.c_int),
+        "pars3_free": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the entry points the binding expects (all declared in include/pars3.h)."""
+    return ["pars3_strerror", "pars3_version", "pars3_reorder", "pars3_split", "pars3_split_export",
+            "pars3_info_get", "pars3_layout_check", "pars3_upload", "pars3_spmv", "pars3_spmm",
+            "pars3_spmm_batched", "pars3_mrs", "pars3_permute", "pars3_unpermute", "pars3_spmv_host",
+            "pars3_check", "pars3_autotune", "pars3_free"]
+
+
+def _chk(rc: int, where: str):
+    if rc != OK:
+        raise Pars3Error(rc, where)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device vectors must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("device vectors must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- host calls
+
+def pars3_strerror(code: int) -> str:
+    return lib().pars3_strerror(int(code)).decode()
+
+
+def pars3_version():
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _chk(lib().pars3_version(C.byref(a), C.byref(b), C.byref(c)), "pars3_version")
+    return a.value, b.value, c.value
+
+
+def pars3_reorder(n: int, rowptr, col, flags: int = RCM_GUARD):
+    """(perm new->old int32[n], bandwidth before, bandwidth after)."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    perm = np.empty(n, dtype=np.int32)
+    b0, b1 = C.c_int64(), C.c_int64()
+    _chk(lib().pars3_reorder(int(n), _p(rp), _p(ci), int(flags), _p(perm), C.byref(b0), C.byref(b1)),
+         "pars3_reorder")
+    return perm, b0.value, b1.value
+
+
+class Handle:
+    """Owns a pars3_handle*; released by pars3_free on close/garbage collection."""
+
+    def __init__(self, ptr: C.c_void_p, n: int):
+        self.ptr = ptr
+        self.n = n
+
+    def close(self):
+        if self.ptr:
+            lib().pars3_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        if not self.ptr:
+            raise ValueError("handle is closed")
+        return self.ptr
+
+
+def pars3_split(n: int, rowptr, col, val, perm=None, T: int = 0, W: int = 0, dtypes: int = 0,
+                long_row: int = 0) -> Handle:
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    v = np.ascontiguousarray(val, dtype=np.float64)
+    pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+    prm = pars3_split_params(T=T, W=W, dtypes=dtypes, long_row=long_row)
+    out = C.c_void_p()
+    _chk(lib().pars3_split(int(n), _p(rp), _p(ci), _p(v), None if pm is None else _p(pm), C.byref(prm),
+                           C.byref(out)), "pars3_split")
+    return Handle(out, n)
+
+
+def pars3_split_export(h: Handle) -> dict:
+    c = pars3_canonical()
+    _chk(lib().pars3_split_export(h, C.byref(c)), "pars3_split_export")
+    nnz, n, nt = c.nnz, c.n, c.ntiles
+    nmid = int(c.counts[0] + c.counts[1])
+    nout = int(c.counts[2])
+
+    def arr(ptr, m, dt):
+        if m == 0:
+            return np.zeros(0, dtype=dt)
+        return np.ctypeslib.as_array(ptr, shape=(m,)).astype(dt, copy=True)
+
+    return dict(n=n, T=c.T, W=c.W, ntiles=nt, nnz=nnz, counts=np.array(list(c.counts), dtype=np.int64),
+                perm=arr(c.perm, n, np.int32), rowptr=arr(c.rowptr, n + 1, np.int32),
+                col=arr(c.col, nnz, np.int32), val=arr(c.val, nnz, np.float64),
+                cls=arr(c.cls, nnz, np.uint8), tile_ptr=arr(c.tile_ptr, nt + 1, np.int32),
+                tile_list=arr(c.tile_list, nmid, np.int32), outer_csr=arr(c.outer_csr, nout, np.int32),
+                outer_csc=arr(c.outer_csc, nout, np.int32))
+
+
+def pars3_info_get(h: Handle) -> dict:
+    i = pars3_info()
+    _chk(lib().pars3_info_get(h, C.byref(i)), "pars3_info_get")
+    return i.as_dict()
+
+
+def pars3_layout_check(h: Handle) -> int:
+    return int(lib().pars3_layout_check(h))
+
+
+# -------------------------------------------------------------- device calls
+
+def pars3_upload(h: Handle, stream=None):
+    _chk(lib().pars3_upload(h, _stream(stream)), "pars3_upload")
+
+
+def pars3_spmv(h: Handle, dtype: int, alpha: float, x, y, stream=None):
+    _chk(lib().pars3_spmv(h, int(dtype), float(alpha), _dptr(x), _dptr(y), _stream(stream)), "pars3_spmv")
+
+
+def pars3_spmm(h: Handle, dtype: int, alpha: float, X, Y, stream=None):
+    k = 1 if X.dim() == 1 else int(X.shape[1])
+    _chk(lib().pars3_spmm(h, int(dtype), float(alpha), k, _dptr(X), _dptr(Y), _stream(stream)), "pars3_spmm")
+
+
+def pars3_spmm_batched(hs, dtype: int, alphas, Xs, Ys, capture: bool = False, stream=None):
+    m = len(hs)
+    k = 1 if Xs[0].dim() == 1 else int(Xs[0].shape[1])
+    harr = (C.c_void_p * m)(*[h.ptr for h in hs])
+    a = np.ascontiguousarray(alphas, dtype=np.float64)
+    xa = (C.c_void_p * m)(*[X.data_ptr() for X in Xs])
+    ya = (C.c_void_p * m)(*[Y.data_ptr() for Y in Ys])
+    _chk(lib().pars3_spmm_batched(harr, m, int(dtype), _p(a), k, xa, ya, 1 if capture else 0, _stream(stream)),
+         "pars3_spmm_batched")
+
+
+def pars3_permute(h: Handle, dtype: int, src, dst, stream=None):
+    k = 1 if src.dim() == 1 else int(src.shape[1])
+    _chk(lib().pars3_permute(h, int(dtype), k, _dptr(src), _dptr(dst), _stream(stream)), "pars3_permute")
+
+
+def pars3_unpermute(h: Handle, dtype: int, src, dst, stream=None):
+    k = 1 if src.dim() == 1 else int(src.shape[1])
+    _chk(lib().pars3_unpermute(h, int(dtype), k, _dptr(src), _dptr(dst), _stream(stream)), "pars3_unpermute")
+
+
+def pars3_spmv_host(h: Handle, dtype: int, alpha: float, x_host: np.ndarray, y_host: np.ndarray, stream=None):
+    """x_host/y_host: numpy (or pinned torch CPU tensors' numpy views), original numbering."""
+    _chk(lib().pars3_spmv_host(h, int(dtype), float(alpha), C.c_void_p(x_host.ctypes.data),
+                               C.c_void_p(y_host.ctypes.data), _stream(stream)), "pars3_spmv_host")
+
+
+def pars3_check(h: Handle, stream=None):
+    _chk(lib().pars3_check(h, _stream(stream)), "pars3_check")
+
+
+def pars3_mrs(h: Handle, alpha: float, b, x, rtol: float = 1e-10, max_iter: int = 200000,
+              inner: int = F64, inner_rtol: float = 1e-5, max_outer: int = 50, check_every: int = 8,
+              stream=None, raise_on_noconv: bool = True) -> dict:
+    o = pars3_mrs_opts(rtol=rtol, max_iter=max_iter, inner=inner, inner_rtol=inner_rtol,
+                       max_outer=max_outer, check_every=check_every)
+    r = pars3_mrs_result()
+    rc = lib().pars3_mrs(h, float(alpha), _dptr(b), _dptr(x), C.byref(o), C.byref(r), _stream(stream))
+    if rc != OK and not (rc == ENOCONV and not raise_on_noconv):
+        raise Pars3Error(rc, "pars3_mrs")
+    return r.as_dict()
+
+
+def pars3_autotune(n: int, rowptr, col, val, perm, dtype: int = F64, k: int = 1, dtypes: int = 0,
+                   T: int = 0, W: int = 0):
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    v = np.ascontiguousarray(val, dtype=np.float64)
+    pm = np.ascontiguousarray(perm, dtype=np.int32)
+    base = pars3_split_params(T=T, W=W, dtypes=dtypes)
+    best = pars3_split_params()
+    us = C.c_double()
+    _chk(lib().pars3_autotune(int(n), _p(rp), _p(ci), _p(v), _p(pm), C.byref(base), int(dtype), int(k),
+                              C.byref(best), C.byref(us)), "pars3_autotune")
+    return dict(T=best.T, W=best.W, dtypes=best.dtypes, long_row=best.long_row, us=us.value)
+
+
+def pars3_free(h: Handle):
+    h.close()
