@@ -68,7 +68,8 @@ typedef struct pars3_handle pars3_handle;
  * user-given bandwidth).  T and W are powers of two with 32 <= W <= T <=
  * 32768; 0 selects the default rule (W = smallest power of two >= the
  * reordered bandwidth, clamped to [32, w_cap]; T = max(W, 1024)), where
- * w_cap = 4096 when PARS3_F64 is packed and 8192 otherwise. */
+ * w_cap = 1024 when PARS3_F64 is packed and 2048 otherwise (two tile stages
+ * must fit in shared memory). */
 typedef struct {
     int32_t T;          /* row tile: rows [tT, tT+T) are owned by one thread block */
     int32_t W;          /* middle bandwidth: stored (i, j) with i - j <= W are middle entries */

@@ -65,13 +65,23 @@ static int upload_impl(pars3_handle *h, cudaStream_t st) {
     UP(D.hcperm, L.hcperm);
     UP(D.hhoff, L.hhoff);
     UP(D.hhrow, L.hhrow);
-    UP(D.frp, L.frp);
+    UP(D.sl_off, L.sl_off);
+    UP(D.sl_ent, L.sl_ent);
+    UP(D.sl_meta, L.sl_meta);
     UP(D.fcol, L.fcol);
     UP(D.lrow, L.lrow);
-    UP(D.lcptr, L.lcptr);
+    UP(D.lrp, L.lrp);
+    UP(D.lc0, L.lc0);
+    UP(D.lc1, L.lc1);
     UP(D.lcbeg, L.lcbeg);
     UP(D.lcend, L.lcend);
+    UP(D.lcfirst, L.lcfirst);
+    UP(D.lcrows, L.lcrows);
+    UP(D.lcslot, L.lcslot);
     UP(D.lcol, L.lcol);
+    UP(D.fold_row, L.fold_row);
+    UP(D.fold_halo, L.fold_halo);
+    UP(D.fold_long, L.fold_long);
     UP(D.perm, h->perm);
     if (h->dtypes & PARS3_DTYPE_BIT(PARS3_F64)) {
         double *a, *b, *c;
@@ -91,7 +101,8 @@ static int upload_impl(pars3_handle *h, cudaStream_t st) {
 #undef UP
     // scratch sized for fp64 accumulators and one right-hand side
     if ((rc = dev_alloc(D, &D.halo, L.hhrow.size() * sizeof(double))) != PARS3_OK) return rc;
-    if ((rc = dev_alloc(D, &D.lpart, L.lcbeg.size() * sizeof(double))) != PARS3_OK) return rc;
+    if ((rc = dev_alloc(D, &D.lpart, static_cast<size_t>(L.nslots) * sizeof(double))) != PARS3_OK) return rc;
+    D.scratch_k = 1;
     void *err = nullptr;
     if ((rc = dev_alloc(D, &err, sizeof(int32_t))) != PARS3_OK) return rc;
     D.err = static_cast<int32_t *>(err);

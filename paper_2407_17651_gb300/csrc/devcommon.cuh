@@ -1,7 +1,7 @@
 // devcommon.cuh -- device helpers shared by the kernels of libpars3:
 // value types, TMA bulk copies with mbarrier completion (inline PTX for
 // sm_100-class GPUs), bounded waits that report through an error word, and
-// the merge-path row pass.
+// warp helpers.
 #pragma once
 
 #include <cstdint>
@@ -95,58 +95,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         }
     }
     return true;
-}
-
-// ------------------------------------------------------------- merge pass
-// Row sums over a contiguous run of CSR entries [0, ne) of rows [0, nr) with
-// row pointers rp (rp[0] = 0, rp[nr] = ne), balanced on entries: thread t
-// takes entries [t*ipt, (t+1)*ipt).  op(e, r) returns entry e's contribution
-// to row r.  A row's first piece is added to rowacc[r] by the thread that
-// holds the row's first entry; later pieces (a row spilling over thread
-// boundaries) are carried and added after a barrier in thread order, so the
-// summation order is fixed for a given block size.
-template <typename AT, typename RP, typename Op>
-__device__ __forceinline__ void merge_rows(int ne, int nr, const RP *rp, Op op, AT *rowacc,
-                                           int *carry_row, AT *carry_val) {
-    const int tid = threadIdx.x, P = blockDim.x;
-    carry_row[tid] = -1;
-    if (ne > 0) {
-        const int ipt = (ne + P - 1) / P;
-        const int lo = tid * ipt;
-        const int hi = min(lo + ipt, ne);
-        if (lo < hi) {
-            int L = 0, H = nr;
-            while (H - L > 1) {
-                const int m = (L + H) >> 1;
-                if (static_cast<int>(rp[m]) <= lo) L = m;
-                else H = m;
-            }
-            int r = L;
-            int rend = static_cast<int>(rp[r + 1]);
-            bool cont = static_cast<int>(rp[r]) < lo;
-            AT acc = AT(0);
-            for (int e = lo; e < hi; ++e) {
-                if (e >= rend) {
-                    if (cont) { carry_row[tid] = r; carry_val[tid] = acc; }
-                    else rowacc[r] += acc;
-                    cont = false;
-                    acc = AT(0);
-                    do { ++r; rend = static_cast<int>(rp[r + 1]); } while (e >= rend);
-                }
-                acc += op(e, r);
-            }
-            if (cont) { carry_row[tid] = r; carry_val[tid] = acc; }
-            else rowacc[r] += acc;
-        }
-    }
-    __syncthreads();
-    const int cr = carry_row[tid];
-    if (cr >= 0 && (tid == 0 || carry_row[tid - 1] != cr)) {
-        AT s = carry_val[tid];
-        for (int u = tid + 1; u < P && carry_row[u] == cr; ++u) s += carry_val[u];
-        rowacc[cr] += s;
-    }
-    __syncthreads();
 }
 
 }  // namespace pars3

@@ -13,12 +13,15 @@
 //   half path  -- middle entries of ordinary rows: stored once, one block per
 //                 row tile uses each twice (row sum and mirrored sum), the
 //                 mirrored sums of halo entries go to a compact halo list;
-//   full path  -- outer entries, and every entry touching a long row or an
-//                 over-full tile, stored in both rows with mirrored sign, so
-//                 that each row is a plain gather (no write conflicts);
-//   long rows  -- rows whose full-path length exceeds long_row are summed in
-//                 chunks of kLongChunk entries and folded in fixed order.
+//   full path  -- outer entries, and the middle entries of tiles too large
+//                 for shared memory, stored in both rows with mirrored sign,
+//                 so that each row is a plain gather (no write conflicts);
+//   long rows  -- rows longer than a per-tile cap on full-path entries (and
+//                 the heaviest rows of tiles above the cap) are summed in
+//                 chunks of kLongChunk entries; the partial sums of every
+//                 (chunk, row) pair are folded in chunk order.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -127,36 +130,56 @@ static int canonical_split(pars3_handle *h, const int32_t *rowptr, const int32_t
     return PARS3_OK;
 }
 
-static int primary_dtype(int32_t dtypes) {
-    return (dtypes & PARS3_DTYPE_BIT(PARS3_F64)) ? PARS3_F64 : PARS3_F32;
+void dtype_sizes(int dtype, uint32_t *vsz, uint32_t *xsz, uint32_t *asz) {
+    if (dtype == PARS3_F64) { *vsz = 8; *xsz = 8; *asz = 8; }
+    else if (dtype == PARS3_F32) { *vsz = 4; *xsz = 4; *asz = 4; }
+    else { *vsz = 2; *xsz = 4; *asz = 4; }
 }
 
-static void dtype_sizes(int dtype, uint32_t *xsz, uint32_t *asz) {
-    if (dtype == PARS3_F64) { *xsz = 8; *asz = 8; }
-    else { *xsz = 4; *asz = 4; }
+constexpr int64_t kLongSlots = kLongChunk + 2 * kAlignFull;  // long chunk staging incl. alignment slack
+
+int32_t stage_full_entries(const pars3_handle *h) {
+    int64_t F = h->L.max_tile_full;
+    if (!h->L.lrow.empty()) F = std::max<int64_t>(F, kLongSlots);
+    return static_cast<int32_t>(round_up(F, kAlignFull));
+}
+
+static uint32_t smem_total(const pars3_handle *h, int dtype, int64_t Mh, int64_t S, int64_t F) {
+    uint32_t vsz, xsz, asz;
+    dtype_sizes(dtype, &vsz, &xsz, &asz);
+    return smem_layout(h->T, h->W, static_cast<uint32_t>(round_up(Mh, kAlignHalf)), static_cast<uint32_t>(S),
+                       static_cast<uint32_t>(round_up(F, kAlignFull)), vsz, xsz, asz).total;
 }
 
 int smem_bytes_for(const pars3_handle *h, int dtype) {
-    uint32_t xsz, asz;
-    dtype_sizes(dtype, &xsz, &asz);
-    SmemLayout s = smem_layout(h->T, h->W, static_cast<uint32_t>(h->L.max_tile_half), kBlock, xsz, asz, 1);
-    return static_cast<int>(s.total);
+    return static_cast<int>(smem_total(h, dtype, h->L.max_tile_half, h->L.max_tile_slices, stage_full_entries(h)));
 }
 
-// Largest half-path tile (entries) that still fits in shared memory.
-static int32_t half_cap(const pars3_handle *h) {
-    uint32_t xsz, asz;
-    dtype_sizes(primary_dtype(h->dtypes), &xsz, &asz);
-    SmemLayout s0 = smem_layout(h->T, h->W, 0, kBlock, xsz, asz, 1);
-    int64_t room = static_cast<int64_t>(kSmemLimit) - s0.total - 64;
-    int64_t per = asz + 4;
-    int64_t cap = room > 0 ? room / per : 0;
-    cap = std::min<int64_t>(cap, 65535 - kAlignEntries);
-    return static_cast<int32_t>(std::max<int64_t>(cap, 0));
+static int max_smem_all(const pars3_handle *h) {
+    int m = 0;
+    for (int d = 0; d < kNumDtypes; ++d)
+        if (h->dtypes & PARS3_DTYPE_BIT(d)) m = std::max(m, smem_bytes_for(h, d));
+    return m;
 }
 
-int build_layout(pars3_handle *h) {
+// half-path entries a tile may hold with no full-path data, for every packed precision
+static int64_t half_room(const pars3_handle *h) {
+    int64_t best = INT64_MAX;
+    for (int d = 0; d < kNumDtypes; ++d) {
+        if (!(h->dtypes & PARS3_DTYPE_BIT(d))) continue;
+        uint32_t vsz, xsz, asz;
+        dtype_sizes(d, &vsz, &xsz, &asz);
+        const int64_t base = smem_total(h, d, 0, 0, kLongSlots);
+        const int64_t per = 2 * (vsz + 4) + (vsz == asz ? 0 : asz);   // two stages + separate q
+        const int64_t room = static_cast<int64_t>(kSmemLimit) - base - 1024;
+        best = std::min<int64_t>(best, room > 0 ? room / per : -1);
+    }
+    return std::min<int64_t>(best, 65535 - kAlignHalf);
+}
+
+static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
     Layout &L = h->L;
+    L = Layout();
     const int32_t n = h->n, T = h->T, W = h->W, nt = h->ntiles;
     const int64_t nnz = h->nnz;
     const std::vector<int32_t> &rp = h->rowptr;
@@ -164,7 +187,7 @@ int build_layout(pars3_handle *h) {
     std::vector<int32_t> row_of(nnz);
     for (int32_t i = 0; i < n; ++i)
         for (int32_t e = rp[i]; e < rp[i + 1]; ++e) row_of[e] = i;
-    // column-major view of the band CSR: entries of column j in increasing row
+    // column view of the band CSR: entries of column j in increasing row
     std::vector<int32_t> cptr(static_cast<size_t>(n) + 1, 0);
     for (int64_t e = 0; e < nnz; ++e) ++cptr[ci[e] + 1];
     for (int32_t j = 0; j < n; ++j) cptr[j + 1] += cptr[j];
@@ -173,45 +196,38 @@ int build_layout(pars3_handle *h) {
         std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
         for (int64_t e = 0; e < nnz; ++e) cent[fill[ci[e]]++] = static_cast<int32_t>(e);
     }
-    // long rows: full degree above the threshold
-    std::vector<uint8_t> is_long(n, 0);
-    for (int32_t i = 0; i < n; ++i) {
-        int64_t d = (rp[i + 1] - rp[i]) + (cptr[i + 1] - cptr[i]);
-        if (d > h->long_row) is_long[i] = 1;
-    }
-    // routing: half if middle, both ends ordinary and the tile fits
-    const int32_t cap = half_cap(h);
+    // ---- 1. half path: middle entries, unless the tile would not fit
+    const int64_t mcap = mcap_in;
     std::vector<uint8_t> half(nnz, 0);
     std::vector<int32_t> tcount(nt, 0);
     for (int64_t e = 0; e < nnz; ++e) {
-        if (h->cls[e] != 2 && !is_long[row_of[e]] && !is_long[ci[e]]) {
+        if (h->cls[e] != 2) {
             half[e] = 1;
             ++tcount[row_of[e] / T];
         }
     }
     for (int32_t t = 0; t < nt; ++t) {
-        if (tcount[t] > cap) {
-            int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+        if (tcount[t] > mcap) {
+            const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
             for (int64_t e = rp[r0]; e < rp[r1]; ++e) half[e] = 0;
             tcount[t] = 0;
         }
     }
-    // half path arrays
     L.hoff.assign(static_cast<size_t>(nt) + 1, 0);
     L.hcnt.assign(nt, 0);
     for (int32_t t = 0; t < nt; ++t) {
         L.hcnt[t] = tcount[t];
-        L.hoff[t + 1] = static_cast<int32_t>(L.hoff[t] + round_up(tcount[t], kAlignEntries));
+        L.hoff[t + 1] = static_cast<int32_t>(L.hoff[t] + round_up(tcount[t], kAlignHalf));
+        L.max_tile_half = std::max(L.max_tile_half, tcount[t]);
     }
     const int64_t hn = L.hoff[nt];
     L.hcol.assign(hn, 0);
     L.hcperm.assign(hn, 0);
     L.hrp.assign(static_cast<size_t>(nt) * (T + 8), 0);
-    std::vector<int32_t> hpos(nnz, -1);  // entry -> global half position
-    L.max_tile_half = 0;
+    std::vector<int32_t> hsrc(hn, 0);   // entry + 1 (0 = padding)
+    std::vector<int32_t> hpos(nnz, -1);
     for (int32_t t = 0; t < nt; ++t) {
-        int32_t r0 = t * T, r1 = std::min(n, r0 + T);
-        int32_t wb = r0 - W;
+        const int32_t r0 = t * T, r1 = std::min(n, r0 + T), wb = r0 - W;
         int32_t q = 0;
         uint16_t *lrp = &L.hrp[static_cast<size_t>(t) * (T + 8)];
         for (int32_t i = r0; i < r1; ++i) {
@@ -219,25 +235,23 @@ int build_layout(pars3_handle *h) {
             for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
                 if (!half[e]) continue;
                 hpos[e] = L.hoff[t] + q;
+                hsrc[L.hoff[t] + q] = e + 1;
                 L.hcol[L.hoff[t] + q] = static_cast<uint16_t>(ci[e] - wb);
                 ++q;
             }
         }
-        for (int32_t i = r1; i <= r0 + T; ++i) lrp[i - r0] = static_cast<uint16_t>(q);
-        L.max_tile_half = std::max(L.max_tile_half, q);
+        for (int32_t i = r1; i <= r0 + T + 7; ++i) lrp[i - r0] = static_cast<uint16_t>(q);
     }
-    // (col, row) order per tile: the canonical tile lists filtered to half entries
     L.hhoff.assign(static_cast<size_t>(nt) + 1, 0);
-    L.hhrow.clear();
     for (int32_t t = 0; t < nt; ++t) {
-        int32_t r0 = t * T;
+        const int32_t r0 = t * T;
         int32_t q = 0, last = -1;
         for (int32_t s = h->tile_ptr[t]; s < h->tile_ptr[t + 1]; ++s) {
-            int32_t e = h->tile_list[s];
+            const int32_t e = h->tile_list[s];
             if (!half[e]) continue;
             L.hcperm[L.hoff[t] + q] = static_cast<uint16_t>(hpos[e] - L.hoff[t]);
             ++q;
-            int32_t j = ci[e];
+            const int32_t j = ci[e];
             if (j < r0 && j != last) {
                 L.hhrow.push_back(j);
                 last = j;
@@ -245,103 +259,222 @@ int build_layout(pars3_handle *h) {
         }
         L.hhoff[t + 1] = static_cast<int32_t>(L.hhrow.size());
     }
-    // full path: row i = its full lower entries (+a) then the full entries of
-    // column i (mirrored, -a), both in increasing column
-    L.frp.assign(static_cast<size_t>(n) + 1, 0);
+    // ---- 2. full-path length of every row: its non-half lower entries and the
+    // non-half entries of its column (mirrored)
+    std::vector<int32_t> flen(n, 0);
+    int64_t ftotal = 0;
     for (int32_t i = 0; i < n; ++i) {
-        int32_t cnt = 0;
-        if (!is_long[i]) {
-            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) cnt += !half[e];
-            for (int32_t s = cptr[i]; s < cptr[i + 1]; ++s) cnt += !half[cent[s]];
-        }
-        L.frp[i + 1] = L.frp[i] + cnt;
+        int32_t c = 0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) c += !half[e];
+        for (int32_t s = cptr[i]; s < cptr[i + 1]; ++s) c += !half[cent[s]];
+        flen[i] = c;
+        ftotal += c;
     }
-    const int64_t fn = L.frp[n];
-    L.fcol.resize(fn);
-    std::vector<int32_t> fsrc(fn);   // signed source entry: e+1 (lower) or -(e+1) (mirrored)
-    // long rows
-    L.lrow.clear();
-    L.lcptr.assign(1, 0);
-    L.lcbeg.clear();
-    L.lcend.clear();
-    L.lcol.clear();
-    std::vector<int32_t> lsrc;
-    for (int32_t i = 0; i < n; ++i) {
-        if (is_long[i]) {
-            int32_t start = static_cast<int32_t>(L.lcol.size());
-            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) { L.lcol.push_back(ci[e]); lsrc.push_back(e + 1); }
-            for (int32_t s = cptr[i]; s < cptr[i + 1]; ++s) {
-                int32_t e = cent[s];
-                L.lcol.push_back(row_of[e]);
-                lsrc.push_back(-(e + 1));
+    // ---- 3. long rows: longer than the cap, or the heaviest rows of a tile
+    // whose full entries exceed the cap (rows of at least kLongMin entries,
+    // longest first, ties by index)
+    const int64_t avg = nt > 0 ? (ftotal + nt - 1) / nt : 0;
+    const int64_t cap = cap_in > 0 ? cap_in : std::max<int64_t>(2048, round_up(2 * avg, kAlignFull));
+    L.cap_full = static_cast<int32_t>(std::min<int64_t>(cap, INT32_MAX));
+    const int64_t long_thr = std::min<int64_t>(h->long_row > 0 ? h->long_row : kSellMax, kSellMax);
+    std::vector<uint8_t> is_long(n, 0);
+    for (int32_t i = 0; i < n; ++i)
+        if (flen[i] > long_thr) is_long[i] = 1;
+    for (int32_t t = 0; t < nt; ++t) {
+        const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+        int64_t f = 0;
+        for (int32_t i = r0; i < r1; ++i)
+            if (!is_long[i]) f += flen[i];
+        if (f <= cap) continue;
+        // balance: rows of at least kLongMin entries, longest first (ties by
+        // index); then, if the tile is still above the cap, any row
+        for (int pass = 0; pass < 2 && f > cap; ++pass) {
+            std::vector<int32_t> cand;
+            for (int32_t i = r0; i < r1; ++i)
+                if (!is_long[i] && flen[i] > 0 && (pass == 1 || flen[i] >= kLongMin)) cand.push_back(i);
+            std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
+                return flen[a] != flen[b] ? flen[a] > flen[b] : a < b;
+            });
+            const int64_t goal = cap;
+            for (int32_t i : cand) {
+                if (f <= goal) break;
+                is_long[i] = 1;
+                f -= flen[i];
             }
-            int32_t end = static_cast<int32_t>(L.lcol.size());
-            L.lrow.push_back(i);
-            for (int32_t b = start; b < end; b += kLongChunk) {
-                L.lcbeg.push_back(b);
-                L.lcend.push_back(std::min(end, b + kLongChunk));
-            }
-            L.lcptr.push_back(static_cast<int32_t>(L.lcbeg.size()));
-            continue;
         }
-        int32_t q = L.frp[i];
+    }
+    // ---- 4. full path per tile as sliced ELL (rows sorted by length, longest first)
+    auto emit_row = [&](int32_t i, int32_t *colp, int32_t *srcp, int64_t stride) {
+        int64_t q = 0;
         for (int32_t e = rp[i]; e < rp[i + 1]; ++e)
-            if (!half[e]) { L.fcol[q] = ci[e]; fsrc[q] = e + 1; ++q; }
-        for (int32_t s = cptr[i]; s < cptr[i + 1]; ++s) {
-            int32_t e = cent[s];
-            if (!half[e]) { L.fcol[q] = row_of[e]; fsrc[q] = -(e + 1); ++q; }
+            if (!half[e]) { colp[q * stride] = ci[e]; srcp[q * stride] = e + 1; ++q; }
+        for (int32_t s2 = cptr[i]; s2 < cptr[i + 1]; ++s2) {
+            const int32_t e = cent[s2];
+            if (!half[e]) { colp[q * stride] = row_of[e]; srcp[q * stride] = -(e + 1); ++q; }
+        }
+        return q;
+    };
+    L.sl_off.assign(static_cast<size_t>(nt) + 1, 0);
+    L.sl_ent.assign(1, 0);
+    std::vector<std::vector<int32_t>> tile_rows(1);
+    {
+        std::vector<int32_t> rows;
+        for (int32_t t = 0; t < nt; ++t) {
+            const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+            rows.clear();
+            for (int32_t i = r0; i < r1; ++i)
+                if (!is_long[i] && flen[i] > 0) rows.push_back(i);
+            std::sort(rows.begin(), rows.end(), [&](int32_t a, int32_t b) {
+                return flen[a] != flen[b] ? flen[a] > flen[b] : a < b;
+            });
+            int64_t tile_ent = 0;
+            for (size_t g = 0; g < rows.size(); g += kSlice) {
+                const int32_t width = flen[rows[g]];
+                L.sl_ent.push_back(static_cast<int32_t>(L.sl_ent.back() + static_cast<int64_t>(kSlice) * width));
+                for (int l = 0; l < kSlice; ++l) {
+                    const size_t k = g + l;
+                    L.sl_meta.push_back(k < rows.size()
+                                            ? static_cast<uint32_t>(rows[k] - r0) | (static_cast<uint32_t>(flen[rows[k]]) << 16)
+                                            : 0xffffu);
+                }
+                tile_ent += static_cast<int64_t>(kSlice) * width;
+            }
+            L.sl_off[t + 1] = static_cast<int32_t>(L.sl_ent.size() - 1);
+            L.max_tile_full = static_cast<int32_t>(std::max<int64_t>(L.max_tile_full, tile_ent));
+            L.max_tile_slices = std::max(L.max_tile_slices, L.sl_off[t + 1] - L.sl_off[t]);
         }
     }
-    // values per precision
-    auto fill_vals = [&](const std::vector<int32_t> &src, std::vector<double> &v64,
-                         std::vector<float> &v32, std::vector<uint16_t> &v16) {
+    const int64_t fnp = L.sl_ent.back();
+    L.fcol.assign(fnp, 0);
+    std::vector<int32_t> fsrc(fnp, 0);  // +(e+1): lower entry, -(e+1): mirrored entry, 0: padding
+    for (int32_t t = 0; t < nt; ++t) {
+        const int32_t r0 = t * T;
+        for (int32_t s2 = L.sl_off[t]; s2 < L.sl_off[t + 1]; ++s2)
+            for (int l = 0; l < kSlice; ++l) {
+                const uint32_t meta = L.sl_meta[static_cast<size_t>(s2) * kSlice + l];
+                if ((meta & 0xffffu) == 0xffffu) continue;
+                const int32_t i = r0 + static_cast<int32_t>(meta & 0xffffu);
+                emit_row(i, &L.fcol[L.sl_ent[s2] + l], &fsrc[L.sl_ent[s2] + l], kSlice);
+            }
+    }
+    // ---- 5. long rows, concatenated and chunked
+    L.lrp.assign(1, 0);
+    for (int32_t i = 0; i < n; ++i)
+        if (is_long[i]) {
+            L.lrow.push_back(i);
+            L.lrp.push_back(L.lrp.back() + flen[i]);
+        }
+    const int64_t ltot = L.lrp.back();
+    L.lcol.assign(round_up(ltot, kAlignFull), 0);
+    std::vector<int32_t> lsrc(L.lcol.size(), 0);
+    for (size_t l = 0; l < L.lrow.size(); ++l) emit_row(L.lrow[l], &L.lcol[L.lrp[l]], &lsrc[L.lrp[l]], 1);
+    // chunks: consecutive long entries, at most kLongChunk entries and T rows each
+    const size_t nlong = L.lrow.size();
+    L.lc0.assign(nlong, 0);
+    L.lc1.assign(nlong, 0);
+    L.lcslot.assign(1, 0);
+    {
+        size_t l = 0;
+        int64_t beg = 0;
+        while (beg < ltot) {
+            while (L.lrp[l + 1] <= beg) ++l;
+            int64_t end = std::min<int64_t>(ltot, beg + kLongChunk);
+            size_t m = l;
+            while (m + 1 < nlong && L.lrp[m + 1] < end) {
+                if (static_cast<int64_t>(m + 1 - l) + 1 > T) {   // next row would exceed T rows
+                    end = L.lrp[m + 1];
+                    break;
+                }
+                ++m;
+            }
+            const int32_t c = static_cast<int32_t>(L.lcbeg.size());
+            L.lcbeg.push_back(static_cast<int32_t>(beg));
+            L.lcend.push_back(static_cast<int32_t>(end));
+            L.lcfirst.push_back(static_cast<int32_t>(l));
+            L.lcrows.push_back(static_cast<int32_t>(m - l + 1));
+            L.lcslot.push_back(L.lcslot.back() + static_cast<int32_t>(m - l + 1));
+            for (size_t u = l; u <= m; ++u) {
+                if (L.lrp[u] >= beg) L.lc0[u] = c;
+                L.lc1[u] = c;
+            }
+            beg = end;
+        }
+    }
+    L.nslots = L.lcslot.back();
+    // ---- 6. fold items: each receiving row once, in row order
+    {
+        std::vector<int32_t> hidx(n, -1), lidx(n, -1);
+        for (size_t k = 0; k < L.hhrow.size(); ++k) hidx[L.hhrow[k]] = static_cast<int32_t>(k);
+        for (size_t l = 0; l < L.lrow.size(); ++l) lidx[L.lrow[l]] = static_cast<int32_t>(l);
+        for (int32_t i = 0; i < n; ++i)
+            if (hidx[i] >= 0 || lidx[i] >= 0) {
+                L.fold_row.push_back(i);
+                L.fold_halo.push_back(hidx[i]);
+                L.fold_long.push_back(lidx[i]);
+            }
+    }
+    // ---- 7. values per precision
+    auto fill_vals = [&](const std::vector<int32_t> &src, std::vector<double> &v64, std::vector<float> &v32,
+                         std::vector<uint16_t> &v16) {
         const size_t m = src.size();
-        if (h->dtypes & PARS3_DTYPE_BIT(PARS3_F64)) v64.resize(m);
-        if (h->dtypes & PARS3_DTYPE_BIT(PARS3_F32)) v32.resize(m);
-        if (h->dtypes & PARS3_DTYPE_BIT(PARS3_BF16)) v16.resize(m);
+        if (h->dtypes & PARS3_DTYPE_BIT(PARS3_F64)) v64.assign(m, 0.0);
+        if (h->dtypes & PARS3_DTYPE_BIT(PARS3_F32)) v32.assign(m, 0.0f);
+        if (h->dtypes & PARS3_DTYPE_BIT(PARS3_BF16)) v16.assign(m, 0);
         for (size_t q = 0; q < m; ++q) {
-            int32_t s = src[q];
-            double a = s > 0 ? h->val[s - 1] : -h->val[-s - 1];
+            const int32_t s = src[q];
+            if (s == 0) continue;
+            const double a = s > 0 ? h->val[s - 1] : -h->val[-s - 1];
+            const float f = static_cast<float>(a);
             if (!v64.empty()) v64[q] = a;
-            float f = static_cast<float>(a);
             if (!v32.empty()) v32[q] = f;
             if (!v16.empty()) v16[q] = f32_to_bf16_rne(f);
         }
     };
-    std::vector<int32_t> hsrc(hn, 0);
-    for (int64_t e = 0; e < nnz; ++e)
-        if (half[e]) hsrc[hpos[e]] = static_cast<int32_t>(e + 1);
-    // padding slots carry source 0 -> value handled below as 0
-    {
-        const size_t m = hsrc.size();
-        if (h->dtypes & PARS3_DTYPE_BIT(PARS3_F64)) L.hval64.assign(m, 0.0);
-        if (h->dtypes & PARS3_DTYPE_BIT(PARS3_F32)) L.hval32.assign(m, 0.0f);
-        if (h->dtypes & PARS3_DTYPE_BIT(PARS3_BF16)) L.hval16.assign(m, 0);
-        for (size_t q = 0; q < m; ++q) {
-            if (hsrc[q] == 0) continue;
-            double a = h->val[hsrc[q] - 1];
-            float f = static_cast<float>(a);
-            if (!L.hval64.empty()) L.hval64[q] = a;
-            if (!L.hval32.empty()) L.hval32[q] = f;
-            if (!L.hval16.empty()) L.hval16[q] = f32_to_bf16_rne(f);
-        }
-    }
+    fill_vals(hsrc, L.hval64, L.hval32, L.hval16);
     fill_vals(fsrc, L.fval64, L.fval32, L.fval16);
     fill_vals(lsrc, L.lval64, L.lval32, L.lval16);
     return PARS3_OK;
 }
 
+// Largest layout that fits: start with every middle entry of a fitting tile
+// on the half path and the balance cap on the full path; while two stages
+// do not fit in shared memory, halve whichever of the two dominates (more
+// middle tiles become full storage, more rows go to the chunked long path).
+int build_layout(pars3_handle *h) {
+    int64_t mcap = half_room(h);
+    if (mcap < 0) return PARS3_EUNSUPPORTED;
+    int64_t cap = 0;
+    for (int iter = 0; iter < 40; ++iter) {
+        int rc = build_layout_try(h, mcap, cap);
+        if (rc != PARS3_OK) return rc;
+        if (max_smem_all(h) <= kSmemLimit) return PARS3_OK;
+        const int64_t half_bytes = static_cast<int64_t>(h->L.max_tile_half) * 12;
+        const int64_t full_bytes = static_cast<int64_t>(h->L.max_tile_full) * 12;
+        if (half_bytes >= full_bytes && h->L.max_tile_half > 0) {
+            mcap = h->L.max_tile_half / 2;
+        } else if (h->L.max_tile_full > kLongSlots / 2) {
+            cap = std::max<int64_t>(h->L.max_tile_full / 2, 64);
+        } else if (h->L.max_tile_half > 0) {
+            mcap = h->L.max_tile_half / 2;
+        } else {
+            return PARS3_EUNSUPPORTED;
+        }
+    }
+    return PARS3_EUNSUPPORTED;
+}
+
 int64_t model_bytes(const pars3_handle *h, int dtype) {
     if (!(h->dtypes & PARS3_DTYPE_BIT(dtype))) return 0;
     const Layout &L = h->L;
-    int64_t sv = dtype == PARS3_F64 ? 8 : (dtype == PARS3_F32 ? 4 : 2);
-    int64_t sx = dtype == PARS3_F64 ? 8 : 4;
+    const int64_t sv = dtype == PARS3_F64 ? 8 : (dtype == PARS3_F32 ? 4 : 2);
+    const int64_t sx = dtype == PARS3_F64 ? 8 : 4;
     int64_t b = 0;
-    b += static_cast<int64_t>(L.hcol.size()) * (sv + 2 + 2);             // half values, columns, order
-    b += static_cast<int64_t>(h->ntiles) * (h->T + 8) * 2;               // tile row pointers
-    b += static_cast<int64_t>(L.fcol.size()) * (sv + 4) + (h->n + 1) * 4; // full rows
-    b += static_cast<int64_t>(L.lcol.size()) * (sv + 4);                  // long rows
-    b += 2 * static_cast<int64_t>(h->n) * sx;                             // x once, y once
+    b += static_cast<int64_t>(L.hcol.size()) * (sv + 2 + 2);               // half values, columns, order
+    b += static_cast<int64_t>(L.fcol.size()) * (sv + 4);                   // full rows (sliced ELL)
+    b += static_cast<int64_t>(L.sl_meta.size()) * 4 + static_cast<int64_t>(L.sl_ent.size()) * 4;
+    b += static_cast<int64_t>(L.lcol.size()) * (sv + 4);                   // long rows
+    b += static_cast<int64_t>(h->ntiles) * (h->T + 8) * 2;                 // tile row pointers
+    b += 2 * static_cast<int64_t>(h->n) * sx;                              // x once, y once
     return b;
 }
 
@@ -385,7 +518,7 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
             std::vector<int32_t> pinv(n);
             for (int32_t k = 0; k < n; ++k) pinv[h->perm[k]] = k;
             int64_t bw = bandwidth(n, rowptr, col, pinv.data());
-            int32_t wcap = (prm.dtypes & PARS3_DTYPE_BIT(PARS3_F64)) ? 4096 : 8192;
+            int32_t wcap = (prm.dtypes & PARS3_DTYPE_BIT(PARS3_F64)) ? 1024 : 2048;
             auto_cut(bw, 32, wcap, 1024, &prm.T, &prm.W);
         }
         if (!is_pow2(prm.T) || !is_pow2(prm.W) || prm.W < 32 || prm.W > prm.T || prm.T > 32768) {
@@ -395,7 +528,7 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
         h->T = prm.T;
         h->W = prm.W;
         h->ntiles = n > 0 ? (n + prm.T - 1) / prm.T : 0;
-        h->long_row = prm.long_row > 0 ? prm.long_row : std::max(2048, 4 * prm.T);
+        h->long_row = prm.long_row > 0 ? prm.long_row : 0;
         rc = canonical_split(h, rowptr, col, val);
         if (rc == PARS3_OK) rc = build_layout(h);
         if (rc != PARS3_OK) { delete h; return rc; }
@@ -436,11 +569,13 @@ extern "C" int pars3_info_get(const pars3_handle *h, pars3_info *o) {
     o->ntiles = h->ntiles;
     o->dtypes = h->dtypes;
     o->nnz = h->nnz;
-    int64_t hsum = 0;
+    int64_t hsum = 0, fsum = 0;
     for (int32_t c : h->L.hcnt) hsum += c;
+    for (uint32_t m : h->L.sl_meta)
+        if ((m & 0xffffu) != 0xffffu) fsum += m >> 16;
     o->half_entries = hsum;
-    o->full_entries = static_cast<int64_t>(h->L.fcol.size());
-    o->long_entries = static_cast<int64_t>(h->L.lcol.size());
+    o->full_entries = fsum;
+    o->long_entries = h->L.lrp.empty() ? 0 : h->L.lrp.back();
     o->long_rows = static_cast<int32_t>(h->L.lrow.size());
     o->long_chunks = static_cast<int32_t>(h->L.lcbeg.size());
     o->halo_targets = static_cast<int64_t>(h->L.hhrow.size());
@@ -460,9 +595,8 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
     if (!h) return PARS3_EINVAL;
     const Layout &L = h->L;
     const int32_t n = h->n, T = h->T, W = h->W;
-    const double *v64 = L.hval64.empty() ? nullptr : L.hval64.data();
+    const bool has64 = (h->dtypes & PARS3_DTYPE_BIT(PARS3_F64)) != 0;
     try {
-        // expected multiset: (row, col, value) for every entry and its mirror
         struct E { int32_t r, c; double v; };
         std::vector<E> want, got;
         want.reserve(2 * h->nnz);
@@ -473,41 +607,75 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
             }
         got.reserve(2 * h->nnz);
         for (int32_t t = 0; t < h->ntiles; ++t) {
-            int32_t r0 = t * T, r1 = std::min(n, r0 + T), wb = r0 - W;
+            const int32_t r0 = t * T, r1 = std::min(n, r0 + T), wb = r0 - W;
             const uint16_t *lrp = &L.hrp[static_cast<size_t>(t) * (T + 8)];
-            if (lrp[r1 - r0] != L.hcnt[t]) return PARS3_EINVAL;
+            if (lrp[r1 - r0] != L.hcnt[t] || L.hoff[t] % kAlignHalf) return PARS3_EINVAL;
             std::vector<uint8_t> used(L.hcnt[t], 0);
             for (int32_t i = r0; i < r1; ++i)
                 for (int32_t q = lrp[i - r0]; q < lrp[i - r0 + 1]; ++q) {
-                    int32_t j = wb + L.hcol[L.hoff[t] + q];
+                    const int32_t j = wb + L.hcol[L.hoff[t] + q];
                     if (j < std::max(wb, 0) || j >= i || i - j > W) return PARS3_EINVAL;
-                    double a = v64 ? v64[L.hoff[t] + q] : 0.0;
+                    const double a = has64 ? L.hval64[L.hoff[t] + q] : 0.0;
                     got.push_back({i, j, a});
                     got.push_back({j, i, -a});
                 }
             for (int32_t q = 0; q < L.hcnt[t]; ++q) {
-                uint16_t e = L.hcperm[L.hoff[t] + q];
+                const uint16_t e = L.hcperm[L.hoff[t] + q];
                 if (e >= L.hcnt[t] || used[e]) return PARS3_EINVAL;
                 used[e] = 1;
                 if (q > 0 && L.hcol[L.hoff[t] + e] < L.hcol[L.hoff[t] + L.hcperm[L.hoff[t] + q - 1]])
                     return PARS3_EINVAL;
             }
+            std::vector<uint8_t> seen(r1 - r0, 0);
+            for (int32_t s2 = L.sl_off[t]; s2 < L.sl_off[t + 1]; ++s2) {
+                const int32_t width = (L.sl_ent[s2 + 1] - L.sl_ent[s2]) / kSlice;
+                for (int l = 0; l < kSlice; ++l) {
+                    const uint32_t meta = L.sl_meta[static_cast<size_t>(s2) * kSlice + l];
+                    if ((meta & 0xffffu) == 0xffffu) continue;
+                    const int32_t rl = static_cast<int32_t>(meta & 0xffffu), len = static_cast<int32_t>(meta >> 16);
+                    if (rl >= r1 - r0 || seen[rl] || len > width || len > kSellMax) return PARS3_EINVAL;
+                    seen[rl] = 1;
+                    for (int32_t m = 0; m < len; ++m) {
+                        const int64_t q = L.sl_ent[s2] + static_cast<int64_t>(m) * kSlice + l;
+                        got.push_back({r0 + rl, L.fcol[q], has64 ? L.fval64[q] : 0.0});
+                    }
+                }
+            }
         }
-        for (int32_t i = 0; i < n; ++i)
-            for (int32_t q = L.frp[i]; q < L.frp[i + 1]; ++q)
-                got.push_back({i, L.fcol[q], L.fval64.empty() ? 0.0 : L.fval64[q]});
         for (size_t l = 0; l < L.lrow.size(); ++l)
-            for (int32_t c = L.lcptr[l]; c < L.lcptr[l + 1]; ++c)
-                for (int32_t q = L.lcbeg[c]; q < L.lcend[c]; ++q)
-                    got.push_back({L.lrow[l], L.lcol[q], L.lval64.empty() ? 0.0 : L.lval64[q]});
+            for (int32_t q = L.lrp[l]; q < L.lrp[l + 1]; ++q)
+                got.push_back({L.lrow[l], L.lcol[q], has64 ? L.lval64[q] : 0.0});
+        // chunks tile the long list in order; slots consecutive; row spans consistent
+        int64_t pos = 0;
+        for (size_t c = 0; c < L.lcbeg.size(); ++c) {
+            if (L.lcbeg[c] != pos || L.lcend[c] <= L.lcbeg[c] || L.lcend[c] - L.lcbeg[c] > kLongChunk) return PARS3_EINVAL;
+            pos = L.lcend[c];
+            const int32_t l0 = L.lcfirst[c];
+            if (!(L.lrp[l0] <= L.lcbeg[c] && L.lcbeg[c] < L.lrp[l0 + 1])) return PARS3_EINVAL;
+            if (L.lcslot[c + 1] - L.lcslot[c] != L.lcrows[c] || L.lcrows[c] > T) return PARS3_EINVAL;
+        }
+        if (!L.lrow.empty() && pos != L.lrp.back()) return PARS3_EINVAL;
+        for (size_t l = 0; l < L.lrow.size(); ++l) {
+            const int32_t c0 = L.lc0[l], c1 = L.lc1[l];
+            if (!(L.lcbeg[c0] <= L.lrp[l] && L.lrp[l] < L.lcend[c0])) return PARS3_EINVAL;
+            if (!(L.lcbeg[c1] < L.lrp[l + 1] && L.lrp[l + 1] <= L.lcend[c1])) return PARS3_EINVAL;
+        }
         if (got.size() != want.size()) return PARS3_EINVAL;
         auto key = [](const E &a, const E &b) { return a.r != b.r ? a.r < b.r : a.c < b.c; };
         std::sort(want.begin(), want.end(), key);
         std::sort(got.begin(), got.end(), key);
         for (size_t q = 0; q < got.size(); ++q) {
             if (got[q].r != want[q].r || got[q].c != want[q].c) return PARS3_EINVAL;
-            if (v64 && got[q].v != want[q].v) return PARS3_EINVAL;
+            if (has64 && got[q].v != want[q].v) return PARS3_EINVAL;
         }
+        // fold items: rows strictly increasing, halo targets and long rows each once
+        size_t nh = 0, nl = 0;
+        for (size_t f = 0; f < L.fold_row.size(); ++f) {
+            if (f > 0 && L.fold_row[f] <= L.fold_row[f - 1]) return PARS3_EINVAL;
+            nh += L.fold_halo[f] >= 0;
+            nl += L.fold_long[f] >= 0;
+        }
+        if (nh != L.hhrow.size() || nl != L.lrow.size()) return PARS3_EINVAL;
     } catch (const std::bad_alloc &) {
         return PARS3_ENOMEM;
     }

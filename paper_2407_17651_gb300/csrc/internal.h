@@ -10,9 +10,14 @@
 namespace pars3 {
 
 constexpr int kNumDtypes = 3;
-constexpr int kAlignEntries = 8;       // half-path tile segments start on 16-byte boundaries
-constexpr int kBlock = 512;            // threads of the tile kernel
-constexpr int kLongChunk = 8192;       // entries per long-row chunk (one block each)
+constexpr int kAlignHalf = 8;          // half-path tile segments start on 16-byte boundaries (u16, bf16)
+constexpr int kAlignFull = 16;         // full-path tile segments: 64 B for int32 columns, 128 B for fp64
+constexpr int kBlock = 1024;           // threads of the persistent tile kernel (one block per SM)
+constexpr int kStages = 2;             // tile staging buffers in flight per block
+constexpr int kLongChunk = 4096;       // entries per long-row chunk (one block each)
+constexpr int kLongMin = 256;          // shortest row moved to the long path to balance tiles
+constexpr int kSellMax = 32;           // longer full-path rows go to the long path
+constexpr int kSlice = 32;             // rows per sliced-ELL slice (one warp)
 constexpr int kSmemLimit = 227 * 1024; // opt-in shared memory per block on sm_100/sm_103
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -20,40 +25,63 @@ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // Device layout on the host side (vectors) and its device mirror.
 struct Layout {
     // half path: per tile t, entries [hoff[t], hoff[t] + hcnt[t]) in (row, col) order
-    std::vector<int32_t> hoff;      // [ntiles+1] (starts padded to kAlignEntries)
+    std::vector<int32_t> hoff;      // [ntiles+1] (starts padded to kAlignHalf)
     std::vector<int32_t> hcnt;      // [ntiles]
     std::vector<uint16_t> hrp;      // [ntiles*(T+8)] tile-local row pointers
     std::vector<uint16_t> hcol;     // window position p = j - (tT - W)
     std::vector<uint16_t> hcperm;   // tile-local entry index, (col, row) order
     std::vector<int32_t> hhoff;     // [ntiles+1] halo targets of tile t
     std::vector<int32_t> hhrow;     // global row of each halo target (sorted per tile)
-    // full path: row i holds [frp[i], frp[i+1]) (long rows: empty)
-    std::vector<int32_t> frp;       // [n+1]
+    // full path, sliced ELL: the short rows of tile t, sorted by length
+    // (longest first, ties by row), form 32-row slices sl_off[t] .. sl_off[t+1]-1;
+    // slice s stores its entries slot-major at [sl_ent[s], sl_ent[s+1]) (slot m
+    // of lane l at sl_ent[s] + 32 m + l); sl_meta[32 s + l] = tile-local row
+    // | (row length << 16), row 0xffff for an empty lane
+    std::vector<int32_t> sl_off;    // [ntiles+1]
+    std::vector<int32_t> sl_ent;    // [nslices+1]
+    std::vector<uint32_t> sl_meta;  // [nslices*32]
     std::vector<int32_t> fcol;
-    // long rows, chunked
-    std::vector<int32_t> lrow;      // [nlong] row ids
-    std::vector<int32_t> lcptr;     // [nlong+1] chunk range of each long row
-    std::vector<int32_t> lcbeg, lcend;  // [nchunks] entry range of each chunk in lcol/lval
-    std::vector<int32_t> lcol;
+    // long rows: full entries of long row l are [lrp[l], lrp[l+1]) of lcol/lval;
+    // chunk c covers entries [lcbeg[c], lcend[c]) (at most kLongChunk entries
+    // and T rows) and touches long rows lcfirst[c] .. lcfirst[c]+lcrows[c]-1,
+    // whose partial sums go to slots lcslot[c] + u; long row l spans chunks
+    // lc0[l] .. lc1[l]
+    std::vector<int32_t> lrow;      // [nlong]
+    std::vector<int32_t> lrp;       // [nlong+1]
+    std::vector<int32_t> lc0, lc1;  // [nlong]
+    std::vector<int32_t> lcbeg, lcend, lcfirst, lcrows, lcslot;  // [nchunks] (+1 for lcslot)
+    std::vector<int32_t> lcol;      // padded to kAlignFull
+    // fold items: one per row that receives a halo sum and/or long-row partials
+    std::vector<int32_t> fold_row, fold_halo, fold_long;  // halo index / long index or -1
     // values per precision (fp64 / fp32 / bf16 bits)
     std::vector<double> hval64, fval64, lval64;
     std::vector<float> hval32, fval32, lval32;
     std::vector<uint16_t> hval16, fval16, lval16;
     int32_t max_tile_half = 0;
+    int32_t max_tile_full = 0;      // sliced-ELL entries (with padding) of the largest tile
+    int32_t max_tile_slices = 0;
+    int32_t cap_full = 0;
+    int64_t nslots = 0;
 };
 
 struct DevLayout {
     int32_t *hoff = nullptr, *hcnt = nullptr;
     uint16_t *hrp = nullptr, *hcol = nullptr, *hcperm = nullptr;
     int32_t *hhoff = nullptr, *hhrow = nullptr;
-    int32_t *frp = nullptr, *fcol = nullptr;
-    int32_t *lrow = nullptr, *lcptr = nullptr, *lcbeg = nullptr, *lcend = nullptr, *lcol = nullptr;
+    int32_t *sl_off = nullptr, *sl_ent = nullptr;
+    uint32_t *sl_meta = nullptr;
+    int32_t *fcol = nullptr;
+    int32_t *lrow = nullptr, *lrp = nullptr, *lc0 = nullptr, *lc1 = nullptr;
+    int32_t *lcbeg = nullptr, *lcend = nullptr, *lcfirst = nullptr, *lcrows = nullptr, *lcslot = nullptr;
+    int32_t *lcol = nullptr;
+    int32_t *fold_row = nullptr, *fold_halo = nullptr, *fold_long = nullptr;
     void *hval[kNumDtypes] = {nullptr, nullptr, nullptr};
     void *fval[kNumDtypes] = {nullptr, nullptr, nullptr};
     void *lval[kNumDtypes] = {nullptr, nullptr, nullptr};
-    // scratch: halo sums and long-row partial sums (sized for fp64, k_max columns)
+    // scratch: halo sums and long-row partial sums (fp64-sized, scratch_k columns)
     void *halo = nullptr;
     void *lpart = nullptr;
+    int32_t scratch_k = 0;
     int32_t *perm = nullptr;
     int32_t *err = nullptr;          // device error word
     // staging for pars3_spmv_host
@@ -95,6 +123,9 @@ int64_t bandwidth(int32_t n, const int32_t *rowptr, const int32_t *col, const in
 void auto_cut(int64_t bw, int32_t w_min, int32_t w_cap, int32_t t_min, int32_t *T, int32_t *W);
 int build_layout(pars3_handle *h);
 int smem_bytes_for(const pars3_handle *h, int dtype);
+int32_t stage_full_entries(const pars3_handle *h);
+int sm_count();
+void dtype_sizes(int dtype, uint32_t *vsz, uint32_t *xsz, uint32_t *asz);
 int64_t model_bytes(const pars3_handle *h, int dtype);
 uint16_t f32_to_bf16_rne(float f);
 

@@ -1,28 +1,35 @@
 // spmv.cu -- y = (alpha I + S) x on the device for a split handle.
 //
-// One launch of the tile kernel covers every row tile (block t owns rows
-// [tT, tT+T), Sec. 3: block-row ownership, Fig. 2) plus one block per chunk
-// of a long row; a second, small launch folds the cross-tile (halo) mirrored
-// sums and the long-row partial sums into y in a fixed order.  No atomics:
-// every y entry is written by one thread, and every sum runs in an order
-// fixed by the layout and the block size, so results are bitwise
-// reproducible.
+// Two launches per product.  The tile kernel is persistent: one block of
+// kBlock threads per SM walks a fixed list of work items (row tiles, then
+// long-row chunks) in a static round-robin order; a second, small launch
+// folds the cross-tile (halo) mirrored sums and the long-row partial sums
+// into y.  No atomics: every y entry has one writer per launch and every sum
+// runs in an order fixed by the layout and the block size, so results are
+// bitwise reproducible from run to run and independent of which block
+// processed which item.
 //
-// Tile kernel, block t:
-//  1. TMA: a 1-D bulk copy stages the x window [tT-W, tT+T) into shared
-//     memory (the x slice a row block needs, Sec. 3.1.2; the paper ships it
-//     between MPI ranks, here it comes from HBM through the copy engine);
-//  2. half pass: each middle entry l_ij of the tile is read once (Eqs. 2-6):
-//     l_ij x_j is summed into row i, and the mirrored product l_ij x_i is kept
-//     in shared memory;
-//  3. full pass: outer rows (both triangles stored) are plain gathers;
-//  4. the mirrored products are summed per column in the (column, row) order
-//     of the canonical tile list: columns inside the tile complete their row,
-//     columns before the tile (conflicting, Fig. 2 R2) go to the halo list.
+// Work item = row tile t (rows [tT, tT+T): the block-row ownership of Sec. 3
+// and Fig. 2).  Its data is staged into shared memory by TMA bulk copies,
+// kStages items ahead: the x window [tT-W, tT+T) (the x slice a row block
+// needs, Sec. 3.1.2), the middle entries of the tile (values, window
+// columns, (column,row) order, row pointers) and its full-storage rows in
+// sliced-ELL order.  Then:
+//  1. full pass: each warp sums the rows of its 32-row slices, one lane per
+//     row, reading the slice from shared memory (slot m of lane l at 32m+l:
+//     no bank conflicts) and gathering x_j from global memory, eight
+//     independent gathers in flight per lane;
+//  2. half pass: each middle entry l_ij is read once and used twice (Eqs.
+//     2-6): l_ij x_j is summed into row i, the mirrored product l_ij x_i is
+//     kept in shared memory;
+//  3. the mirrored products are summed per column in the (column, row)
+//     order of the canonical tile list: columns inside the tile complete
+//     their row, columns before the tile (the conflicting region R2 of
+//     Fig. 2) go to the halo list that the fold adds to the previous tile.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
-#include <cstdio>
 
 #include "devcommon.cuh"
 #include "internal.h"
@@ -32,15 +39,17 @@ namespace pars3 {
 
 template <typename VT, typename XT, typename AT>
 struct SpmvArgs {
-    int32_t n, T, W, ntiles, M;
+    int32_t n, T, W, ntiles, nchunks, Mh, S, F;
     const int32_t *hoff, *hcnt;
     const uint16_t *hrp, *hcol, *hcperm;
     const VT *hval;
     const int32_t *hhoff, *hhrow;
     AT *halo;
-    const int32_t *frp, *fcol;
+    const int32_t *sl_off, *sl_ent;
+    const uint32_t *sl_meta;
+    const int32_t *fcol;
     const VT *fval;
-    const int32_t *lcbeg, *lcend, *lcol;
+    const int32_t *lrp, *lcbeg, *lcend, *lcfirst, *lcrows, *lcslot, *lcol;
     const VT *lval;
     AT *lpart;
     const XT *x;
@@ -49,148 +58,331 @@ struct SpmvArgs {
     int32_t *err;
 };
 
+template <typename VT> __device__ __forceinline__ typename Val<VT>::acc sval(const VT *p, int e);
+template <> __device__ __forceinline__ double sval<double>(const double *p, int e) { return p[e]; }
+template <> __device__ __forceinline__ float sval<float>(const float *p, int e) { return p[e]; }
+template <> __device__ __forceinline__ float sval<uint16_t>(const uint16_t *p, int e) { return bf16_bits_to_f32(p[e]); }
+
+constexpr int kUnroll = 8;       // independent gathers in flight per lane
+constexpr int kShortRow = 16;    // middle rows longer than this are summed by the whole warp
+
+// Sliced-ELL row of lane l in shared memory: slots base + 32 m + l, m < len.
 template <typename VT, typename XT, typename AT>
-__device__ __forceinline__ void long_chunk(const SpmvArgs<VT, XT, AT> &a, int c, unsigned char *smem) {
-    AT *red = reinterpret_cast<AT *>(smem);
-    const int tid = threadIdx.x, P = blockDim.x;
-    const int beg = a.lcbeg[c], end = a.lcend[c];
+__device__ __forceinline__ AT slice_row_sum(const VT *val_s, const int32_t *col_s, int base, int len,
+                                            const XT *__restrict__ xg) {
     AT acc = AT(0);
-    for (int e = beg + tid; e < end; e += P)
-        acc += Val<VT>::ld_stream(a.lval + e) * static_cast<AT>(__ldg(a.x + a.lcol[e]));
-    red[tid] = acc;
-    __syncthreads();
-    for (int s = P >> 1; s > 0; s >>= 1) {
-        if (tid < s) red[tid] += red[tid + s];
-        __syncthreads();
+    for (int m0 = 0; m0 < len; m0 += kUnroll) {
+        AT v[kUnroll], xv[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            v[u] = AT(0);
+            xv[u] = AT(0);
+            if (m0 + u < len) {
+                const int q = base + (m0 + u) * kSlice;
+                v[u] = sval<VT>(val_s, q);
+                xv[u] = static_cast<AT>(__ldg(xg + col_s[q]));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (m0 + u < len) acc += v[u] * xv[u];
     }
-    if (tid == 0) a.lpart[c] = red[0];
+    return acc;
+}
+
+// Row [e0, e1) of a long-row chunk by a whole warp: lane l takes entries
+// e0+l, e0+l+32, ... in order, then a butterfly reduction (every lane ends
+// with the same bits: each step adds the same two partial sums, only in
+// swapped operand order).
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ AT row_sum_warp(int e0, int e1, const int32_t *col_s, const VT *val_s,
+                                           const XT *__restrict__ xg) {
+    const int lane = threadIdx.x & 31;
+    AT acc = AT(0);
+    for (int base = e0 + lane; base < e1; base += 32 * 4) {
+        AT v[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = base + 32 * u;
+            v[u] = AT(0);
+            xv[u] = AT(0);
+            if (e < e1) {
+                v[u] = sval<VT>(val_s, e);
+                xv[u] = static_cast<AT>(__ldg(xg + col_s[e]));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (base + 32 * u < e1) acc += v[u] * xv[u];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Half-storage row of the middle part: returns sum_j l_rj x_j and stores the
+// mirrored products q[e] = l_rj x_r (q may alias the value array: entry e is
+// read before it is overwritten, by the same thread).
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ AT half_row_thread(int e0, int e1, const VT *hval, const uint16_t *hcol, AT *q,
+                                              const XT *xs, AT xr) {
+    AT acc = AT(0);
+    for (int e = e0; e < e1; ++e) {
+        const AT v = sval<VT>(hval, e);
+        const AT xj = static_cast<AT>(xs[hcol[e]]);
+        q[e] = v * xr;
+        acc += v * xj;
+    }
+    return acc;
 }
 
 template <typename VT, typename XT, typename AT>
-__global__ void __launch_bounds__(kBlock) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
-    extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ AT half_row_warp(int e0, int e1, const VT *hval, const uint16_t *hcol, AT *q,
+                                            const XT *xs, AT xr) {
+    const int lane = threadIdx.x & 31;
+    AT acc = AT(0);
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const AT v = sval<VT>(hval, e);
+        const AT xj = static_cast<AT>(xs[hcol[e]]);
+        q[e] = v * xr;
+        acc += v * xj;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+template <typename VT, typename XT>
+struct Stage {
+    XT *xs;
+    uint16_t *hrp, *hcol, *cperm;
+    VT *hval;
+    uint32_t *fmeta;
+    VT *fval;
+    int32_t *fcol;
+    __device__ Stage(unsigned char *b, const StageLayout &g) {
+        xs = reinterpret_cast<XT *>(b + g.xs);
+        hrp = reinterpret_cast<uint16_t *>(b + g.hrp);
+        hval = reinterpret_cast<VT *>(b + g.hval);
+        hcol = reinterpret_cast<uint16_t *>(b + g.hcol);
+        cperm = reinterpret_cast<uint16_t *>(b + g.cperm);
+        fmeta = reinterpret_cast<uint32_t *>(b + g.fmeta);
+        fval = reinterpret_cast<VT *>(b + g.fval);
+        fcol = reinterpret_cast<int32_t *>(b + g.fcol);
+    }
+};
+
+// Thread 0: arm the stage's mbarrier and issue the bulk copies of one item.
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ void issue_item(const SpmvArgs<VT, XT, AT> &a, int item, Stage<VT, XT> &S,
+                                           uint64_t *bar) {
+    if (item < a.ntiles) {
+        const int t = item;
+        const int r0 = t * a.T, r1 = min(r0 + a.T, a.n);
+        const int wb = r0 - a.W, wlo = max(wb, 0);
+        const uint32_t nbulk = (static_cast<uint32_t>(r1 - wlo) * sizeof(XT)) & ~15u;
+        const int hb = a.hoff[t], hm = a.hcnt[t];
+        const uint32_t hmp = static_cast<uint32_t>((hm + kAlignHalf - 1) / kAlignHalf * kAlignHalf);
+        const uint32_t rpb = static_cast<uint32_t>(a.T + 8) * 2u;
+        const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
+        const int e0 = a.sl_ent[s0], e1 = a.sl_ent[s1];
+        const uint32_t fe = static_cast<uint32_t>(e1 - e0);
+        uint32_t tx = nbulk + rpb;
+        if (hm > 0) tx += hmp * (sizeof(VT) + 4u);
+        if (s1 > s0) tx += static_cast<uint32_t>(s1 - s0) * 128u + fe * (sizeof(VT) + 4u);
+        mbar_arrive_expect_tx(bar, tx);
+        if (nbulk > 0) bulk_g2s(S.xs + (wlo - wb), a.x + wlo, nbulk, bar);
+        bulk_g2s(S.hrp, a.hrp + static_cast<size_t>(t) * (a.T + 8), rpb, bar);
+        if (hm > 0) {
+            bulk_g2s(S.hval, a.hval + hb, hmp * sizeof(VT), bar);
+            bulk_g2s(S.hcol, a.hcol + hb, hmp * 2u, bar);
+            bulk_g2s(S.cperm, a.hcperm + hb, hmp * 2u, bar);
+        }
+        if (s1 > s0) {
+            bulk_g2s(S.fmeta, a.sl_meta + static_cast<size_t>(s0) * kSlice, static_cast<uint32_t>(s1 - s0) * 128u, bar);
+            bulk_g2s(S.fval, a.fval + e0, fe * sizeof(VT), bar);
+            bulk_g2s(S.fcol, a.fcol + e0, fe * 4u, bar);
+        }
+    } else {
+        const int c = item - a.ntiles;
+        const int beg = a.lcbeg[c], end = a.lcend[c];
+        const int abeg = beg & ~(kAlignFull - 1);
+        const uint32_t mp = static_cast<uint32_t>((end - abeg + kAlignFull - 1) / kAlignFull * kAlignFull);
+        mbar_arrive_expect_tx(bar, mp * (sizeof(VT) + 4u));
+        bulk_g2s(S.fval, a.lval + abeg, mp * sizeof(VT), bar);
+        bulk_g2s(S.fcol, a.lcol + abeg, mp * 4u, bar);
+    }
+}
+
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ void compute_tile(const SpmvArgs<VT, XT, AT> &a, int t, Stage<VT, XT> &S, AT *rowacc,
+                                             AT *q, uint16_t *cs, uint16_t *ce) {
     const int tid = threadIdx.x, P = blockDim.x;
-    const int t = blockIdx.x;
-    if (t >= a.ntiles) {
-        long_chunk<VT, XT, AT>(a, t - a.ntiles, smem);
+    const int lane = tid & 31, warp = tid >> 5, nwarps = P >> 5;
+    const int r0 = t * a.T, r1 = min(r0 + a.T, a.n), nr = r1 - r0;
+    const int wb = r0 - a.W, wlo = max(wb, 0);
+    const int nbulk_el = static_cast<int>(((static_cast<uint32_t>(r1 - wlo) * sizeof(XT)) & ~15u) / sizeof(XT));
+    const int hm = a.hcnt[t];
+    for (int g = wlo + nbulk_el + tid; g < r1; g += P) S.xs[g - wb] = a.x[g];
+
+    // 1. full pass (sliced ELL)
+    const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
+    const int e0 = __ldg(a.sl_ent + s0);
+    for (int s = warp; s < s1 - s0; s += nwarps) {
+        const uint32_t meta = S.fmeta[s * kSlice + lane];
+        const int rl = static_cast<int>(meta & 0xffffu), len = static_cast<int>(meta >> 16);
+        const int base = __ldg(a.sl_ent + s0 + s) - e0 + lane;
+        const AT fs = slice_row_sum<VT, XT, AT>(S.fval, S.fcol, base, rl == 0xffff ? 0 : len, a.x);
+        if (rl != 0xffff) rowacc[rl] = fs;
+    }
+    __syncthreads();
+
+    if (hm == 0) {
+        for (int r = tid; r < nr; r += P) {
+            const AT xr = static_cast<AT>(S.xs[r + a.W]);
+            a.y[r0 + r] = static_cast<XT>(((a.alpha * xr + AT(0)) + rowacc[r]) - AT(0));
+            rowacc[r] = AT(0);
+        }
         return;
     }
-    const SmemLayout L = smem_layout(a.T, a.W, a.M, P, sizeof(XT), sizeof(AT), 1);
-    XT *xs = reinterpret_cast<XT *>(smem + L.xs);
-    AT *rowacc = reinterpret_cast<AT *>(smem + L.rowacc);
-    AT *q = reinterpret_cast<AT *>(smem + L.q);
-    uint16_t *hcol_s = reinterpret_cast<uint16_t *>(smem + L.hcol);
-    uint16_t *cperm_s = reinterpret_cast<uint16_t *>(smem + L.cperm);
-    uint16_t *hrp_s = reinterpret_cast<uint16_t *>(smem + L.hrp);
-    int32_t *frp_s = reinterpret_cast<int32_t *>(smem + L.frp);
-    uint16_t *cs = reinterpret_cast<uint16_t *>(smem + L.cs);
-    uint16_t *ce = reinterpret_cast<uint16_t *>(smem + L.ce);
-    int *carry_row = reinterpret_cast<int *>(smem + L.carry_row);
-    AT *carry_val = reinterpret_cast<AT *>(smem + L.carry_val);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
 
-    const int r0 = t * a.T;
-    const int r1 = min(r0 + a.T, a.n);
-    const int nr = r1 - r0;
-    const int wb = r0 - a.W;          // window position p <-> global index wb + p
-    const int wlo = max(wb, 0);       // first staged global index
-    const int nx = r1 - wlo;
-    const uint32_t nbulk = (static_cast<uint32_t>(nx) * sizeof(XT)) & ~15u;
-
-    // 1. x window through the copy engine; the <16-byte tail with plain loads
-    if (tid == 0) {
-        mbar_init(mbar, 1);
-        fence_mbar_init();
+    // 2. half pass: alpha x_r + middle row sum (+ mirrored products) + full row
+    // sum.  A warp owns 32 consecutive rows; middle rows longer than
+    // kShortRow are summed by the whole warp, one after the other.
+    for (int rb = (tid & ~31); rb < nr; rb += P) {
+        const int r = rb + lane;
+        const bool valid = r < nr;
+        const AT xr = valid ? static_cast<AT>(S.xs[r + a.W]) : AT(0);
+        const int h0 = valid ? S.hrp[r] : 0, h1 = valid ? S.hrp[r + 1] : 0;
+        const bool hlong = (h1 - h0) > kShortRow;
+        AT hs = AT(0);
+        if (valid && !hlong) hs = half_row_thread<VT, XT, AT>(h0, h1, S.hval, S.hcol, q, S.xs, xr);
+        unsigned m = __ballot_sync(0xffffffffu, hlong);
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int f0 = __shfl_sync(0xffffffffu, h0, b), f1 = __shfl_sync(0xffffffffu, h1, b);
+            const AT xb = __shfl_sync(0xffffffffu, xr, b);
+            const AT s2 = half_row_warp<VT, XT, AT>(f0, f1, S.hval, S.hcol, q, S.xs, xb);
+            if (lane == b) hs = s2;
+        }
+        if (valid) rowacc[r] = (a.alpha * xr + hs) + rowacc[r];
     }
     __syncthreads();
-    if (tid == 0 && nbulk > 0) {
-        mbar_arrive_expect_tx(mbar, nbulk);
-        bulk_g2s(xs + (wlo - wb), a.x + wlo, nbulk, mbar);
-    }
-    for (int g = wlo + static_cast<int>(nbulk / sizeof(XT)) + tid; g < r1; g += P) xs[g - wb] = a.x[g];
-    // accumulators and tile metadata (overlaps the copy)
-    for (int r = tid; r < nr; r += P) rowacc[r] = AT(0);
-    const int tw = nr + a.W;
-    for (int p = tid; p < tw; p += P) {
-        cs[p] = 0;
-        ce[p] = 0;
-    }
-    const int hb = a.hoff[t];
-    const int hm = a.hcnt[t];
-    const uint16_t *hrp_g = a.hrp + static_cast<size_t>(t) * (a.T + 8);
-    for (int r = tid; r <= nr; r += P) hrp_s[r] = hrp_g[r];
-    const int f0 = a.frp[r0];
-    for (int r = tid; r <= nr; r += P) frp_s[r] = a.frp[r0 + r] - f0;
-    for (int k = tid; k < hm; k += P) cperm_s[k] = a.hcperm[hb + k];
-    if (nbulk > 0) mbar_wait_bounded(mbar, 0, a.err);
-    __syncthreads();
 
-    // 2. half pass: row sums and mirrored products of the middle entries
-    merge_rows<AT>(hm, nr, hrp_s,
-                   [&](int e, int r) -> AT {
-                       const AT v = Val<VT>::ld_stream(a.hval + hb + e);
-                       const uint16_t p = __ldcs(a.hcol + hb + e);
-                       hcol_s[e] = p;
-                       q[e] = v * static_cast<AT>(xs[r + a.W]);
-                       return v * static_cast<AT>(xs[p]);
-                   },
-                   rowacc, carry_row, carry_val);
-
-    // 3. full pass: outer rows, x from the window when it is there
-    const int fm = frp_s[nr];
-    const unsigned span = static_cast<unsigned>(r1 - wlo);
-    merge_rows<AT>(fm, nr, frp_s,
-                   [&](int e, int r) -> AT {
-                       const int c = __ldcs(a.fcol + f0 + e);
-                       const AT v = Val<VT>::ld_stream(a.fval + f0 + e);
-                       const unsigned off = static_cast<unsigned>(c - wlo);
-                       const AT xv = off < span ? static_cast<AT>(xs[c - wb]) : static_cast<AT>(__ldg(a.x + c));
-                       return v * xv;
-                   },
-                   rowacc, carry_row, carry_val);
-
-    // 4. mirrored sums per column: segment boundaries of the (col,row) list
+    // 3. mirrored sums per column: segment boundaries of the (column, row) list
     for (int k = tid; k < hm; k += P) {
-        const int key = hcol_s[cperm_s[k]];
-        if (k == 0 || hcol_s[cperm_s[k - 1]] != key) cs[key] = static_cast<uint16_t>(k);
-        if (k == hm - 1 || hcol_s[cperm_s[k + 1]] != key) ce[key] = static_cast<uint16_t>(k + 1);
+        const int key = S.hcol[S.cperm[k]];
+        if (k == 0 || S.hcol[S.cperm[k - 1]] != key) cs[key] = static_cast<uint16_t>(k);
+        if (k == hm - 1 || S.hcol[S.cperm[k + 1]] != key) ce[key] = static_cast<uint16_t>(k + 1);
     }
     __syncthreads();
     for (int r = tid; r < nr; r += P) {
         const int p = r + a.W;
         AT c = AT(0);
-        for (int k = cs[p]; k < ce[p]; ++k) c += q[cperm_s[k]];
-        a.y[r0 + r] = static_cast<XT>((a.alpha * static_cast<AT>(xs[p]) + rowacc[r]) - c);
+        for (int k = cs[p]; k < ce[p]; ++k) c += q[S.cperm[k]];
+        a.y[r0 + r] = static_cast<XT>(rowacc[r] - c);
+        rowacc[r] = AT(0);
+        cs[p] = 0;
+        ce[p] = 0;
     }
-    const int h0 = a.hhoff[t], h1 = a.hhoff[t + 1];
-    for (int h = h0 + tid; h < h1; h += P) {
+    const int g0 = a.hhoff[t], g1 = a.hhoff[t + 1];
+    for (int h = g0 + tid; h < g1; h += P) {
         const int p = a.hhrow[h] - wb;
         AT c = AT(0);
-        for (int k = cs[p]; k < ce[p]; ++k) c += q[cperm_s[k]];
+        for (int k = cs[p]; k < ce[p]; ++k) c += q[S.cperm[k]];
         a.halo[h] = -c;
+        cs[p] = 0;
+        ce[p] = 0;
     }
 }
 
-// y[row] += halo sum (each halo target once) and y[long row] += its chunk
+// Long-row chunk c: entries [lcbeg[c], lcend[c]) of the long list, staged
+// from the 16-entry boundary below; one warp per row touched, partial sum
+// into the row's slot.
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ void compute_long(const SpmvArgs<VT, XT, AT> &a, int c, Stage<VT, XT> &S) {
+    const int tid = threadIdx.x, P = blockDim.x;
+    const int beg = a.lcbeg[c], end = a.lcend[c];
+    const int shift = beg - (beg & ~(kAlignFull - 1));
+    const int l0 = a.lcfirst[c], nrc = a.lcrows[c];
+    uint16_t *flp = S.hrp;
+    for (int u = tid; u <= nrc; u += P) flp[u] = static_cast<uint16_t>(min(max(a.lrp[l0 + u], beg), end) - beg);
+    __syncthreads();
+    const int warp = tid >> 5, nw = P >> 5;
+    for (int u = warp; u < nrc; u += nw) {
+        const AT s = row_sum_warp<VT, XT, AT>(flp[u], flp[u + 1], S.fcol + shift, S.fval + shift, a.x);
+        if ((tid & 31) == 0) a.lpart[a.lcslot[c] + u] = s;
+    }
+}
+
+template <typename VT, typename XT, typename AT>
+__global__ void __launch_bounds__(kBlock, 1) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const SmemLayout L = smem_layout(a.T, a.W, a.Mh, a.S, a.F, sizeof(VT), sizeof(XT), sizeof(AT));
+    const int tid = threadIdx.x, P = blockDim.x;
+    AT *rowacc = reinterpret_cast<AT *>(smem + L.rowacc);
+    AT *q = reinterpret_cast<AT *>(sizeof(VT) == sizeof(AT) ? nullptr : smem + L.q);
+    uint16_t *cs = reinterpret_cast<uint16_t *>(smem + L.cs);
+    uint16_t *ce = reinterpret_cast<uint16_t *>(smem + L.ce);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.mbar);
+    const int nitems = a.ntiles + a.nchunks;
+    const int G = gridDim.x;
+    for (int r = tid; r < a.T; r += P) rowacc[r] = AT(0);
+    for (int p = tid; p < a.T + a.W; p += P) {
+        cs[p] = 0;
+        ce[p] = 0;
+    }
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        for (int k = 0; k < kStages; ++k) {
+            const int item = blockIdx.x + k * G;
+            if (item < nitems) {
+                Stage<VT, XT> S(smem + k * L.stage_bytes, L.st);
+                issue_item<VT, XT, AT>(a, item, S, &bars[k]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        const int item = blockIdx.x + k * G;
+        if (item >= nitems) break;
+        const int st = k & 1;
+        Stage<VT, XT> S(smem + st * L.stage_bytes, L.st);
+        mbar_wait_bounded(&bars[st], static_cast<uint32_t>((k >> 1) & 1), a.err);
+        if (item < a.ntiles) {
+            AT *qq = q ? q : reinterpret_cast<AT *>(S.hval);
+            compute_tile<VT, XT, AT>(a, item, S, rowacc, qq, cs, ce);
+        } else {
+            compute_long<VT, XT, AT>(a, item - a.ntiles, S);
+        }
+        __syncthreads();   // the stage and the scratch are free again
+        const int next = item + kStages * G;
+        if (tid == 0 && next < nitems) issue_item<VT, XT, AT>(a, next, S, &bars[st]);
+    }
+}
+
+// One thread per receiving row: y[row] += halo sum, then the row's long-row
 // partial sums in chunk order.
 template <typename XT, typename AT>
-__global__ void __launch_bounds__(256) fold_kernel(int nhalo, const int32_t *__restrict__ hhrow,
-                                                   const AT *__restrict__ halo, int nlong,
-                                                   const int32_t *__restrict__ lrow,
-                                                   const int32_t *__restrict__ lcptr,
+__global__ void __launch_bounds__(256) fold_kernel(int nitems, const int32_t *__restrict__ frow,
+                                                   const int32_t *__restrict__ fhalo,
+                                                   const int32_t *__restrict__ flong, const AT *__restrict__ halo,
+                                                   const int32_t *__restrict__ lc0, const int32_t *__restrict__ lc1,
+                                                   const int32_t *__restrict__ lcfirst,
+                                                   const int32_t *__restrict__ lcslot,
                                                    const AT *__restrict__ lpart, XT *__restrict__ y) {
-    const int total = nhalo + nlong;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        if (idx < nhalo) {
-            const int r = hhrow[idx];
-            y[r] = static_cast<XT>(static_cast<AT>(y[r]) + halo[idx]);
-        } else {
-            const int l = idx - nhalo;
-            AT s = AT(0);
-            for (int c = lcptr[l]; c < lcptr[l + 1]; ++c) s += lpart[c];
-            const int r = lrow[l];
-            y[r] = static_cast<XT>(static_cast<AT>(y[r]) + s);
-        }
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nitems; f += gridDim.x * blockDim.x) {
+        const int r = frow[f];
+        AT v = static_cast<AT>(y[r]);
+        const int hi = fhalo[f];
+        if (hi >= 0) v += halo[hi];
+        const int l = flong[f];
+        if (l >= 0)
+            for (int c = lc0[l]; c <= lc1[l]; ++c) v += lpart[lcslot[c] + (l - lcfirst[c])];
+        y[r] = static_cast<XT>(v);
     }
 }
 
@@ -209,6 +401,17 @@ __global__ void permute_kernel(int64_t n, int k, const int32_t *__restrict__ per
 
 // ------------------------------------------------------------ host side
 
+int sm_count() {
+    static std::atomic<int> cached{0};
+    int v = cached.load();
+    if (v > 0) return v;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+    cached.store(v);
+    return v;
+}
+
 template <typename VT, typename XT, typename AT>
 static int launch_typed(const pars3_handle *h, int dtype, double alpha, const void *x, void *y,
                         cudaStream_t st) {
@@ -219,7 +422,10 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     a.T = h->T;
     a.W = h->W;
     a.ntiles = h->ntiles;
-    a.M = L.max_tile_half;
+    a.nchunks = static_cast<int32_t>(L.lcbeg.size());
+    a.Mh = static_cast<int32_t>(round_up(L.max_tile_half, kAlignHalf));
+    a.S = L.max_tile_slices;
+    a.F = stage_full_entries(h);
     a.hoff = D.hoff;
     a.hcnt = D.hcnt;
     a.hrp = D.hrp;
@@ -229,11 +435,17 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     a.hhoff = D.hhoff;
     a.hhrow = D.hhrow;
     a.halo = static_cast<AT *>(D.halo);
-    a.frp = D.frp;
+    a.sl_off = D.sl_off;
+    a.sl_ent = D.sl_ent;
+    a.sl_meta = D.sl_meta;
     a.fcol = D.fcol;
     a.fval = static_cast<const VT *>(D.fval[dtype]);
+    a.lrp = D.lrp;
     a.lcbeg = D.lcbeg;
     a.lcend = D.lcend;
+    a.lcfirst = D.lcfirst;
+    a.lcrows = D.lcrows;
+    a.lcslot = D.lcslot;
     a.lcol = D.lcol;
     a.lval = static_cast<const VT *>(D.lval[dtype]);
     a.lpart = static_cast<AT *>(D.lpart);
@@ -243,21 +455,21 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     a.err = D.err;
     const int smem = smem_bytes_for(h, dtype);
     static std::atomic<int> configured{0};
-    if (configured.load() < smem) {
+    if (!configured.load()) {
         cudaError_t e = cudaFuncSetAttribute(tile_kernel<VT, XT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kSmemLimit);
         if (e != cudaSuccess) return cuda_status(e);
-        configured.store(kSmemLimit);
+        configured.store(1);
     }
-    const int nchunks = static_cast<int>(L.lcbeg.size());
-    const int grid = h->ntiles + nchunks;
+    const int nitems = h->ntiles + a.nchunks;
+    const int grid = std::min(nitems, sm_count());
     if (grid > 0) tile_kernel<VT, XT, AT><<<grid, kBlock, smem, st>>>(a);
-    const int nhalo = static_cast<int>(L.hhrow.size());
-    const int nlong = static_cast<int>(L.lrow.size());
-    if (nhalo + nlong > 0) {
-        const int blocks = static_cast<int>(std::min<int64_t>((nhalo + nlong + 255) / 256, 152 * 8));
-        fold_kernel<XT, AT><<<blocks, 256, 0, st>>>(nhalo, D.hhrow, static_cast<const AT *>(D.halo), nlong, D.lrow,
-                                                    D.lcptr, static_cast<const AT *>(D.lpart), static_cast<XT *>(y));
+    const int nf = static_cast<int>(L.fold_row.size());
+    if (nf > 0) {
+        const int blocks = static_cast<int>(std::min<int64_t>((nf + 255) / 256, 152 * 8));
+        fold_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, D.fold_row, D.fold_halo, D.fold_long,
+                                                    static_cast<const AT *>(D.halo), D.lc0, D.lc1, D.lcfirst, D.lcslot,
+                                                    static_cast<const AT *>(D.lpart), static_cast<XT *>(y));
     }
     return cuda_status(cudaGetLastError());
 }

@@ -108,9 +108,9 @@ def test_default_cut_rule_matches_oracle():
     perm, _, bw = P.pars3_reorder(A.n, A.rowptr, A.col)
     h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm)
     info = P.pars3_info_get(h)
-    assert (info["T"], info["W"]) == O.auto_cut(bw, 32, 4096, 1024)
+    assert (info["T"], info["W"]) == O.auto_cut(bw, 32, 1024, 1024)
     h32 = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, dtypes=P.dtype_bit(P.F32))
-    assert (P.pars3_info_get(h32)["T"], P.pars3_info_get(h32)["W"]) == O.auto_cut(bw, 32, 8192, 1024)
+    assert (P.pars3_info_get(h32)["T"], P.pars3_info_get(h32)["W"]) == O.auto_cut(bw, 32, 2048, 1024)
 
 
 def test_layout_routes_long_rows_and_full_tiles():
@@ -118,7 +118,19 @@ def test_layout_routes_long_rows_and_full_tiles():
     perm, _, _ = P.pars3_reorder(A.n, A.rowptr, A.col)
     h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=256, W=256, long_row=64)
     info = P.pars3_info_get(h)
-    assert info["long_rows"] > 0 and info["long_chunks"] >= info["long_rows"]
+    assert info["long_rows"] > 0 and info["long_chunks"] >= 1
+    assert info["half_entries"] + (info["full_entries"] + info["long_entries"]) // 2 == A.nnz
+    assert P.pars3_layout_check(h) == 0
+
+
+def test_overfull_tile_leaves_the_half_path():
+    """A tile whose middle entries do not fit in shared memory is stored in
+    full (both triangles) instead; the layout still reconstructs the split."""
+    A = W.banded_skew(4096, 1024, 0.05, 11)
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, T=1024, W=1024)
+    info = P.pars3_info_get(h)
+    assert info["half_entries"] < A.nnz
+    assert info["full_entries"] + info["long_entries"] > 0
     assert info["half_entries"] + (info["full_entries"] + info["long_entries"]) // 2 == A.nnz
     assert P.pars3_layout_check(h) == 0
 

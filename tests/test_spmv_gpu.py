@@ -99,13 +99,6 @@ def test_spmv_parity(name, gen, kw, dtype):
         check(A, h, perm, dtype, alpha, x)
 
 
-def test_overfull_tile_is_routed_to_full_path():
-    A = W.banded_skew(4096, 1024, 0.05, 11)
-    h, _ = make(A, T=1024, Wc=1024)
-    info = P.pars3_info_get(h)
-    assert info["full_entries"] > 0 and info["half_entries"] < A.nnz
-
-
 def test_bitwise_determinism():
     A = W.rmat(13, 60000, seed=10)
     h, perm = make(A, T=256, Wc=256, long_row=64)
