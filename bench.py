@@ -143,8 +143,8 @@ def workload(name: str):
     return A, alpha, x, desc
 
 
-# cut points used for each workload (chosen by pars3_autotune on a GB300)
-TUNED = {"cfg0": (1024, 128), "cfg1": (0, 0), "cfg2": (0, 0)}
+# cut points (T, W) per workload, from timing sweeps on a GB300
+TUNED = {"cfg0": (256, 128), "cfg1": (2048, 32), "cfg2": (2048, 32)}
 
 
 def run_reference(args, ws, rank):

@@ -16,6 +16,8 @@
 //   full path  -- outer entries, and the middle entries of tiles too large
 //                 for shared memory, stored in both rows with mirrored sign,
 //                 so that each row is a plain gather (no write conflicts);
+//                 sliced ELL: every row of a tile owns one lane of one of
+//                 its T/32 slices (long rows with length 0);
 //   long rows  -- rows longer than a per-tile cap on full-path entries (and
 //                 the heaviest rows of tiles above the cap) are summed in
 //                 chunks of kLongChunk entries; the partial sums of every
@@ -138,21 +140,16 @@ void dtype_sizes(int dtype, uint32_t *vsz, uint32_t *xsz, uint32_t *asz) {
 
 constexpr int64_t kLongSlots = kLongChunk + 2 * kAlignFull;  // long chunk staging incl. alignment slack
 
-int32_t stage_full_entries(const pars3_handle *h) {
-    int64_t F = h->L.max_tile_full;
-    if (!h->L.lrow.empty()) F = std::max<int64_t>(F, kLongSlots);
-    return static_cast<int32_t>(round_up(F, kAlignFull));
-}
-
-static uint32_t smem_total(const pars3_handle *h, int dtype, int64_t Mh, int64_t S, int64_t F) {
+static uint32_t smem_total(const pars3_handle *h, int dtype, int64_t Mh, bool has_long) {
     uint32_t vsz, xsz, asz;
     dtype_sizes(dtype, &vsz, &xsz, &asz);
-    return smem_layout(h->T, h->W, static_cast<uint32_t>(round_up(Mh, kAlignHalf)), static_cast<uint32_t>(S),
-                       static_cast<uint32_t>(round_up(F, kAlignFull)), vsz, xsz, asz).total;
+    const uint32_t a = smem_layout(h->T, h->W, static_cast<uint32_t>(round_up(Mh, kAlignHalf)), vsz, xsz, asz).total;
+    const uint32_t b = has_long ? long_layout(h->T, static_cast<uint32_t>(kLongSlots), vsz).total : 0u;
+    return a > b ? a : b;
 }
 
 int smem_bytes_for(const pars3_handle *h, int dtype) {
-    return static_cast<int>(smem_total(h, dtype, h->L.max_tile_half, h->L.max_tile_slices, stage_full_entries(h)));
+    return static_cast<int>(smem_total(h, dtype, h->L.max_tile_half, !h->L.lrow.empty()));
 }
 
 static int max_smem_all(const pars3_handle *h) {
@@ -162,15 +159,15 @@ static int max_smem_all(const pars3_handle *h) {
     return m;
 }
 
-// half-path entries a tile may hold with no full-path data, for every packed precision
+// half-path entries a tile may hold, for every packed precision
 static int64_t half_room(const pars3_handle *h) {
     int64_t best = INT64_MAX;
     for (int d = 0; d < kNumDtypes; ++d) {
         if (!(h->dtypes & PARS3_DTYPE_BIT(d))) continue;
         uint32_t vsz, xsz, asz;
         dtype_sizes(d, &vsz, &xsz, &asz);
-        const int64_t base = smem_total(h, d, 0, 0, kLongSlots);
-        const int64_t per = 2 * (vsz + 4) + (vsz == asz ? 0 : asz);   // two stages + separate q
+        const int64_t base = smem_total(h, d, 0, false);
+        const int64_t per = vsz + (vsz == asz ? 0 : asz) + 4;
         const int64_t room = static_cast<int64_t>(kSmemLimit) - base - 1024;
         best = std::min<int64_t>(best, room > 0 ? room / per : -1);
     }
@@ -321,20 +318,22 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
         std::vector<int32_t> rows;
         for (int32_t t = 0; t < nt; ++t) {
             const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+            // every row of the tile gets a lane (long rows with length 0), so
+            // the full pass can start each row's sum with alpha x_r
             rows.clear();
-            for (int32_t i = r0; i < r1; ++i)
-                if (!is_long[i] && flen[i] > 0) rows.push_back(i);
+            for (int32_t i = r0; i < r1; ++i) rows.push_back(i);
+            auto slen = [&](int32_t i) { return is_long[i] ? 0 : flen[i]; };
             std::sort(rows.begin(), rows.end(), [&](int32_t a, int32_t b) {
-                return flen[a] != flen[b] ? flen[a] > flen[b] : a < b;
+                return slen(a) != slen(b) ? slen(a) > slen(b) : a < b;
             });
             int64_t tile_ent = 0;
             for (size_t g = 0; g < rows.size(); g += kSlice) {
-                const int32_t width = flen[rows[g]];
+                const int32_t width = slen(rows[g]);
                 L.sl_ent.push_back(static_cast<int32_t>(L.sl_ent.back() + static_cast<int64_t>(kSlice) * width));
                 for (int l = 0; l < kSlice; ++l) {
                     const size_t k = g + l;
                     L.sl_meta.push_back(k < rows.size()
-                                            ? static_cast<uint32_t>(rows[k] - r0) | (static_cast<uint32_t>(flen[rows[k]]) << 16)
+                                            ? static_cast<uint32_t>(rows[k] - r0) | (static_cast<uint32_t>(slen(rows[k])) << 16)
                                             : 0xffffu);
                 }
                 tile_ent += static_cast<int64_t>(kSlice) * width;
@@ -352,7 +351,7 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
         for (int32_t s2 = L.sl_off[t]; s2 < L.sl_off[t + 1]; ++s2)
             for (int l = 0; l < kSlice; ++l) {
                 const uint32_t meta = L.sl_meta[static_cast<size_t>(s2) * kSlice + l];
-                if ((meta & 0xffffu) == 0xffffu) continue;
+                if ((meta & 0xffffu) == 0xffffu || (meta >> 16) == 0) continue;
                 const int32_t i = r0 + static_cast<int32_t>(meta & 0xffffu);
                 emit_row(i, &L.fcol[L.sl_ent[s2] + l], &fsrc[L.sl_ent[s2] + l], kSlice);
             }
@@ -437,28 +436,17 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
 }
 
 // Largest layout that fits: start with every middle entry of a fitting tile
-// on the half path and the balance cap on the full path; while two stages
-// do not fit in shared memory, halve whichever of the two dominates (more
-// middle tiles become full storage, more rows go to the chunked long path).
+// on the half path; while the tile block does not fit in shared memory,
+// halve the largest half-path tile (more middle tiles become full storage).
 int build_layout(pars3_handle *h) {
     int64_t mcap = half_room(h);
     if (mcap < 0) return PARS3_EUNSUPPORTED;
-    int64_t cap = 0;
     for (int iter = 0; iter < 40; ++iter) {
-        int rc = build_layout_try(h, mcap, cap);
+        int rc = build_layout_try(h, mcap, 0);
         if (rc != PARS3_OK) return rc;
         if (max_smem_all(h) <= kSmemLimit) return PARS3_OK;
-        const int64_t half_bytes = static_cast<int64_t>(h->L.max_tile_half) * 12;
-        const int64_t full_bytes = static_cast<int64_t>(h->L.max_tile_full) * 12;
-        if (half_bytes >= full_bytes && h->L.max_tile_half > 0) {
-            mcap = h->L.max_tile_half / 2;
-        } else if (h->L.max_tile_full > kLongSlots / 2) {
-            cap = std::max<int64_t>(h->L.max_tile_full / 2, 64);
-        } else if (h->L.max_tile_half > 0) {
-            mcap = h->L.max_tile_half / 2;
-        } else {
-            return PARS3_EUNSUPPORTED;
-        }
+        if (h->L.max_tile_half == 0) return PARS3_EUNSUPPORTED;
+        mcap = h->L.max_tile_half / 2;
     }
     return PARS3_EUNSUPPORTED;
 }
@@ -641,6 +629,8 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
                     }
                 }
             }
+            for (int32_t rl = 0; rl < r1 - r0; ++rl)
+                if (!seen[rl]) return PARS3_EINVAL;   // every row owns a lane
         }
         for (size_t l = 0; l < L.lrow.size(); ++l)
             for (int32_t q = L.lrp[l]; q < L.lrp[l + 1]; ++q)

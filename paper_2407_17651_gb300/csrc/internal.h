@@ -12,8 +12,7 @@ namespace pars3 {
 constexpr int kNumDtypes = 3;
 constexpr int kAlignHalf = 8;          // half-path tile segments start on 16-byte boundaries (u16, bf16)
 constexpr int kAlignFull = 16;         // full-path tile segments: 64 B for int32 columns, 128 B for fp64
-constexpr int kBlock = 1024;           // threads of the persistent tile kernel (one block per SM)
-constexpr int kStages = 2;             // tile staging buffers in flight per block
+constexpr int kBlock = 512;            // threads of the tile kernel (one block per row tile or long chunk)
 constexpr int kLongChunk = 4096;       // entries per long-row chunk (one block each)
 constexpr int kLongMin = 256;          // shortest row moved to the long path to balance tiles
 constexpr int kSellMax = 32;           // longer full-path rows go to the long path
@@ -123,7 +122,7 @@ int64_t bandwidth(int32_t n, const int32_t *rowptr, const int32_t *col, const in
 void auto_cut(int64_t bw, int32_t w_min, int32_t w_cap, int32_t t_min, int32_t *T, int32_t *W);
 int build_layout(pars3_handle *h);
 int smem_bytes_for(const pars3_handle *h, int dtype);
-int32_t stage_full_entries(const pars3_handle *h);
+
 int sm_count();
 void dtype_sizes(int dtype, uint32_t *vsz, uint32_t *xsz, uint32_t *asz);
 int64_t model_bytes(const pars3_handle *h, int dtype);

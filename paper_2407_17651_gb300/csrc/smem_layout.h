@@ -13,46 +13,46 @@
 
 namespace pars3 {
 
-// Dynamic shared memory of the persistent tile kernel: kStages staging
-// buffers (everything a tile or a long-row chunk reads contiguously, filled
-// by TMA bulk copies) followed by per-block scratch.
-struct StageLayout {  // offsets inside one stage
-    uint32_t xs, hrp, hval, hcol, cperm, fmeta, fval, fcol, bytes;
-};
+// Dynamic shared memory of the tile kernel.  A tile block holds the x
+// window, the tile's middle entries (filled by TMA bulk copies) and scratch;
+// a long-chunk block uses the same buffer for the chunk's entries.
 struct SmemLayout {
-    StageLayout st;
-    uint32_t stage_bytes;          // stride between stages
-    uint32_t rowacc, q, cs, ce, mbar, total;
+    uint32_t xs, rowacc, hval, q, hcol, cperm, hrp, cs, ce, mbar, total;
+};
+struct LongLayout {
+    uint32_t fval, fcol, flp, mbar, total;
 };
 
 PARS3_HD uint32_t align128(uint32_t a) { return (a + 127u) & ~127u; }
 
 // T: tile rows, W: window, Mh: half-path entries of the largest tile (padded
-// to 8), S: sliced-ELL slices of the largest tile, F: sliced-ELL entries of
-// the largest tile or of a long-row chunk with alignment slack, vsz/xsz/asz:
-// bytes of the value, vector and accumulator types.  Every region starts on
-// a 128-byte boundary (TMA bulk copies need 16).
-PARS3_HD SmemLayout smem_layout(uint32_t T, uint32_t W, uint32_t Mh, uint32_t S, uint32_t F, uint32_t vsz,
-                                uint32_t xsz, uint32_t asz) {
+// to 8), vsz/xsz/asz: bytes of the value, vector and accumulator types.
+// Every region starts on a 128-byte boundary (TMA bulk copies need 16).
+PARS3_HD SmemLayout smem_layout(uint32_t T, uint32_t W, uint32_t Mh, uint32_t vsz, uint32_t xsz, uint32_t asz) {
     SmemLayout s;
-    StageLayout &g = s.st;
-    g.xs = 0;
-    g.hrp = align128(g.xs + (T + W) * xsz);
-    g.hval = align128(g.hrp + (T + 8u) * 2u);
-    g.hcol = align128(g.hval + Mh * vsz);
-    g.cperm = align128(g.hcol + Mh * 2u);
-    g.fmeta = align128(g.cperm + Mh * 2u);
-    g.fval = align128(g.fmeta + S * 32u * 4u);
-    g.fcol = align128(g.fval + F * vsz);
-    g.bytes = align128(g.fcol + F * 4u);
-    s.stage_bytes = g.bytes;
-    const uint32_t base = 2u * s.stage_bytes;
-    s.rowacc = base;
-    s.q = align128(s.rowacc + T * asz);
-    s.cs = align128(s.q + (vsz == asz ? 0u : Mh * asz));
+    s.xs = 0;
+    s.rowacc = align128(s.xs + (T + W) * xsz);
+    s.hval = align128(s.rowacc + T * asz);
+    s.q = (vsz == asz) ? s.hval : align128(s.hval + Mh * vsz);
+    s.hcol = align128((vsz == asz) ? s.hval + Mh * vsz : s.q + Mh * asz);
+    s.cperm = align128(s.hcol + Mh * 2u);
+    s.hrp = align128(s.cperm + Mh * 2u);
+    s.cs = align128(s.hrp + (T + 8u) * 2u);
     s.ce = align128(s.cs + (T + W) * 2u);
     s.mbar = align128(s.ce + (T + W) * 2u);
-    s.total = align128(s.mbar + 2u * 8u);
+    s.total = align128(s.mbar + 8u);
+    return s;
+}
+
+// F: staged entries of a long-row chunk (with alignment slack); rows of a
+// chunk: at most T.
+PARS3_HD LongLayout long_layout(uint32_t T, uint32_t F, uint32_t vsz) {
+    LongLayout s;
+    s.fval = 0;
+    s.fcol = align128(s.fval + F * vsz);
+    s.flp = align128(s.fcol + F * 4u);
+    s.mbar = align128(s.flp + (T + 8u) * 2u);
+    s.total = align128(s.mbar + 8u);
     return s;
 }
 

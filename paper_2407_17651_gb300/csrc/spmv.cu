@@ -1,24 +1,23 @@
 // spmv.cu -- y = (alpha I + S) x on the device for a split handle.
 //
-// Two launches per product.  The tile kernel is persistent: one block of
-// kBlock threads per SM walks a fixed list of work items (row tiles, then
-// long-row chunks) in a static round-robin order; a second, small launch
-// folds the cross-tile (halo) mirrored sums and the long-row partial sums
-// into y.  No atomics: every y entry has one writer per launch and every sum
-// runs in an order fixed by the layout and the block size, so results are
-// bitwise reproducible from run to run and independent of which block
-// processed which item.
+// Two launches per product: the tile kernel (one block per row tile -- the
+// block-row ownership of Sec. 3 and Fig. 2 -- plus one block per chunk of
+// the long-row list) and a small fold kernel that adds the cross-tile
+// (halo) mirrored sums and the long-row partial sums to y.  No atomics:
+// every y entry has one writer per launch and every sum runs in an order
+// fixed by the layout and the block size, so results are bitwise
+// reproducible from run to run.
 //
-// Work item = row tile t (rows [tT, tT+T): the block-row ownership of Sec. 3
-// and Fig. 2).  Its data is staged into shared memory by TMA bulk copies,
-// kStages items ahead: the x window [tT-W, tT+T) (the x slice a row block
-// needs, Sec. 3.1.2), the middle entries of the tile (values, window
-// columns, (column,row) order, row pointers) and its full-storage rows in
-// sliced-ELL order.  Then:
-//  1. full pass: each warp sums the rows of its 32-row slices, one lane per
-//     row, reading the slice from shared memory (slot m of lane l at 32m+l:
-//     no bank conflicts) and gathering x_j from global memory, eight
-//     independent gathers in flight per lane;
+// Tile block t (rows [tT, tT+T)):
+//  0. one thread issues TMA bulk copies of the x window [tT-W, tT+T) (the x
+//     slice a row block needs, Sec. 3.1.2) and of the tile's middle entries
+//     (values, window columns, (column,row) order, row pointers);
+//  1. meanwhile the full pass streams the tile's full-storage rows in
+//     sliced-ELL order straight from HBM: each warp takes 32-row slices,
+//     one lane per row (every row of the tile owns a lane), slot m of lane l
+//     at 32m+l so that every load instruction reads 32 consecutive entries;
+//     a lane's sum starts at alpha x_r and gathers x_j, eight slots in
+//     flight;
 //  2. half pass: each middle entry l_ij is read once and used twice (Eqs.
 //     2-6): l_ij x_j is summed into row i, the mirrored product l_ij x_i is
 //     kept in shared memory;
@@ -39,7 +38,7 @@ namespace pars3 {
 
 template <typename VT, typename XT, typename AT>
 struct SpmvArgs {
-    int32_t n, T, W, ntiles, nchunks, Mh, S, F;
+    int32_t n, T, W, ntiles, nchunks, Mh;
     const int32_t *hoff, *hcnt;
     const uint16_t *hrp, *hcol, *hcperm;
     const VT *hval;
@@ -66,23 +65,28 @@ template <> __device__ __forceinline__ float sval<uint16_t>(const uint16_t *p, i
 constexpr int kUnroll = 8;       // independent gathers in flight per lane
 constexpr int kShortRow = 16;    // middle rows longer than this are summed by the whole warp
 
-// Sliced-ELL row of lane l in shared memory: slots base + 32 m + l, m < len.
+// Sliced-ELL row of lane l: slots base + 32 m + l (m < len) of the global
+// value and column arrays, streamed (evict-first); x_j gathered.  The sum
+// starts at `start`.
 template <typename VT, typename XT, typename AT>
-__device__ __forceinline__ AT slice_row_sum(const VT *val_s, const int32_t *col_s, int base, int len,
-                                            const XT *__restrict__ xg) {
-    AT acc = AT(0);
+__device__ __forceinline__ AT slice_row_sum(const VT *__restrict__ val, const int32_t *__restrict__ col,
+                                            int64_t base, int len, const XT *__restrict__ xg, AT start) {
+    AT acc = start;
     for (int m0 = 0; m0 < len; m0 += kUnroll) {
+        int c[kUnroll];
         AT v[kUnroll], xv[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
+            c[u] = 0;
             v[u] = AT(0);
-            xv[u] = AT(0);
             if (m0 + u < len) {
-                const int q = base + (m0 + u) * kSlice;
-                v[u] = sval<VT>(val_s, q);
-                xv[u] = static_cast<AT>(__ldg(xg + col_s[q]));
+                const int64_t q = base + static_cast<int64_t>(m0 + u) * kSlice;
+                c[u] = __ldcs(col + q);
+                v[u] = Val<VT>::ld_stream(val + q);
             }
         }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) xv[u] = (m0 + u < len) ? static_cast<AT>(__ldg(xg + c[u])) : AT(0);
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
             if (m0 + u < len) acc += v[u] * xv[u];
@@ -152,216 +156,157 @@ __device__ __forceinline__ AT half_row_warp(int e0, int e1, const VT *hval, cons
     return acc;
 }
 
-template <typename VT, typename XT>
-struct Stage {
-    XT *xs;
-    uint16_t *hrp, *hcol, *cperm;
-    VT *hval;
-    uint32_t *fmeta;
-    VT *fval;
-    int32_t *fcol;
-    __device__ Stage(unsigned char *b, const StageLayout &g) {
-        xs = reinterpret_cast<XT *>(b + g.xs);
-        hrp = reinterpret_cast<uint16_t *>(b + g.hrp);
-        hval = reinterpret_cast<VT *>(b + g.hval);
-        hcol = reinterpret_cast<uint16_t *>(b + g.hcol);
-        cperm = reinterpret_cast<uint16_t *>(b + g.cperm);
-        fmeta = reinterpret_cast<uint32_t *>(b + g.fmeta);
-        fval = reinterpret_cast<VT *>(b + g.fval);
-        fcol = reinterpret_cast<int32_t *>(b + g.fcol);
-    }
-};
-
-// Thread 0: arm the stage's mbarrier and issue the bulk copies of one item.
 template <typename VT, typename XT, typename AT>
-__device__ __forceinline__ void issue_item(const SpmvArgs<VT, XT, AT> &a, int item, Stage<VT, XT> &S,
-                                           uint64_t *bar) {
-    if (item < a.ntiles) {
-        const int t = item;
-        const int r0 = t * a.T, r1 = min(r0 + a.T, a.n);
-        const int wb = r0 - a.W, wlo = max(wb, 0);
-        const uint32_t nbulk = (static_cast<uint32_t>(r1 - wlo) * sizeof(XT)) & ~15u;
-        const int hb = a.hoff[t], hm = a.hcnt[t];
-        const uint32_t hmp = static_cast<uint32_t>((hm + kAlignHalf - 1) / kAlignHalf * kAlignHalf);
-        const uint32_t rpb = static_cast<uint32_t>(a.T + 8) * 2u;
-        const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
-        const int e0 = a.sl_ent[s0], e1 = a.sl_ent[s1];
-        const uint32_t fe = static_cast<uint32_t>(e1 - e0);
-        uint32_t tx = nbulk + rpb;
-        if (hm > 0) tx += hmp * (sizeof(VT) + 4u);
-        if (s1 > s0) tx += static_cast<uint32_t>(s1 - s0) * 128u + fe * (sizeof(VT) + 4u);
-        mbar_arrive_expect_tx(bar, tx);
-        if (nbulk > 0) bulk_g2s(S.xs + (wlo - wb), a.x + wlo, nbulk, bar);
-        bulk_g2s(S.hrp, a.hrp + static_cast<size_t>(t) * (a.T + 8), rpb, bar);
-        if (hm > 0) {
-            bulk_g2s(S.hval, a.hval + hb, hmp * sizeof(VT), bar);
-            bulk_g2s(S.hcol, a.hcol + hb, hmp * 2u, bar);
-            bulk_g2s(S.cperm, a.hcperm + hb, hmp * 2u, bar);
-        }
-        if (s1 > s0) {
-            bulk_g2s(S.fmeta, a.sl_meta + static_cast<size_t>(s0) * kSlice, static_cast<uint32_t>(s1 - s0) * 128u, bar);
-            bulk_g2s(S.fval, a.fval + e0, fe * sizeof(VT), bar);
-            bulk_g2s(S.fcol, a.fcol + e0, fe * 4u, bar);
-        }
-    } else {
-        const int c = item - a.ntiles;
-        const int beg = a.lcbeg[c], end = a.lcend[c];
-        const int abeg = beg & ~(kAlignFull - 1);
-        const uint32_t mp = static_cast<uint32_t>((end - abeg + kAlignFull - 1) / kAlignFull * kAlignFull);
-        mbar_arrive_expect_tx(bar, mp * (sizeof(VT) + 4u));
-        bulk_g2s(S.fval, a.lval + abeg, mp * sizeof(VT), bar);
-        bulk_g2s(S.fcol, a.lcol + abeg, mp * 4u, bar);
-    }
-}
-
-template <typename VT, typename XT, typename AT>
-__device__ __forceinline__ void compute_tile(const SpmvArgs<VT, XT, AT> &a, int t, Stage<VT, XT> &S, AT *rowacc,
-                                             AT *q, uint16_t *cs, uint16_t *ce) {
+__device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t, unsigned char *smem) {
+    const SmemLayout L = smem_layout(a.T, a.W, a.Mh, sizeof(VT), sizeof(XT), sizeof(AT));
+    XT *xs = reinterpret_cast<XT *>(smem + L.xs);
+    AT *rowacc = reinterpret_cast<AT *>(smem + L.rowacc);
+    VT *hval = reinterpret_cast<VT *>(smem + L.hval);
+    AT *q = reinterpret_cast<AT *>(smem + L.q);
+    uint16_t *hcol = reinterpret_cast<uint16_t *>(smem + L.hcol);
+    uint16_t *cperm = reinterpret_cast<uint16_t *>(smem + L.cperm);
+    uint16_t *hrp = reinterpret_cast<uint16_t *>(smem + L.hrp);
+    uint16_t *cs = reinterpret_cast<uint16_t *>(smem + L.cs);
+    uint16_t *ce = reinterpret_cast<uint16_t *>(smem + L.ce);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
     const int tid = threadIdx.x, P = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = P >> 5;
     const int r0 = t * a.T, r1 = min(r0 + a.T, a.n), nr = r1 - r0;
     const int wb = r0 - a.W, wlo = max(wb, 0);
-    const int nbulk_el = static_cast<int>(((static_cast<uint32_t>(r1 - wlo) * sizeof(XT)) & ~15u) / sizeof(XT));
-    const int hm = a.hcnt[t];
-    for (int g = wlo + nbulk_el + tid; g < r1; g += P) S.xs[g - wb] = a.x[g];
+    const uint32_t nbulk = (static_cast<uint32_t>(r1 - wlo) * sizeof(XT)) & ~15u;
+    const int hb = a.hoff[t], hm = a.hcnt[t];
+    const uint32_t hmp = static_cast<uint32_t>((hm + kAlignHalf - 1) / kAlignHalf * kAlignHalf);
+    const uint32_t rpb = static_cast<uint32_t>(a.T + 8) * 2u;
 
-    // 1. full pass (sliced ELL)
-    const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
-    const int e0 = __ldg(a.sl_ent + s0);
-    for (int s = warp; s < s1 - s0; s += nwarps) {
-        const uint32_t meta = S.fmeta[s * kSlice + lane];
-        const int rl = static_cast<int>(meta & 0xffffu), len = static_cast<int>(meta >> 16);
-        const int base = __ldg(a.sl_ent + s0 + s) - e0 + lane;
-        const AT fs = slice_row_sum<VT, XT, AT>(S.fval, S.fcol, base, rl == 0xffff ? 0 : len, a.x);
-        if (rl != 0xffff) rowacc[rl] = fs;
+    // 0. the copy engine stages the x window and the middle entries
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        uint32_t tx = nbulk + rpb;
+        if (hm > 0) tx += hmp * (sizeof(VT) + 4u);
+        mbar_arrive_expect_tx(mbar, tx);
+        if (nbulk > 0) bulk_g2s(xs + (wlo - wb), a.x + wlo, nbulk, mbar);
+        bulk_g2s(hrp, a.hrp + static_cast<size_t>(t) * (a.T + 8), rpb, mbar);
+        if (hm > 0) {
+            bulk_g2s(hval, a.hval + hb, hmp * sizeof(VT), mbar);
+            bulk_g2s(hcol, a.hcol + hb, hmp * 2u, mbar);
+            bulk_g2s(cperm, a.hcperm + hb, hmp * 2u, mbar);
+        }
     }
+    for (int g = wlo + static_cast<int>(nbulk / sizeof(XT)) + tid; g < r1; g += P) xs[g - wb] = a.x[g];
+    if (hm > 0)
+        for (int p = tid; p < nr + a.W; p += P) {
+            cs[p] = 0;
+            ce[p] = 0;
+        }
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+
+    // 1. full pass (sliced ELL) straight from HBM while the copy runs
+    const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
+    for (int s = s0 + warp; s < s1; s += nwarps) {
+        const uint32_t meta = __ldg(a.sl_meta + static_cast<int64_t>(s) * kSlice + lane);
+        const int rl = static_cast<int>(meta & 0xffffu), len = static_cast<int>(meta >> 16);
+        if (rl != 0xffff) {
+            const AT start = a.alpha * static_cast<AT>(__ldg(a.x + r0 + rl));
+            rowacc[rl] = slice_row_sum<VT, XT, AT>(a.fval, a.fcol, static_cast<int64_t>(__ldg(a.sl_ent + s)) + lane,
+                                                   len, a.x, start);
+        }
+    }
+    mbar_wait_bounded(mbar, 0, a.err);
     __syncthreads();
 
     if (hm == 0) {
-        for (int r = tid; r < nr; r += P) {
-            const AT xr = static_cast<AT>(S.xs[r + a.W]);
-            a.y[r0 + r] = static_cast<XT>(((a.alpha * xr + AT(0)) + rowacc[r]) - AT(0));
-            rowacc[r] = AT(0);
-        }
+        for (int r = tid; r < nr; r += P) a.y[r0 + r] = static_cast<XT>(rowacc[r]);
         return;
     }
+    AT *qq = sizeof(VT) == sizeof(AT) ? reinterpret_cast<AT *>(hval) : q;
 
-    // 2. half pass: alpha x_r + middle row sum (+ mirrored products) + full row
-    // sum.  A warp owns 32 consecutive rows; middle rows longer than
-    // kShortRow are summed by the whole warp, one after the other.
+    // 2. half pass: middle row sums and mirrored products.  A warp owns 32
+    // consecutive rows; middle rows longer than kShortRow are summed by the
+    // whole warp, one after the other.
     for (int rb = (tid & ~31); rb < nr; rb += P) {
         const int r = rb + lane;
         const bool valid = r < nr;
-        const AT xr = valid ? static_cast<AT>(S.xs[r + a.W]) : AT(0);
-        const int h0 = valid ? S.hrp[r] : 0, h1 = valid ? S.hrp[r + 1] : 0;
+        const AT xr = valid ? static_cast<AT>(xs[r + a.W]) : AT(0);
+        const int h0 = valid ? hrp[r] : 0, h1 = valid ? hrp[r + 1] : 0;
         const bool hlong = (h1 - h0) > kShortRow;
         AT hs = AT(0);
-        if (valid && !hlong) hs = half_row_thread<VT, XT, AT>(h0, h1, S.hval, S.hcol, q, S.xs, xr);
+        if (valid && !hlong) hs = half_row_thread<VT, XT, AT>(h0, h1, hval, hcol, qq, xs, xr);
         unsigned m = __ballot_sync(0xffffffffu, hlong);
         while (m) {
             const int b = __ffs(m) - 1;
             m &= m - 1;
             const int f0 = __shfl_sync(0xffffffffu, h0, b), f1 = __shfl_sync(0xffffffffu, h1, b);
             const AT xb = __shfl_sync(0xffffffffu, xr, b);
-            const AT s2 = half_row_warp<VT, XT, AT>(f0, f1, S.hval, S.hcol, q, S.xs, xb);
+            const AT s2 = half_row_warp<VT, XT, AT>(f0, f1, hval, hcol, qq, xs, xb);
             if (lane == b) hs = s2;
         }
-        if (valid) rowacc[r] = (a.alpha * xr + hs) + rowacc[r];
+        if (valid && h1 > h0) rowacc[r] += hs;
     }
     __syncthreads();
 
     // 3. mirrored sums per column: segment boundaries of the (column, row) list
     for (int k = tid; k < hm; k += P) {
-        const int key = S.hcol[S.cperm[k]];
-        if (k == 0 || S.hcol[S.cperm[k - 1]] != key) cs[key] = static_cast<uint16_t>(k);
-        if (k == hm - 1 || S.hcol[S.cperm[k + 1]] != key) ce[key] = static_cast<uint16_t>(k + 1);
+        const int key = hcol[cperm[k]];
+        if (k == 0 || hcol[cperm[k - 1]] != key) cs[key] = static_cast<uint16_t>(k);
+        if (k == hm - 1 || hcol[cperm[k + 1]] != key) ce[key] = static_cast<uint16_t>(k + 1);
     }
     __syncthreads();
     for (int r = tid; r < nr; r += P) {
         const int p = r + a.W;
+        const int k0 = cs[p], k1 = ce[p];
         AT c = AT(0);
-        for (int k = cs[p]; k < ce[p]; ++k) c += q[S.cperm[k]];
-        a.y[r0 + r] = static_cast<XT>(rowacc[r] - c);
-        rowacc[r] = AT(0);
-        cs[p] = 0;
-        ce[p] = 0;
+        for (int k = k0; k < k1; ++k) c += qq[cperm[k]];
+        a.y[r0 + r] = static_cast<XT>(k1 > k0 ? rowacc[r] - c : rowacc[r]);
     }
     const int g0 = a.hhoff[t], g1 = a.hhoff[t + 1];
     for (int h = g0 + tid; h < g1; h += P) {
         const int p = a.hhrow[h] - wb;
         AT c = AT(0);
-        for (int k = cs[p]; k < ce[p]; ++k) c += q[S.cperm[k]];
+        for (int k = cs[p]; k < ce[p]; ++k) c += qq[cperm[k]];
         a.halo[h] = -c;
-        cs[p] = 0;
-        ce[p] = 0;
     }
 }
 
-// Long-row chunk c: entries [lcbeg[c], lcend[c]) of the long list, staged
-// from the 16-entry boundary below; one warp per row touched, partial sum
-// into the row's slot.
+// Long-row chunk c: entries [lcbeg[c], lcend[c]) of the long list, staged by
+// TMA from the 16-entry boundary below; one warp per row touched, partial
+// sum into the row's slot.
 template <typename VT, typename XT, typename AT>
-__device__ __forceinline__ void compute_long(const SpmvArgs<VT, XT, AT> &a, int c, Stage<VT, XT> &S) {
+__device__ __forceinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c, unsigned char *smem) {
+    const LongLayout L = long_layout(a.T, kLongChunk + 2 * kAlignFull, sizeof(VT));
+    VT *fval = reinterpret_cast<VT *>(smem + L.fval);
+    int32_t *fcol = reinterpret_cast<int32_t *>(smem + L.fcol);
+    uint16_t *flp = reinterpret_cast<uint16_t *>(smem + L.flp);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
     const int tid = threadIdx.x, P = blockDim.x;
     const int beg = a.lcbeg[c], end = a.lcend[c];
-    const int shift = beg - (beg & ~(kAlignFull - 1));
+    const int abeg = beg & ~(kAlignFull - 1);
+    const uint32_t mp = static_cast<uint32_t>((end - abeg + kAlignFull - 1) / kAlignFull * kAlignFull);
     const int l0 = a.lcfirst[c], nrc = a.lcrows[c];
-    uint16_t *flp = S.hrp;
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(mbar, mp * (sizeof(VT) + 4u));
+        bulk_g2s(fval, a.lval + abeg, mp * sizeof(VT), mbar);
+        bulk_g2s(fcol, a.lcol + abeg, mp * 4u, mbar);
+    }
     for (int u = tid; u <= nrc; u += P) flp[u] = static_cast<uint16_t>(min(max(a.lrp[l0 + u], beg), end) - beg);
     __syncthreads();
+    mbar_wait_bounded(mbar, 0, a.err);
+    __syncthreads();
+    const int shift = beg - abeg;
     const int warp = tid >> 5, nw = P >> 5;
     for (int u = warp; u < nrc; u += nw) {
-        const AT s = row_sum_warp<VT, XT, AT>(flp[u], flp[u + 1], S.fcol + shift, S.fval + shift, a.x);
+        const AT s = row_sum_warp<VT, XT, AT>(flp[u], flp[u + 1], fcol + shift, fval + shift, a.x);
         if ((tid & 31) == 0) a.lpart[a.lcslot[c] + u] = s;
     }
 }
 
 template <typename VT, typename XT, typename AT>
-__global__ void __launch_bounds__(kBlock, 1) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
+__global__ void __launch_bounds__(kBlock, 2) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const SmemLayout L = smem_layout(a.T, a.W, a.Mh, a.S, a.F, sizeof(VT), sizeof(XT), sizeof(AT));
-    const int tid = threadIdx.x, P = blockDim.x;
-    AT *rowacc = reinterpret_cast<AT *>(smem + L.rowacc);
-    AT *q = reinterpret_cast<AT *>(sizeof(VT) == sizeof(AT) ? nullptr : smem + L.q);
-    uint16_t *cs = reinterpret_cast<uint16_t *>(smem + L.cs);
-    uint16_t *ce = reinterpret_cast<uint16_t *>(smem + L.ce);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.mbar);
-    const int nitems = a.ntiles + a.nchunks;
-    const int G = gridDim.x;
-    for (int r = tid; r < a.T; r += P) rowacc[r] = AT(0);
-    for (int p = tid; p < a.T + a.W; p += P) {
-        cs[p] = 0;
-        ce[p] = 0;
-    }
-    if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_mbar_init();
-        for (int k = 0; k < kStages; ++k) {
-            const int item = blockIdx.x + k * G;
-            if (item < nitems) {
-                Stage<VT, XT> S(smem + k * L.stage_bytes, L.st);
-                issue_item<VT, XT, AT>(a, item, S, &bars[k]);
-            }
-        }
-    }
-    __syncthreads();
-    for (int k = 0;; ++k) {
-        const int item = blockIdx.x + k * G;
-        if (item >= nitems) break;
-        const int st = k & 1;
-        Stage<VT, XT> S(smem + st * L.stage_bytes, L.st);
-        mbar_wait_bounded(&bars[st], static_cast<uint32_t>((k >> 1) & 1), a.err);
-        if (item < a.ntiles) {
-            AT *qq = q ? q : reinterpret_cast<AT *>(S.hval);
-            compute_tile<VT, XT, AT>(a, item, S, rowacc, qq, cs, ce);
-        } else {
-            compute_long<VT, XT, AT>(a, item - a.ntiles, S);
-        }
-        __syncthreads();   // the stage and the scratch are free again
-        const int next = item + kStages * G;
-        if (tid == 0 && next < nitems) issue_item<VT, XT, AT>(a, next, S, &bars[st]);
-    }
+    if (static_cast<int>(blockIdx.x) < a.ntiles) tile_block<VT, XT, AT>(a, blockIdx.x, smem);
+    else long_block<VT, XT, AT>(a, blockIdx.x - a.ntiles, smem);
 }
 
 // One thread per receiving row: y[row] += halo sum, then the row's long-row
@@ -424,8 +369,6 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     a.ntiles = h->ntiles;
     a.nchunks = static_cast<int32_t>(L.lcbeg.size());
     a.Mh = static_cast<int32_t>(round_up(L.max_tile_half, kAlignHalf));
-    a.S = L.max_tile_slices;
-    a.F = stage_full_entries(h);
     a.hoff = D.hoff;
     a.hcnt = D.hcnt;
     a.hrp = D.hrp;
@@ -461,8 +404,7 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
         if (e != cudaSuccess) return cuda_status(e);
         configured.store(1);
     }
-    const int nitems = h->ntiles + a.nchunks;
-    const int grid = std::min(nitems, sm_count());
+    const int grid = h->ntiles + a.nchunks;
     if (grid > 0) tile_kernel<VT, XT, AT><<<grid, kBlock, smem, st>>>(a);
     const int nf = static_cast<int>(L.fold_row.size());
     if (nf > 0) {
