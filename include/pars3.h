@@ -240,6 +240,23 @@ int pars3_unpermute(const pars3_handle *h, int32_t dtype, int32_t k_cols, const 
 int pars3_spmv_host(pars3_handle *h, int32_t dtype, double alpha, const void *x_host, void *y_host,
                     void *stream);
 
+/* pars3_spmv_noalloc -- the same product as pars3_spmv, for callers that
+ * cannot have the library allocate device memory for its scratch (all
+ * device memory handed to another allocator or pool, or a fixed memory
+ * budget).  The paper has no counterpart: this is a deployment variant.
+ * The scratch (cross-tile halo sums and long-row partial sums) lives in one
+ * library-wide device array of 4 MiB that every GPU loading the library
+ * holds until the process exits; the call allocates nothing.  The array's
+ * device address is looked up on the first call with a given device
+ * current, and that first call should come before any stream capture.
+ * Every call shares the array (its contents are overwritten before they
+ * are read), so calls that overlap on the GPU race.  Returns
+ * PARS3_EUNSUPPORTED when the handle needs more scratch than the array
+ * holds (halo targets plus long-row slots times the accumulator size: 8
+ * bytes for PARS3_F64, 4 otherwise); other errors as pars3_spmv. */
+int pars3_spmv_noalloc(const pars3_handle *h, int32_t dtype, double alpha, const void *x, void *y,
+                       void *stream);
+
 /* Reads and clears the handle's device error word (synchronizes the
  * stream).  Returns PARS3_OK, PARS3_ETIMEOUT or PARS3_ECUDA. */
 int pars3_check(const pars3_handle *h, void *stream);

@@ -134,6 +134,8 @@ int cuda_status(int cuda_err);
 // spmv.cu
 int launch_spmv(const pars3_handle *h, int dtype, double alpha, int k, const void *x, void *y,
                 void *stream);
+int launch_spmv_scratch(const pars3_handle *h, int dtype, double alpha, const void *x, void *y, void *halo,
+                        void *lpart, void *stream);
 int launch_permute(const pars3_handle *h, int dtype, int k, const void *src, void *dst, bool inverse,
                    void *stream);
 int prepare_kernels();

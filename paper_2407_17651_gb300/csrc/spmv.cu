@@ -358,8 +358,8 @@ int sm_count() {
 }
 
 template <typename VT, typename XT, typename AT>
-static int launch_typed(const pars3_handle *h, int dtype, double alpha, const void *x, void *y,
-                        cudaStream_t st) {
+static int launch_typed(const pars3_handle *h, int dtype, double alpha, const void *x, void *y, void *halo,
+                        void *lpart, cudaStream_t st) {
     const Layout &L = h->L;
     const DevLayout &D = h->D;
     SpmvArgs<VT, XT, AT> a;
@@ -377,7 +377,7 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     a.hval = static_cast<const VT *>(D.hval[dtype]);
     a.hhoff = D.hhoff;
     a.hhrow = D.hhrow;
-    a.halo = static_cast<AT *>(D.halo);
+    a.halo = static_cast<AT *>(halo);
     a.sl_off = D.sl_off;
     a.sl_ent = D.sl_ent;
     a.sl_meta = D.sl_meta;
@@ -391,7 +391,7 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     a.lcslot = D.lcslot;
     a.lcol = D.lcol;
     a.lval = static_cast<const VT *>(D.lval[dtype]);
-    a.lpart = static_cast<AT *>(D.lpart);
+    a.lpart = static_cast<AT *>(lpart);
     a.x = static_cast<const XT *>(x);
     a.y = static_cast<XT *>(y);
     a.alpha = static_cast<AT>(alpha);
@@ -410,21 +410,26 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     if (nf > 0) {
         const int blocks = static_cast<int>(std::min<int64_t>((nf + 255) / 256, 152 * 8));
         fold_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, D.fold_row, D.fold_halo, D.fold_long,
-                                                    static_cast<const AT *>(D.halo), D.lc0, D.lc1, D.lcfirst, D.lcslot,
-                                                    static_cast<const AT *>(D.lpart), static_cast<XT *>(y));
+                                                    static_cast<const AT *>(halo), D.lc0, D.lc1, D.lcfirst, D.lcslot,
+                                                    static_cast<const AT *>(lpart), static_cast<XT *>(y));
     }
     return cuda_status(cudaGetLastError());
 }
 
-int launch_spmv(const pars3_handle *h, int dtype, double alpha, int k, const void *x, void *y, void *stream) {
+int launch_spmv_scratch(const pars3_handle *h, int dtype, double alpha, const void *x, void *y, void *halo,
+                        void *lpart, void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (k != 1) return PARS3_EUNSUPPORTED;
     switch (dtype) {
-        case PARS3_F64: return launch_typed<double, double, double>(h, dtype, alpha, x, y, st);
-        case PARS3_F32: return launch_typed<float, float, float>(h, dtype, alpha, x, y, st);
-        case PARS3_BF16: return launch_typed<uint16_t, float, float>(h, dtype, alpha, x, y, st);
+        case PARS3_F64: return launch_typed<double, double, double>(h, dtype, alpha, x, y, halo, lpart, st);
+        case PARS3_F32: return launch_typed<float, float, float>(h, dtype, alpha, x, y, halo, lpart, st);
+        case PARS3_BF16: return launch_typed<uint16_t, float, float>(h, dtype, alpha, x, y, halo, lpart, st);
         default: return PARS3_EINVAL;
     }
+}
+
+int launch_spmv(const pars3_handle *h, int dtype, double alpha, int k, const void *x, void *y, void *stream) {
+    if (k != 1) return PARS3_EUNSUPPORTED;
+    return launch_spmv_scratch(h, dtype, alpha, x, y, h->D.halo, h->D.lpart, stream);
 }
 
 int launch_permute(const pars3_handle *h, int dtype, int k, const void *src, void *dst, bool inverse,

@@ -101,6 +101,7 @@ def lib() -> C.CDLL:
         "pars3_layout_check": ([P], C.c_int),
         "pars3_upload": ([P, P], C.c_int),
         "pars3_spmv": ([P, i32, f64, P, P, P], C.c_int),
+        "pars3_spmv_noalloc": ([P, i32, f64, P, P, P], C.c_int),
         "pars3_spmm": ([P, i32, f64, i32, P, P, P], C.c_int),
         "pars3_spmm_batched": ([P, i32, i32, P, i32, P, P, i32, P], C.c_int),
         "pars3_mrs": ([P, f64, P, P, P, P, P], C.c_int),
@@ -124,7 +125,7 @@ def exported_symbols():
     return ["pars3_strerror", "pars3_version", "pars3_reorder", "pars3_split", "pars3_split_export",
             "pars3_info_get", "pars3_layout_check", "pars3_upload", "pars3_spmv", "pars3_spmm",
             "pars3_spmm_batched", "pars3_mrs", "pars3_permute", "pars3_unpermute", "pars3_spmv_host",
-            "pars3_check", "pars3_autotune", "pars3_free"]
+            "pars3_check", "pars3_autotune", "pars3_free", "pars3_spmv_noalloc"]
 
 
 def _chk(rc: int, where: str):
@@ -255,6 +256,12 @@ def pars3_upload(h: Handle, stream=None):
 
 def pars3_spmv(h: Handle, dtype: int, alpha: float, x, y, stream=None):
     _chk(lib().pars3_spmv(h, int(dtype), float(alpha), _dptr(x), _dptr(y), _stream(stream)), "pars3_spmv")
+
+
+def pars3_spmv_noalloc(h: Handle, dtype: int, alpha: float, x, y, stream=None):
+    """pars3_spmv with its scratch in the library's fixed device array (the call allocates nothing)."""
+    _chk(lib().pars3_spmv_noalloc(h, int(dtype), float(alpha), _dptr(x), _dptr(y), _stream(stream)),
+         "pars3_spmv_noalloc")
 
 
 def pars3_spmm(h: Handle, dtype: int, alpha: float, X, Y, stream=None):
