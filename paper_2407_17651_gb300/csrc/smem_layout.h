@@ -17,7 +17,7 @@ namespace pars3 {
 // window, the tile's middle entries (filled by TMA bulk copies) and scratch;
 // a long-chunk block uses the same buffer for the chunk's entries.
 struct SmemLayout {
-    uint32_t xs, rowacc, hval, q, hcol, cperm, hrp, cs, ce, mbar, total;
+    uint32_t xs, rowacc, hval, q, hcol, cperm, hrp, cs, ce, red, mbar, total;
 };
 struct LongLayout {
     uint32_t fval, fcol, flp, mbar, total;
@@ -39,7 +39,8 @@ PARS3_HD SmemLayout smem_layout(uint32_t T, uint32_t W, uint32_t Mh, uint32_t vs
     s.hrp = align128(s.cperm + Mh * 2u);
     s.cs = align128(s.hrp + (T + 8u) * 2u);
     s.ce = align128(s.cs + (T + W) * 2u);
-    s.mbar = align128(s.ce + (T + W) * 2u);
+    s.red = align128(s.ce + (T + W) * 2u);
+    s.mbar = align128(s.red + 32u * 8u);
     s.total = align128(s.mbar + 8u);
     return s;
 }

@@ -1,0 +1,476 @@
+// spmv_kernels.cuh -- device code of the skew product, shared by the
+// operator (spmv.cu) and the MRS solver (mrs.cu, which runs the same tile
+// kernel in its Lanczos mode).
+//
+// Two launches per product: the tile kernel (one block per row tile -- the
+// block-row ownership of Sec. 3 and Fig. 2 -- plus one block per chunk of
+// the long-row list) and a small fold kernel that adds the cross-tile
+// (halo) mirrored sums and the long-row partial sums to y.  No atomics:
+// every y entry has one writer per launch and every sum runs in an order
+// fixed by the layout and the block size, so results are bitwise
+// reproducible from run to run.
+//
+// Tile block t (rows [tT, tT+T)):
+//  0. one thread issues TMA bulk copies of the x window [tT-W, tT+T) (the x
+//     slice a row block needs, Sec. 3.1.2) and of the tile's middle entries
+//     (values, window columns, (column,row) order, row pointers);
+//  1. meanwhile the full pass streams the tile's full-storage rows in
+//     sliced-ELL order straight from HBM: each warp takes 32-row slices,
+//     one lane per row (every row of the tile owns a lane), slot m of lane
+//     l at 32m+l so that every load instruction reads 32 consecutive
+//     entries; a lane's sum starts at alpha x_r and gathers x_j, eight
+//     slots in flight;
+//  2. half pass: each middle entry l_ij is read once and used twice (Eqs.
+//     2-6): l_ij x_j is summed into row i, the mirrored product l_ij x_i is
+//     kept in shared memory;
+//  3. the mirrored products are summed per column in the (column, row)
+//     order of the canonical tile list: columns inside the tile complete
+//     their row, columns before the tile (the conflicting region R2 of
+//     Fig. 2) go to the halo list that the fold adds to the previous tile.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "devcommon.cuh"
+#include "internal.h"
+#include "smem_layout.h"
+
+namespace pars3 {
+
+template <typename VT, typename XT, typename AT>
+struct SpmvArgs {
+    int32_t n, T, W, ntiles, nchunks, Mh;
+    const int32_t *hoff, *hcnt;
+    const uint16_t *hrp, *hcol, *hcperm;
+    const VT *hval;
+    const int32_t *hhoff, *hhrow;
+    AT *halo;
+    const int32_t *sl_off, *sl_ent;
+    const uint32_t *sl_meta;
+    const int32_t *fcol;
+    const VT *fval;
+    const int32_t *lrp, *lcbeg, *lcend, *lcfirst, *lcrows, *lcslot, *lcol;
+    const VT *lval;
+    AT *lpart;
+    const XT *x;
+    XT *y;
+    AT alpha;
+    int32_t *err;
+};
+
+template <typename VT> __device__ __forceinline__ typename Val<VT>::acc sval(const VT *p, int e);
+template <> __device__ __forceinline__ double sval<double>(const double *p, int e) { return p[e]; }
+template <> __device__ __forceinline__ float sval<float>(const float *p, int e) { return p[e]; }
+template <> __device__ __forceinline__ float sval<uint16_t>(const uint16_t *p, int e) { return bf16_bits_to_f32(p[e]); }
+
+constexpr int kUnroll = 8;       // independent gathers in flight per lane
+constexpr int kShortRow = 16;    // middle rows longer than this are summed by the whole warp
+
+// Sliced-ELL row of lane l: slots base + 32 m + l (m < len) of the global
+// value and column arrays, streamed (evict-first); x_j gathered.  The sum
+// starts at `start`.
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ AT slice_row_sum(const VT *__restrict__ val, const int32_t *__restrict__ col,
+                                            int64_t base, int len, const XT *__restrict__ xg, AT start) {
+    AT acc = start;
+    for (int m0 = 0; m0 < len; m0 += kUnroll) {
+        int c[kUnroll];
+        AT v[kUnroll], xv[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            c[u] = 0;
+            v[u] = AT(0);
+            if (m0 + u < len) {
+                const int64_t q = base + static_cast<int64_t>(m0 + u) * kSlice;
+                c[u] = __ldcs(col + q);
+                v[u] = Val<VT>::ld_stream(val + q);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) xv[u] = (m0 + u < len) ? static_cast<AT>(__ldg(xg + c[u])) : AT(0);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (m0 + u < len) acc += v[u] * xv[u];
+    }
+    return acc;
+}
+
+// Row [e0, e1) of a long-row chunk by a whole warp: lane l takes entries
+// e0+l, e0+l+32, ... in order, then a butterfly reduction (every lane ends
+// with the same bits: each step adds the same two partial sums, only in
+// swapped operand order).
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ AT row_sum_warp(int e0, int e1, const int32_t *col_s, const VT *val_s,
+                                           const XT *__restrict__ xg) {
+    const int lane = threadIdx.x & 31;
+    AT acc = AT(0);
+    for (int base = e0 + lane; base < e1; base += 32 * 4) {
+        AT v[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = base + 32 * u;
+            v[u] = AT(0);
+            xv[u] = AT(0);
+            if (e < e1) {
+                v[u] = sval<VT>(val_s, e);
+                xv[u] = static_cast<AT>(__ldg(xg + col_s[e]));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (base + 32 * u < e1) acc += v[u] * xv[u];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Half-storage row of the middle part: returns sum_j l_rj x_j and stores the
+// mirrored products q[e] = l_rj x_r (q may alias the value array: entry e is
+// read before it is overwritten, by the same thread).
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ AT half_row_thread(int e0, int e1, const VT *hval, const uint16_t *hcol, AT *q,
+                                              const XT *xs, AT xr) {
+    AT acc = AT(0);
+    for (int e = e0; e < e1; ++e) {
+        const AT v = sval<VT>(hval, e);
+        const AT xj = static_cast<AT>(xs[hcol[e]]);
+        q[e] = v * xr;
+        acc += v * xj;
+    }
+    return acc;
+}
+
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ AT half_row_warp(int e0, int e1, const VT *hval, const uint16_t *hcol, AT *q,
+                                            const XT *xs, AT xr) {
+    const int lane = threadIdx.x & 31;
+    AT acc = AT(0);
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const AT v = sval<VT>(hval, e);
+        const AT xj = static_cast<AT>(xs[hcol[e]]);
+        q[e] = v * xr;
+        acc += v * xj;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Row epilogues of the tile block.  Plain product: a row sum starts at
+// alpha x_r and is stored as y_r.
+template <typename XT, typename AT>
+struct EpiSpmv {
+    AT alpha;
+    XT *y;
+    __device__ __forceinline__ AT start(const XT *__restrict__ x, int r) const {
+        return alpha * static_cast<AT>(__ldg(x + r));
+    }
+    __device__ __forceinline__ void finish(int r, AT v) { y[r] = static_cast<XT>(v); }
+    __device__ __forceinline__ void end_block(int, double *) {}
+};
+
+// fp64 scalars of the MRS recurrence, kept on the device.  Per-iteration
+// values sit in rings of four indexed by j & 3.
+struct MrsState {
+    double beta[4], rho[4], c[4], s[4], tau[4];
+    double gamma;      // gamma_{j+1}
+    double t;          // t_{j+1}
+    double alpha, tol;
+    int32_t j;         // last completed iteration
+    int32_t jmax, done, pad;
+    uint32_t ticket, pad2;
+};
+
+// Lanczos epilogue of MRS iteration j (the tile kernel computes the raw
+// product S w_{j-1}): w_j = (S w_{j-1}) / beta_{j-1} + (beta_{j-1} /
+// beta_{j-2}) w_{j-2} (that is S v_j + beta_{j-1} v_{j-1} with v_j =
+// w_{j-1}/beta_{j-1}), its squared norm over rows the fold does not touch,
+// and the lagged update of iteration j-1: p_{j-1} = (v_{j-1} - R[j-3,j-1]
+// p_{j-3}) / rho_{j-1}, x += tau_{j-1} p_{j-1}.
+template <typename XT, typename AT>
+struct EpiMrs {
+    XT *y;
+    const XT *wpp, *pold;
+    XT *pnew, *xsol;
+    const uint32_t *fold_bits;
+    double *part;
+    AT scale, coef, inv_b2, r3, inv_rho, tau;
+    bool lag;
+    double nrm;
+    __device__ __forceinline__ AT start(const XT *__restrict__, int) const { return AT(0); }
+    __device__ __forceinline__ void finish(int r, AT raw) {
+        AT w = raw * scale;
+        if (coef != AT(0)) w += coef * static_cast<AT>(wpp[r]);
+        const XT wx = static_cast<XT>(w);
+        y[r] = wx;
+        if (!((__ldg(fold_bits + (r >> 5)) >> (r & 31)) & 1u)) nrm += static_cast<double>(wx) * static_cast<double>(wx);
+        if (lag) {
+            const AT pv = (static_cast<AT>(wpp[r]) * inv_b2 - r3 * static_cast<AT>(pold[r])) * inv_rho;
+            pnew[r] = static_cast<XT>(pv);
+            xsol[r] = static_cast<XT>(static_cast<AT>(xsol[r]) + tau * pv);
+        }
+    }
+    // fixed-order block sum of the thread norms into part[t]
+    __device__ __forceinline__ void end_block(int t, double *red) {
+        double v = nrm;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[warp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[w];
+            part[t] = s;
+        }
+    }
+};
+
+template <typename XT, typename AT>
+__device__ __forceinline__ EpiMrs<XT, AT> make_mrs_epi(const MrsState *st, XT *const *wr, XT *const *pr, XT *xsol,
+                                                       const uint32_t *fold_bits, double *part, const XT **xop) {
+    EpiMrs<XT, AT> e;
+    const int j = st->j + 1;
+    const double b1 = st->beta[(j - 1) & 3];
+    const double b2 = j >= 2 ? st->beta[(j - 2) & 3] : 1.0;
+    *xop = wr[(j + 2) % 3];
+    e.y = wr[j % 3];
+    e.wpp = wr[(j + 1) % 3];
+    e.pold = pr[j % 3];
+    e.pnew = pr[(j + 2) % 3];
+    e.xsol = xsol;
+    e.fold_bits = fold_bits;
+    e.part = part;
+    e.scale = static_cast<AT>(1.0 / b1);
+    e.coef = static_cast<AT>(j >= 2 ? b1 / b2 : 0.0);
+    e.lag = j >= 2;
+    e.inv_b2 = static_cast<AT>(1.0 / b2);
+    e.r3 = static_cast<AT>(j >= 4 ? -st->s[(j - 3) & 3] * b2 : 0.0);
+    e.inv_rho = static_cast<AT>(j >= 2 ? 1.0 / st->rho[(j - 1) & 3] : 0.0);
+    e.tau = static_cast<AT>(j >= 2 ? st->tau[(j - 1) & 3] : 0.0);
+    e.nrm = 0.0;
+    return e;
+}
+
+template <typename VT, typename XT, typename AT, class Epi>
+__device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t, unsigned char *smem,
+                                           const XT *__restrict__ xop, Epi &epi) {
+    const SmemLayout L = smem_layout(a.T, a.W, a.Mh, sizeof(VT), sizeof(XT), sizeof(AT));
+    XT *xs = reinterpret_cast<XT *>(smem + L.xs);
+    AT *rowacc = reinterpret_cast<AT *>(smem + L.rowacc);
+    VT *hval = reinterpret_cast<VT *>(smem + L.hval);
+    AT *q = reinterpret_cast<AT *>(smem + L.q);
+    uint16_t *hcol = reinterpret_cast<uint16_t *>(smem + L.hcol);
+    uint16_t *cperm = reinterpret_cast<uint16_t *>(smem + L.cperm);
+    uint16_t *hrp = reinterpret_cast<uint16_t *>(smem + L.hrp);
+    uint16_t *cs = reinterpret_cast<uint16_t *>(smem + L.cs);
+    uint16_t *ce = reinterpret_cast<uint16_t *>(smem + L.ce);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
+    const int tid = threadIdx.x, P = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = P >> 5;
+    const int r0 = t * a.T, r1 = min(r0 + a.T, a.n), nr = r1 - r0;
+    const int wb = r0 - a.W, wlo = max(wb, 0);
+    const uint32_t nbulk = (static_cast<uint32_t>(r1 - wlo) * sizeof(XT)) & ~15u;
+    const int hb = a.hoff[t], hm = a.hcnt[t];
+    const uint32_t hmp = static_cast<uint32_t>((hm + kAlignHalf - 1) / kAlignHalf * kAlignHalf);
+    const uint32_t rpb = static_cast<uint32_t>(a.T + 8) * 2u;
+
+    // 0. the copy engine stages the x window and the middle entries
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        uint32_t tx = nbulk + rpb;
+        if (hm > 0) tx += hmp * (sizeof(VT) + 4u);
+        mbar_arrive_expect_tx(mbar, tx);
+        if (nbulk > 0) bulk_g2s(xs + (wlo - wb), xop + wlo, nbulk, mbar);
+        bulk_g2s(hrp, a.hrp + static_cast<size_t>(t) * (a.T + 8), rpb, mbar);
+        if (hm > 0) {
+            bulk_g2s(hval, a.hval + hb, hmp * sizeof(VT), mbar);
+            bulk_g2s(hcol, a.hcol + hb, hmp * 2u, mbar);
+            bulk_g2s(cperm, a.hcperm + hb, hmp * 2u, mbar);
+        }
+    }
+    for (int g = wlo + static_cast<int>(nbulk / sizeof(XT)) + tid; g < r1; g += P) xs[g - wb] = xop[g];
+    if (hm > 0)
+        for (int p = tid; p < nr + a.W; p += P) {
+            cs[p] = 0;
+            ce[p] = 0;
+        }
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+
+    // 1. full pass (sliced ELL) straight from HBM while the copy runs
+    const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
+    for (int s = s0 + warp; s < s1; s += nwarps) {
+        const uint32_t meta = __ldg(a.sl_meta + static_cast<int64_t>(s) * kSlice + lane);
+        const int rl = static_cast<int>(meta & 0xffffu), len = static_cast<int>(meta >> 16);
+        if (rl != 0xffff) {
+            const AT start = epi.start(xop, r0 + rl);
+            rowacc[rl] = slice_row_sum<VT, XT, AT>(a.fval, a.fcol, static_cast<int64_t>(__ldg(a.sl_ent + s)) + lane,
+                                                   len, xop, start);
+        }
+    }
+    mbar_wait_bounded(mbar, 0, a.err);
+    __syncthreads();
+
+    double *red = reinterpret_cast<double *>(smem + L.red);
+    if (hm == 0) {
+        for (int r = tid; r < nr; r += P) epi.finish(r0 + r, rowacc[r]);
+        epi.end_block(t, red);
+        return;
+    }
+    AT *qq = sizeof(VT) == sizeof(AT) ? reinterpret_cast<AT *>(hval) : q;
+
+    // 2. half pass: middle row sums and mirrored products.  A warp owns 32
+    // consecutive rows; middle rows longer than kShortRow are summed by the
+    // whole warp, one after the other.
+    for (int rb = (tid & ~31); rb < nr; rb += P) {
+        const int r = rb + lane;
+        const bool valid = r < nr;
+        const AT xr = valid ? static_cast<AT>(xs[r + a.W]) : AT(0);
+        const int h0 = valid ? hrp[r] : 0, h1 = valid ? hrp[r + 1] : 0;
+        const bool hlong = (h1 - h0) > kShortRow;
+        AT hs = AT(0);
+        if (valid && !hlong) hs = half_row_thread<VT, XT, AT>(h0, h1, hval, hcol, qq, xs, xr);
+        unsigned m = __ballot_sync(0xffffffffu, hlong);
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int f0 = __shfl_sync(0xffffffffu, h0, b), f1 = __shfl_sync(0xffffffffu, h1, b);
+            const AT xb = __shfl_sync(0xffffffffu, xr, b);
+            const AT s2 = half_row_warp<VT, XT, AT>(f0, f1, hval, hcol, qq, xs, xb);
+            if (lane == b) hs = s2;
+        }
+        if (valid && h1 > h0) rowacc[r] += hs;
+    }
+    __syncthreads();
+
+    // 3. mirrored sums per column: segment boundaries of the (column, row) list
+    for (int k = tid; k < hm; k += P) {
+        const int key = hcol[cperm[k]];
+        if (k == 0 || hcol[cperm[k - 1]] != key) cs[key] = static_cast<uint16_t>(k);
+        if (k == hm - 1 || hcol[cperm[k + 1]] != key) ce[key] = static_cast<uint16_t>(k + 1);
+    }
+    __syncthreads();
+    for (int r = tid; r < nr; r += P) {
+        const int p = r + a.W;
+        const int k0 = cs[p], k1 = ce[p];
+        AT c = AT(0);
+        for (int k = k0; k < k1; ++k) c += qq[cperm[k]];
+        epi.finish(r0 + r, k1 > k0 ? rowacc[r] - c : rowacc[r]);
+    }
+    const int g0 = a.hhoff[t], g1 = a.hhoff[t + 1];
+    for (int h = g0 + tid; h < g1; h += P) {
+        const int p = a.hhrow[h] - wb;
+        AT c = AT(0);
+        for (int k = cs[p]; k < ce[p]; ++k) c += qq[cperm[k]];
+        a.halo[h] = -c;
+    }
+    epi.end_block(t, red);
+}
+
+// Long-row chunk c: entries [lcbeg[c], lcend[c]) of the long list, staged by
+// TMA from the 16-entry boundary below; one warp per row touched, partial
+// sum into the row's slot.
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c, unsigned char *smem,
+                                           const XT *__restrict__ xop) {
+    const LongLayout L = long_layout(a.T, kLongChunk + 2 * kAlignFull, sizeof(VT));
+    VT *fval = reinterpret_cast<VT *>(smem + L.fval);
+    int32_t *fcol = reinterpret_cast<int32_t *>(smem + L.fcol);
+    uint16_t *flp = reinterpret_cast<uint16_t *>(smem + L.flp);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
+    const int tid = threadIdx.x, P = blockDim.x;
+    const int beg = a.lcbeg[c], end = a.lcend[c];
+    const int abeg = beg & ~(kAlignFull - 1);
+    const uint32_t mp = static_cast<uint32_t>((end - abeg + kAlignFull - 1) / kAlignFull * kAlignFull);
+    const int l0 = a.lcfirst[c], nrc = a.lcrows[c];
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(mbar, mp * (sizeof(VT) + 4u));
+        bulk_g2s(fval, a.lval + abeg, mp * sizeof(VT), mbar);
+        bulk_g2s(fcol, a.lcol + abeg, mp * 4u, mbar);
+    }
+    for (int u = tid; u <= nrc; u += P) flp[u] = static_cast<uint16_t>(min(max(a.lrp[l0 + u], beg), end) - beg);
+    __syncthreads();
+    mbar_wait_bounded(mbar, 0, a.err);
+    __syncthreads();
+    const int shift = beg - abeg;
+    const int warp = tid >> 5, nw = P >> 5;
+    for (int u = warp; u < nrc; u += nw) {
+        const AT s = row_sum_warp<VT, XT, AT>(flp[u], flp[u + 1], fcol + shift, fval + shift, xop);
+        if ((tid & 31) == 0) a.lpart[a.lcslot[c] + u] = s;
+    }
+}
+
+template <typename VT, typename XT, typename AT>
+__global__ void __launch_bounds__(kBlock, 2) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (static_cast<int>(blockIdx.x) < a.ntiles) {
+        EpiSpmv<XT, AT> epi{a.alpha, a.y};
+        tile_block<VT, XT, AT>(a, blockIdx.x, smem, a.x, epi);
+    } else {
+        long_block<VT, XT, AT>(a, blockIdx.x - a.ntiles, smem, a.x);
+    }
+}
+
+// Lanczos step of MRS iteration j = st->j + 1 (see EpiMrs); the operand,
+// output and ring slots follow from j, read on the device, so the launch
+// can be replayed from a CUDA graph.
+template <typename XT>
+struct MrsVectors {
+    MrsState *st;
+    XT *w[3];
+    XT *p[3];
+    XT *xsol;
+    const uint32_t *fold_bits;
+    double *part;
+};
+
+template <typename VT, typename XT, typename AT>
+__global__ void __launch_bounds__(kBlock, 2) tile_kernel_mrs(const SpmvArgs<VT, XT, AT> a, const MrsVectors<XT> m) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const XT *xop = nullptr;
+    EpiMrs<XT, AT> epi = make_mrs_epi<XT, AT>(m.st, m.w, m.p, m.xsol, m.fold_bits, m.part, &xop);
+    if (static_cast<int>(blockIdx.x) < a.ntiles) tile_block<VT, XT, AT>(a, blockIdx.x, smem, xop, epi);
+    else long_block<VT, XT, AT>(a, blockIdx.x - a.ntiles, smem, xop);
+}
+
+// One thread per receiving row: y[row] += halo sum, then the row's long-row
+// partial sums in chunk order.
+template <typename XT, typename AT>
+__global__ void __launch_bounds__(256) fold_kernel(int nitems, const int32_t *__restrict__ frow,
+                                                   const int32_t *__restrict__ fhalo,
+                                                   const int32_t *__restrict__ flong, const AT *__restrict__ halo,
+                                                   const int32_t *__restrict__ lc0, const int32_t *__restrict__ lc1,
+                                                   const int32_t *__restrict__ lcfirst,
+                                                   const int32_t *__restrict__ lcslot,
+                                                   const AT *__restrict__ lpart, XT *__restrict__ y) {
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nitems; f += gridDim.x * blockDim.x) {
+        const int r = frow[f];
+        AT v = static_cast<AT>(y[r]);
+        const int hi = fhalo[f];
+        if (hi >= 0) v += halo[hi];
+        const int l = flong[f];
+        if (l >= 0)
+            for (int c = lc0[l]; c <= lc1[l]; ++c) v += lpart[lcslot[c] + (l - lcfirst[c])];
+        y[r] = static_cast<XT>(v);
+    }
+}
+
+template <typename T>
+__global__ void permute_kernel(int64_t n, int k, const int32_t *__restrict__ perm, const T *__restrict__ src,
+                               T *__restrict__ dst, bool inverse) {
+    const int64_t total = n * k;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = idx / k, c = idx - i * k;
+        const int64_t o = perm[i];
+        if (!inverse) dst[i * k + c] = src[o * k + c];
+        else dst[o * k + c] = src[i * k + c];
+    }
+}
+
+}  // namespace pars3
