@@ -196,6 +196,47 @@ def cpu_baseline(A, alpha, x, budget_s: float):
             "sample": f"{cnt} full-storage fp64 SpMVs of the whole matrix ({el:.1f} s, single thread)"}
 
 
+def mrs_section(A, perm, T, Wc, alphas, budget_iters: int):
+    """Configuration 3: (alpha I + S) x = b on the configuration-1 matrix,
+    time to a true relative residual of 1e-10: plain fp64 MRS against an
+    fp32 / bf16-value inner MRS inside fp64 refinement (wall time of one
+    pars3_mrs call, graph capture done by an untimed warm-up solve)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2407_17651_gb300 import pars3 as P
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=Wc,
+                      dtypes=P.dtype_bit(P.F64) | P.dtype_bit(P.F32) | P.dtype_bit(P.BF16))
+    P.pars3_upload(h)
+    b = torch.from_numpy(W.config3_rhs(A.n)[perm]).cuda()
+    x = torch.zeros_like(b)
+    inner_rtol = {P.F64: 0.0, P.F32: 1e-4, P.BF16: 1e-2}
+    names = {P.F64: "fp64", P.F32: "fp32-ir", P.BF16: "bf16-ir"}
+    for inner in (P.F64, P.F32, P.BF16):   # capture the loops
+        x.zero_()
+        P.pars3_mrs(h, 1.0, b, x, rtol=1e-10, inner=inner, inner_rtol=inner_rtol[inner], max_iter=5,
+                    raise_on_noconv=False)
+    out = {}
+    for alpha in alphas:
+        row = {}
+        for inner in (P.F64, P.F32, P.BF16):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = P.pars3_mrs(h, alpha, b, x, rtol=1e-10, inner=inner, inner_rtol=inner_rtol[inner],
+                            max_iter=budget_iters, max_outer=40, raise_on_noconv=False)
+            el = time.perf_counter() - t0
+            row[names[inner]] = {"time_s": el, "iters": r["iters"], "outer": r["outer"],
+                                 "true_relres": r["true_relres"], "converged": r["status"] == 0,
+                                 "inner_rtol": inner_rtol[inner] or None}
+        t64 = row["fp64"]["time_s"]
+        for k in ("fp32-ir", "bf16-ir"):
+            row[k]["speedup_vs_fp64"] = (t64 / row[k]["time_s"]) if row[k]["converged"] and row["fp64"]["converged"] else None
+        out[str(alpha)] = row
+    h.close()
+    return out
+
+
 def traffic_from_profile(kernel_hash: str, launch_units: float):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source."""
@@ -230,6 +271,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-spmvs", type=int, default=10)
+    ap.add_argument("--mrs", default="1,0.1,0.01", help="alphas of the MRS comparison ('' to skip)")
+    ap.add_argument("--mrs-iters", type=int, default=60000)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -325,6 +368,9 @@ def main():
                "api": "pars3_spmv_host (H2D, permute, SpMV, unpermute, D2H, sync per product)"}
 
     cpu = cpu_baseline(A, alpha, x, args.cpu_budget) if (rank == 0 and ws == 1) else None
+    mrs = None
+    if args.mrs and args.workload == "cfg1":
+        mrs = mrs_section(A, perm, info["T"], info["W"], [float(a) for a in args.mrs.split(",")], args.mrs_iters)
     launches_per_spmv = 1 + (1 if info["halo_targets"] + info["long_rows"] > 0 else 0)
     if rank == 0:
         line = {
@@ -349,6 +395,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_spmv * REPEATS * args.steps,
+            "mrs": mrs,
             "clocks": clk,
             "preprocess_s": {"rcm": t_rcm, "split": t_split, "upload": t_up},
             "spmv_us": {"mean": 1e6 * avg_spmv_s, "median": 1e6 * statistics.median(spmv_ms) / 1e3,

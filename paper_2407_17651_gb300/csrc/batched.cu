@@ -1,0 +1,307 @@
+// batched.cu -- Y_m = (alpha_m I + S_m) X_m for many split handles of uneven
+// sizes in ONE persistent launch: a fixed grid of blocks walks the
+// concatenated list of work units (every tile and long-row chunk of every
+// matrix) in a static round-robin order, followed by one batched fold
+// launch.  Per-matrix kernel arguments live in a device table; with
+// capture != 0 the pair of launches is recorded once in a CUDA graph and
+// replayed while the arguments stay the same.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "spmm_device.cuh"
+
+namespace pars3 {
+
+int spmm_smem_bytes(const pars3_handle *h, int dtype);
+
+// work unit u belongs to matrix m with upre[m] <= u < upre[m+1]
+__device__ __forceinline__ int unit_matrix(const int32_t *upre, int count, int u) {
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (upre[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename VT, typename XT, typename AT, int LPR>
+__global__ void __launch_bounds__(kBlock, 2) batched_kernel(const SpmvArgs<VT, XT, AT> *__restrict__ args,
+                                                             const int32_t *__restrict__ upre, int count,
+                                                             int total, int k) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ SpmvArgs<VT, XT, AT> a;
+    __shared__ int item;
+    for (int u = blockIdx.x; u < total; u += gridDim.x) {
+        // the previous unit's shared-memory accesses finish before the next
+        // unit's bulk copies overwrite the same bytes
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int m = unit_matrix(upre, count, u);
+            a = args[m];
+            item = u - upre[m];
+        }
+        __syncthreads();
+        if (k == 1) {
+            if (item < a.ntiles) {
+                EpiSpmv<XT, AT> epi{a.alpha, a.y};
+                tile_block<VT, XT, AT>(a, item, smem, a.x, epi);
+            } else {
+                long_block<VT, XT, AT>(a, item - a.ntiles, smem, a.x);
+            }
+        } else {
+            if (item < a.ntiles) spmm_tile<VT, XT, AT, LPR>(a, k, item, smem);
+            else spmm_long<VT, XT, AT, LPR>(a, k, item - a.ntiles);
+        }
+    }
+}
+
+// fold of all matrices: one thread per (receiving row, column)
+struct FoldArgs {
+    int32_t nf;
+    const int32_t *frow, *fhalo, *flong, *lc0, *lc1, *lcfirst, *lcslot;
+};
+
+template <typename XT, typename AT>
+__global__ void __launch_bounds__(256) batched_fold_kernel(const FoldArgs *__restrict__ fa,
+                                                           const AT *const *__restrict__ halos,
+                                                           const AT *const *__restrict__ lparts,
+                                                           XT *const *__restrict__ ys, const int64_t *__restrict__ fpre,
+                                                           int count, int64_t total, int k) {
+    for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        int lo = 0, hi = count;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (fpre[mid] <= q) lo = mid;
+            else hi = mid;
+        }
+        const int m = lo;
+        const int64_t local = q - fpre[m];
+        const int f = static_cast<int>(local / k), c = static_cast<int>(local - static_cast<int64_t>(f) * k);
+        const FoldArgs F = fa[m];
+        const int64_t r = F.frow[f];
+        XT *y = ys[m];
+        AT v = static_cast<AT>(y[r * k + c]);
+        const int hh = F.fhalo[f];
+        if (hh >= 0) v += halos[m][static_cast<int64_t>(hh) * k + c];
+        const int l = F.flong[f];
+        if (l >= 0)
+            for (int ch = F.lc0[l]; ch <= F.lc1[l]; ++ch)
+                v += lparts[m][static_cast<int64_t>(F.lcslot[ch] + (l - F.lcfirst[ch])) * k + c];
+        y[r * k + c] = static_cast<XT>(v);
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+struct BatchCache {
+    std::vector<uint64_t> serial;   // handle serials: a freed handle never matches again
+    std::vector<double> alpha;
+    std::vector<const void *> X;
+    std::vector<void *> Y;
+    int dtype = -1, k = 0;
+    void *args = nullptr, *upre = nullptr, *fa = nullptr, *halos = nullptr, *lparts = nullptr, *ys = nullptr,
+         *fpre = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t capture = nullptr;
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void *p : {args, upre, fa, halos, lparts, ys, fpre})
+            if (p) cudaFree(p);
+        if (capture) cudaStreamDestroy(capture);
+        *this = BatchCache();
+    }
+};
+
+template <typename VT, typename XT, typename AT>
+static SpmvArgs<VT, XT, AT> make_args(const pars3_handle *h, int dtype, double alpha, const void *X, void *Y) {
+    const Layout &L = h->L;
+    const DevLayout &D = h->D;
+    SpmvArgs<VT, XT, AT> a;
+    a.n = h->n;
+    a.T = h->T;
+    a.W = h->W;
+    a.ntiles = h->ntiles;
+    a.nchunks = static_cast<int32_t>(L.lcbeg.size());
+    a.Mh = static_cast<int32_t>(round_up(L.max_tile_half, kAlignHalf));
+    a.hoff = D.hoff;
+    a.hcnt = D.hcnt;
+    a.hrp = D.hrp;
+    a.hcol = D.hcol;
+    a.hcperm = D.hcperm;
+    a.hval = static_cast<const VT *>(D.hval[dtype]);
+    a.hhoff = D.hhoff;
+    a.hhrow = D.hhrow;
+    a.halo = static_cast<AT *>(D.halo);
+    a.sl_off = D.sl_off;
+    a.sl_ent = D.sl_ent;
+    a.sl_meta = D.sl_meta;
+    a.fcol = D.fcol;
+    a.fval = static_cast<const VT *>(D.fval[dtype]);
+    a.lrp = D.lrp;
+    a.lcbeg = D.lcbeg;
+    a.lcend = D.lcend;
+    a.lcfirst = D.lcfirst;
+    a.lcrows = D.lcrows;
+    a.lcslot = D.lcslot;
+    a.lcol = D.lcol;
+    a.lval = static_cast<const VT *>(D.lval[dtype]);
+    a.lpart = static_cast<AT *>(D.lpart);
+    a.x = static_cast<const XT *>(X);
+    a.y = static_cast<XT *>(Y);
+    a.alpha = static_cast<AT>(alpha);
+    a.err = D.err;
+    return a;
+}
+
+template <typename T>
+static int upload_vec(void **dst, const std::vector<T> &v) {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(16, v.size() * sizeof(T)));
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return cuda_status(e);
+}
+
+template <typename VT, typename XT, typename AT, int LPR>
+static int enqueue(BatchCache &C, int count, int64_t total_units, int64_t total_fold, int smem, int k,
+                   cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(batched_kernel<VT, XT, AT, LPR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSmemLimit - static_cast<int>(sizeof(SpmvArgs<VT, XT, AT>)) - 64);
+        if (e != cudaSuccess) return cuda_status(e);
+        configured = true;
+    }
+    const int grid = static_cast<int>(std::min<int64_t>(total_units, 2LL * sm_count()));
+    if (grid > 0)
+        batched_kernel<VT, XT, AT, LPR><<<grid, kBlock, smem, st>>>(
+            static_cast<const SpmvArgs<VT, XT, AT> *>(C.args), static_cast<const int32_t *>(C.upre), count,
+            static_cast<int>(total_units), k);
+    if (total_fold > 0) {
+        const int blocks = static_cast<int>(std::min<int64_t>((total_fold + 255) / 256, 152 * 8));
+        batched_fold_kernel<XT, AT><<<blocks, 256, 0, st>>>(
+            static_cast<const FoldArgs *>(C.fa), static_cast<const AT *const *>(C.halos),
+            static_cast<const AT *const *>(C.lparts), static_cast<XT *const *>(C.ys),
+            static_cast<const int64_t *>(C.fpre), count, total_fold, k);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename VT, typename XT, typename AT>
+static int run_batched(BatchCache &C, pars3_handle *const *hs, int count, int dtype, const double *alpha, int k,
+                       const void *const *X, void *const *Y, bool capture, cudaStream_t st) {
+    bool same = C.dtype == dtype && C.k == k && static_cast<int>(C.serial.size()) == count;
+    for (int m = 0; same && m < count; ++m) same = C.serial[m] == hs[m]->serial;
+    same = same && std::equal(C.alpha.begin(), C.alpha.end(), alpha) &&
+                      std::equal(C.X.begin(), C.X.end(), X) && std::equal(C.Y.begin(), C.Y.end(), Y);
+    std::vector<int32_t> upre(1, 0);
+    std::vector<int64_t> fpre(1, 0);
+    int smem = 0;
+    for (int m = 0; m < count; ++m) {
+        const pars3_handle *h = hs[m];
+        upre.push_back(upre.back() + h->ntiles + static_cast<int32_t>(h->L.lcbeg.size()));
+        fpre.push_back(fpre.back() + static_cast<int64_t>(h->L.fold_row.size()) * k);
+        smem = std::max(smem, k == 1 ? smem_bytes_for(h, dtype) : spmm_smem_bytes(h, dtype));
+    }
+    if (smem + static_cast<int>(sizeof(SpmvArgs<VT, XT, AT>)) + 64 > kSmemLimit) return PARS3_EUNSUPPORTED;
+    if (!same) {
+        C.release();
+        std::vector<SpmvArgs<VT, XT, AT>> args;
+        std::vector<FoldArgs> fa;
+        std::vector<const void *> halos, lparts;
+        std::vector<void *> ys;
+        for (int m = 0; m < count; ++m) {
+            const pars3_handle *h = hs[m];
+            args.push_back(make_args<VT, XT, AT>(h, dtype, alpha[m], X[m], Y[m]));
+            const DevLayout &D = h->D;
+            fa.push_back(FoldArgs{static_cast<int32_t>(h->L.fold_row.size()), D.fold_row, D.fold_halo, D.fold_long,
+                                  D.lc0, D.lc1, D.lcfirst, D.lcslot});
+            halos.push_back(D.halo);
+            lparts.push_back(D.lpart);
+            ys.push_back(Y[m]);
+        }
+        int rc;
+        if ((rc = upload_vec(&C.args, args)) != PARS3_OK) return rc;
+        if ((rc = upload_vec(&C.upre, upre)) != PARS3_OK) return rc;
+        if ((rc = upload_vec(&C.fa, fa)) != PARS3_OK) return rc;
+        if ((rc = upload_vec(&C.halos, halos)) != PARS3_OK) return rc;
+        if ((rc = upload_vec(&C.lparts, lparts)) != PARS3_OK) return rc;
+        if ((rc = upload_vec(&C.ys, ys)) != PARS3_OK) return rc;
+        if ((rc = upload_vec(&C.fpre, fpre)) != PARS3_OK) return rc;
+        for (int m = 0; m < count; ++m) C.serial.push_back(hs[m]->serial);
+        C.alpha.assign(alpha, alpha + count);
+        C.X.assign(X, X + count);
+        C.Y.assign(Y, Y + count);
+        C.dtype = dtype;
+        C.k = k;
+    }
+    auto launch = [&](cudaStream_t s) {
+        if (k <= 2) return enqueue<VT, XT, AT, 2>(C, count, upre.back(), fpre.back(), smem, k, s);
+        if (k <= 4) return enqueue<VT, XT, AT, 4>(C, count, upre.back(), fpre.back(), smem, k, s);
+        if (k <= 8) return enqueue<VT, XT, AT, 8>(C, count, upre.back(), fpre.back(), smem, k, s);
+        if (k <= 16) return enqueue<VT, XT, AT, 16>(C, count, upre.back(), fpre.back(), smem, k, s);
+        return enqueue<VT, XT, AT, 32>(C, count, upre.back(), fpre.back(), smem, k, s);
+    };
+    if (!capture) return launch(st);
+    if (!C.exec) {
+        cudaError_t e = cudaStreamCreateWithFlags(&C.capture, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(C.capture, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return cuda_status(e);
+        const int rc = launch(C.capture);
+        e = cudaStreamEndCapture(C.capture, &C.graph);
+        if (rc != PARS3_OK) return rc;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&C.exec, C.graph, 0);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return cuda_status(cudaGraphLaunch(C.exec, st));
+}
+
+}  // namespace pars3
+
+using namespace pars3;
+
+void pars3_release_batch(pars3_handle *h) {
+    if (h && h->batch_cache) {
+        BatchCache *C = static_cast<BatchCache *>(h->batch_cache);
+        C->release();
+        delete C;
+        h->batch_cache = nullptr;
+    }
+}
+
+extern "C" int pars3_spmm_batched(pars3_handle *const *hs, int32_t count, int32_t dtype, const double *alpha,
+                                  int32_t k, const void *const *X, void *const *Y, int32_t capture, void *stream) {
+    if (!hs || !alpha || !X || !Y || count < 1 || k < 1 || k > 32) return PARS3_EINVAL;
+    if (dtype < 0 || dtype >= kNumDtypes) return PARS3_EINVAL;
+    for (int m = 0; m < count; ++m) {
+        pars3_handle *h = hs[m];
+        if (!h) return PARS3_EINVAL;
+        if (!(h->dtypes & PARS3_DTYPE_BIT(dtype))) return PARS3_EUNSUPPORTED;
+        if (!h->uploaded) return PARS3_ESTATE;
+        if (h->n > 0 && (!X[m] || !Y[m] || X[m] == Y[m])) return PARS3_EINVAL;
+        if (k == 1 && ((reinterpret_cast<uintptr_t>(X[m]) | reinterpret_cast<uintptr_t>(Y[m])) & 15u))
+            return PARS3_EINVAL;
+        const int rc = ensure_scratch(h, k);
+        if (rc != PARS3_OK) return rc;
+    }
+    pars3_handle *owner = hs[0];
+    if (!owner->batch_cache) owner->batch_cache = new (std::nothrow) BatchCache();
+    if (!owner->batch_cache) return PARS3_ENOMEM;
+    BatchCache &C = *static_cast<BatchCache *>(owner->batch_cache);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (dtype) {
+        case PARS3_F64: return run_batched<double, double, double>(C, hs, count, dtype, alpha, k, X, Y, capture != 0, st);
+        case PARS3_F32: return run_batched<float, float, float>(C, hs, count, dtype, alpha, k, X, Y, capture != 0, st);
+        case PARS3_BF16:
+            return run_batched<uint16_t, float, float>(C, hs, count, dtype, alpha, k, X, Y, capture != 0, st);
+        default: return PARS3_EINVAL;
+    }
+}

@@ -173,10 +173,12 @@ extern "C" int pars3_upload(pars3_handle *h, void *stream) {
 }
 
 void pars3_release_graphs(pars3_handle *h);
+void pars3_release_batch(pars3_handle *h);
 
 extern "C" void pars3_free(pars3_handle *h) {
     if (!h) return;
     pars3_release_graphs(h);
+    pars3_release_batch(h);
     release_device(h);
     delete h;
 }

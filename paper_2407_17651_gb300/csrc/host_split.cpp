@@ -23,6 +23,7 @@
 //                 chunks of kLongChunk entries; the partial sums of every
 //                 (chunk, row) pair are folded in chunk order.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -31,6 +32,11 @@
 
 #include "internal.h"
 #include "smem_layout.h"
+
+uint64_t next_handle_serial() {
+    static std::atomic<uint64_t> counter{0};
+    return ++counter;
+}
 
 namespace pars3 {
 

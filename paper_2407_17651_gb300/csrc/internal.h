@@ -91,7 +91,10 @@ struct DevLayout {
 
 }  // namespace pars3
 
+uint64_t next_handle_serial();
+
 struct pars3_handle {
+    uint64_t serial = next_handle_serial();   // unique per handle for the process lifetime
     int32_t n = 0;
     int64_t nnz = 0;
     int32_t T = 0, W = 0, ntiles = 0;
@@ -109,7 +112,8 @@ struct pars3_handle {
     pars3::DevLayout D;
     bool uploaded = false;
     int device = -1;
-    void *graph_cache = nullptr;     // batched SpMM graph (owned, see batched.cu)
+    void *graph_cache = nullptr;     // MRS workspace and loop graphs (owned, see mrs.cu)
+    void *batch_cache = nullptr;     // batched-launch argument table and graph (owned, see batched.cu)
 };
 
 namespace pars3 {
@@ -138,6 +142,10 @@ int launch_spmv_scratch(const pars3_handle *h, int dtype, double alpha, const vo
                         void *lpart, void *stream);
 int launch_permute(const pars3_handle *h, int dtype, int k, const void *src, void *dst, bool inverse,
                    void *stream);
-int prepare_kernels();
+// spmm.cu
+int launch_spmm(const pars3_handle *h, int dtype, double alpha, int k, const void *X, void *Y, void *halo,
+                void *lpart, void *stream);
+int ensure_scratch(pars3_handle *h, int k);
+int spmm_smem_bytes(const pars3_handle *h, int dtype);
 
 }  // namespace pars3

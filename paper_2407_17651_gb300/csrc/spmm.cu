@@ -1,0 +1,179 @@
+// spmm.cu -- Y = (alpha I + S) X for k right-hand sides (X, Y row-major,
+// 1 <= k <= 32) on the split layout of the skew product.
+//
+// Same decomposition as the single product (one block per row tile plus one
+// per long-row chunk, then a fold); the device code is in spmm_device.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "spmm_device.cuh"
+
+namespace pars3 {
+
+template <typename VT, typename XT, typename AT, int LPR>
+__global__ void __launch_bounds__(kBlock, 2) spmm_kernel(const SpmvArgs<VT, XT, AT> a, int k) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (static_cast<int>(blockIdx.x) < a.ntiles) spmm_tile<VT, XT, AT, LPR>(a, k, blockIdx.x, smem);
+    else spmm_long<VT, XT, AT, LPR>(a, k, blockIdx.x - a.ntiles);
+}
+
+// y[row, c] += halo sum + long-row partial sums (chunk order), one thread per
+// (receiving row, column)
+template <typename XT, typename AT>
+__global__ void __launch_bounds__(256) fold_spmm_kernel(int nitems, int k, const int32_t *__restrict__ frow,
+                                                        const int32_t *__restrict__ fhalo,
+                                                        const int32_t *__restrict__ flong,
+                                                        const AT *__restrict__ halo, const int32_t *__restrict__ lc0,
+                                                        const int32_t *__restrict__ lc1,
+                                                        const int32_t *__restrict__ lcfirst,
+                                                        const int32_t *__restrict__ lcslot,
+                                                        const AT *__restrict__ lpart, XT *__restrict__ y) {
+    const int64_t total = static_cast<int64_t>(nitems) * k;
+    for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int f = static_cast<int>(q / k), c = static_cast<int>(q - static_cast<int64_t>(f) * k);
+        const int64_t r = frow[f];
+        AT v = static_cast<AT>(y[r * k + c]);
+        const int hi = fhalo[f];
+        if (hi >= 0) v += halo[static_cast<int64_t>(hi) * k + c];
+        const int l = flong[f];
+        if (l >= 0)
+            for (int ch = lc0[l]; ch <= lc1[l]; ++ch)
+                v += lpart[static_cast<int64_t>(lcslot[ch] + (l - lcfirst[ch])) * k + c];
+        y[r * k + c] = static_cast<XT>(v);
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+int spmm_smem_bytes(const pars3_handle *h, int dtype) {
+    uint32_t vsz, xsz, asz;
+    dtype_sizes(dtype, &vsz, &xsz, &asz);
+    return static_cast<int>(
+        spmm_layout(h->T, h->W, static_cast<uint32_t>(round_up(h->L.max_tile_half, kAlignHalf)), vsz).total);
+}
+
+template <typename VT, typename XT, typename AT, int LPR>
+static int launch_spmm_lpr(const pars3_handle *h, int dtype, double alpha, int k, const void *X, void *Y,
+                           void *halo, void *lpart, cudaStream_t st) {
+    const Layout &L = h->L;
+    const DevLayout &D = h->D;
+    SpmvArgs<VT, XT, AT> a;
+    a.n = h->n;
+    a.T = h->T;
+    a.W = h->W;
+    a.ntiles = h->ntiles;
+    a.nchunks = static_cast<int32_t>(L.lcbeg.size());
+    a.Mh = static_cast<int32_t>(round_up(L.max_tile_half, kAlignHalf));
+    a.hoff = D.hoff;
+    a.hcnt = D.hcnt;
+    a.hrp = D.hrp;
+    a.hcol = D.hcol;
+    a.hcperm = D.hcperm;
+    a.hval = static_cast<const VT *>(D.hval[dtype]);
+    a.hhoff = D.hhoff;
+    a.hhrow = D.hhrow;
+    a.halo = static_cast<AT *>(halo);
+    a.sl_off = D.sl_off;
+    a.sl_ent = D.sl_ent;
+    a.sl_meta = D.sl_meta;
+    a.fcol = D.fcol;
+    a.fval = static_cast<const VT *>(D.fval[dtype]);
+    a.lrp = D.lrp;
+    a.lcbeg = D.lcbeg;
+    a.lcend = D.lcend;
+    a.lcfirst = D.lcfirst;
+    a.lcrows = D.lcrows;
+    a.lcslot = D.lcslot;
+    a.lcol = D.lcol;
+    a.lval = static_cast<const VT *>(D.lval[dtype]);
+    a.lpart = static_cast<AT *>(lpart);
+    a.x = static_cast<const XT *>(X);
+    a.y = static_cast<XT *>(Y);
+    a.alpha = static_cast<AT>(alpha);
+    a.err = D.err;
+    const int smem = spmm_smem_bytes(h, dtype);
+    static std::atomic<int> configured{0};
+    if (!configured.load()) {
+        cudaError_t e = cudaFuncSetAttribute(spmm_kernel<VT, XT, AT, LPR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+        if (e != cudaSuccess) return cuda_status(e);
+        configured.store(1);
+    }
+    const int grid = h->ntiles + a.nchunks;
+    if (grid > 0) spmm_kernel<VT, XT, AT, LPR><<<grid, kBlock, smem, st>>>(a, k);
+    const int nf = static_cast<int>(L.fold_row.size());
+    if (nf > 0) {
+        const int64_t total = static_cast<int64_t>(nf) * k;
+        const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 8));
+        fold_spmm_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, k, D.fold_row, D.fold_halo, D.fold_long,
+                                                         static_cast<const AT *>(halo), D.lc0, D.lc1, D.lcfirst,
+                                                         D.lcslot, static_cast<const AT *>(lpart),
+                                                         static_cast<XT *>(Y));
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename VT, typename XT, typename AT>
+static int launch_spmm_typed(const pars3_handle *h, int dtype, double alpha, int k, const void *X, void *Y,
+                             void *halo, void *lpart, cudaStream_t st) {
+    if (k <= 2) return launch_spmm_lpr<VT, XT, AT, 2>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+    if (k <= 4) return launch_spmm_lpr<VT, XT, AT, 4>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+    if (k <= 8) return launch_spmm_lpr<VT, XT, AT, 8>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+    if (k <= 16) return launch_spmm_lpr<VT, XT, AT, 16>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+    return launch_spmm_lpr<VT, XT, AT, 32>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+}
+
+int launch_spmm(const pars3_handle *h, int dtype, double alpha, int k, const void *X, void *Y, void *halo,
+                void *lpart, void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (dtype) {
+        case PARS3_F64: return launch_spmm_typed<double, double, double>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+        case PARS3_F32: return launch_spmm_typed<float, float, float>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+        case PARS3_BF16: return launch_spmm_typed<uint16_t, float, float>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+        default: return PARS3_EINVAL;
+    }
+}
+
+// Scratch for k right-hand sides: grown (and kept) on the first call that
+// needs more than the handle holds.
+int ensure_scratch(pars3_handle *h, int k) {
+    DevLayout &D = h->D;
+    if (D.scratch_k >= k) return PARS3_OK;
+    void *halo = nullptr, *lpart = nullptr;
+    cudaError_t e = cudaMalloc(&halo, std::max<size_t>(16, h->L.hhrow.size() * 8ull * k));
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMalloc(&lpart, std::max<size_t>(16, static_cast<size_t>(h->L.nslots) * 8ull * k));
+    if (e != cudaSuccess) {
+        cudaFree(halo);
+        return cuda_status(e);
+    }
+    D.owned.push_back(halo);
+    D.owned.push_back(lpart);
+    D.halo = halo;
+    D.lpart = lpart;
+    D.scratch_k = k;
+    return PARS3_OK;
+}
+
+}  // namespace pars3
+
+using namespace pars3;
+
+extern "C" int pars3_spmm(const pars3_handle *hc, int32_t dtype, double alpha, int32_t k, const void *X, void *Y,
+                          void *stream) {
+    pars3_handle *h = const_cast<pars3_handle *>(hc);
+    if (!h || k < 1 || k > 32) return PARS3_EINVAL;
+    if (dtype < 0 || dtype >= kNumDtypes) return PARS3_EINVAL;
+    if (!(h->dtypes & PARS3_DTYPE_BIT(dtype))) return PARS3_EUNSUPPORTED;
+    if (!h->uploaded) return PARS3_ESTATE;
+    if (h->n == 0) return PARS3_OK;
+    if (!X || !Y || X == Y) return PARS3_EINVAL;
+    if (k == 1) return pars3_spmv(h, dtype, alpha, X, Y, stream);
+    int rc = ensure_scratch(h, k);
+    if (rc != PARS3_OK) return rc;
+    if (spmm_smem_bytes(h, dtype) > kSmemLimit) return PARS3_EUNSUPPORTED;
+    return launch_spmm(h, dtype, alpha, k, X, Y, h->D.halo, h->D.lpart, stream);
+}

@@ -313,6 +313,7 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     }
     mbar_wait_bounded(mbar, 0, a.err);
     __syncthreads();
+    if (tid == 0) mbar_inval(mbar);
 
     double *red = reinterpret_cast<double *>(smem + L.red);
     if (hm == 0) {
@@ -397,6 +398,7 @@ __device__ __forceinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c,
     __syncthreads();
     mbar_wait_bounded(mbar, 0, a.err);
     __syncthreads();
+    if (tid == 0) mbar_inval(mbar);
     const int shift = beg - abeg;
     const int warp = tid >> 5, nw = P >> 5;
     for (int u = warp; u < nrc; u += nw) {
