@@ -51,9 +51,10 @@ def measured_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling (200 ms) during the timed region."""
+    """nvidia-smi sampling (100 ms); only samples stamped inside the timed
+    region [mark_begin, mark_end] are summarised."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -61,6 +62,7 @@ class Clocks:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t_begin = self.t_end = None
 
     def start(self):
         try:
@@ -68,9 +70,19 @@ class Clocks:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()   # wait for the sampler's first line (up to 5 s)
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.05)
+
+    def mark_begin(self):
+        self.t_begin = time.time()
+
+    def mark_end(self):
+        self.t_end = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -80,18 +92,23 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        import datetime
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [c.strip() for c in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                smv, mxv = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+            if self.t_begin is not None and not (self.t_begin - 0.05 <= ts <= (self.t_end or ts) + 0.05):
+                continue
+            sm.append(smv)
+            mx.append(mxv)
+            for nm, v in zip(names, f[6:10]):
                 if v.lower() == "active":
                     reasons.add(nm)
         os.unlink(self.path)
@@ -253,7 +270,7 @@ def traffic_from_profile(kernel_hash: str, launch_units: float):
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("spmv.cu", "devcommon.cuh", "smem_layout.h"):
+    for f in ("spmv_kernels.cuh", "spmv.cu", "devcommon.cuh", "smem_layout.h", "host_split.cpp", "internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2407_17651_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -261,7 +278,7 @@ def kernel_source_hash() -> str:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg1")
@@ -332,10 +349,12 @@ def main():
     clocks.start()
     barrier(ws)
     torch.cuda.synchronize()
+    clocks.mark_begin()
     for s in range(args.steps):
         flush.zero_()
         step(evs[s])
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier(ws)
     clk = clocks.stop()
     P.pars3_check(h)
