@@ -160,8 +160,125 @@ def workload(name: str):
     return A, alpha, x, desc
 
 
-# cut points (T, W) per workload, from timing sweeps on a GB300
-TUNED = {"cfg0": (256, 128), "cfg1": (2048, 32), "cfg2": (2048, 32)}
+def time_products(P, torch, h, dt, alpha, xp, y, flush, reps=50, groups=5):
+    """Median microseconds per product over `groups` groups of `reps`
+    products, L2 flushed before every group."""
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        P.pars3_spmv(h, dt, alpha, xp, y, st)
+    ts = []
+    for _ in range(groups):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            P.pars3_spmv(h, dt, alpha, xp, y, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e3 / reps)
+    return statistics.median(ts)
+
+
+def extra_section(args, peak):
+    """The other workloads, each reported beside the headline: a
+    band-friendly 2D grid (2048 x 1024, RCM bandwidth about 1024: the
+    half-storage middle band holds the matrix), the R-MAT matrix in FP64 and
+    FP32 (cut points from pars3_autotune), and the batched workload (64
+    uneven grids, k in {1, 4, 16, 32}, FP32 and FP64, one persistent launch
+    replayed from a CUDA graph, cut points from pars3_autotune per matrix)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2407_17651_gb300 import pars3 as P
+    out = {}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    both = P.dtype_bit(P.F64) | P.dtype_bit(P.F32)
+
+    def single(name, A, alpha, x, desc):
+        t0 = time.perf_counter()
+        perm, bw0, bw1 = P.pars3_reorder(A.n, A.rowptr, A.col)
+        t_rcm = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=P.F64, k=1, dtypes=both)
+        t_tune = time.perf_counter() - t0
+        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=tune["T"], W=tune["W"], dtypes=both)
+        P.pars3_upload(h)
+        info = P.pars3_info_get(h)
+        row = {"workload": desc, "n": A.n, "nnz_stored": A.nnz, "alpha": alpha, "rcm_bandwidth": bw1,
+               "T": info["T"], "W": info["W"], "half_entries": info["half_entries"],
+               "full_entries": info["full_entries"], "long_entries": info["long_entries"],
+               "rcm_s": t_rcm, "autotune_s": t_tune}
+        for dt, nm, vt, sv, sx in ((P.F64, "f64", torch.float64, 8, 8), (P.F32, "f32", torch.float32, 4, 4)):
+            xp = torch.from_numpy(x[perm]).to("cuda", vt)
+            y = torch.empty_like(xp)
+            us = time_products(P, torch, h, dt, alpha, xp, y, flush)
+            P.pars3_check(h)
+            ub = alg_bytes(A.n, A.nnz, sv, sx)
+            lb = info["bytes_per_spmv"][dt]
+            row[nm] = {"us": us, "GBps": ub / us / 1e3, "frac_of_peak": ub / us / 1e3 / peak,
+                       "layout_GBps": lb / us / 1e3, "GFLOPs": (4 * A.nnz + (2 * A.n if alpha else 0)) / us / 1e3}
+        h.close()
+        out[name] = row
+
+    t0 = time.perf_counter()
+    A = W.grid((2048, 1024), "normal", W.SEED_BASE + 5, name="grid2d_2048x1024")
+    single("grid2d", A, 0.5, W.vector("uniform", A.n, W.SEED_BASE + 5),
+           "grid2d 2048x1024 (band-friendly: RCM bandwidth ~1024), N(0,1), alpha=0.5")
+    out["grid2d"]["section_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    A, alpha, x = W.config2()
+    single("cfg2", A, alpha, x, "R-MAT scale 22, 20M stored, U(-1,1), alpha=0, cut points autotuned")
+    out["cfg2"]["section_s"] = time.perf_counter() - t0
+    del A, x
+
+    # batched uneven workload
+    t0 = time.perf_counter()
+    shapes = W.config4_shapes()
+    hs, perms, ns, nnzs, cuts = [], [], [], [], []
+    for m, shp in enumerate(shapes):
+        A = W.config4_matrix(m, shp)
+        perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
+        tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=P.F32, k=4, dtypes=both)
+        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=tune["T"], W=tune["W"], dtypes=both)
+        P.pars3_upload(h)
+        hs.append(h); perms.append(perm); ns.append(A.n); nnzs.append(A.nnz); cuts.append((tune["T"], tune["W"]))
+    t_prep = time.perf_counter() - t0
+    rows = {}
+    st = torch.cuda.current_stream()
+    for dt, nm, vt, sv, sx in ((P.F32, "f32", torch.float32, 4, 4), (P.F64, "f64", torch.float64, 8, 8)):
+        for k in W.CONFIG4_KS:
+            Xs, Ys = [], []
+            for m, h in enumerate(hs):
+                X = W.config4_rhs(ns[m], k, m)[perms[m]]
+                X = X[:, 0] if k == 1 else X
+                Xs.append(torch.from_numpy(np.ascontiguousarray(X)).to("cuda", vt))
+                Ys.append(torch.empty_like(Xs[-1]))
+            alphas = [1.0] * len(hs)
+            for _ in range(3):
+                P.pars3_spmm_batched(hs, dt, alphas, Xs, Ys, capture=True, stream=st)
+            ts = []
+            for _ in range(5):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(10):
+                    P.pars3_spmm_batched(hs, dt, alphas, Xs, Ys, capture=True, stream=st)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e3 / 10)
+            us = statistics.median(ts)
+            ub = sum(alg_bytes(n, z, sv, sx, k) for n, z in zip(ns, nnzs))
+            rows[f"{nm}_k{k}"] = {"us": us, "GBps": ub / us / 1e3, "frac_of_peak": ub / us / 1e3 / peak,
+                                  "GFLOPs": sum(4 * z * k + 2 * n * k for n, z in zip(ns, nnzs)) / us / 1e3}
+            del Xs, Ys
+    for h in hs:
+        h.close()
+    out["cfg4"] = {"workload": "64 uneven grids (n log-uniform in [1e4, 5e5], 2D/3D), N(0,1), alpha=1, "
+                               "one persistent launch + fold per call, replayed from a CUDA graph",
+                   "sum_n": sum(ns), "sum_nnz_stored": sum(nnzs), "prep_s": t_prep,
+                   "cut_points": sorted(set(cuts)), "results": rows,
+                   "section_s": time.perf_counter() - t0}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -283,13 +400,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg1")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
-    ap.add_argument("--T", type=int, default=-1)
-    ap.add_argument("--W", type=int, default=-1)
+    ap.add_argument("--T", type=int, default=-1, help="tile rows (default: pars3_autotune)")
+    ap.add_argument("--W", type=int, default=-1, help="middle bandwidth (with --T)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-spmvs", type=int, default=10)
     ap.add_argument("--mrs", default="1,0.1,0.01", help="alphas of the MRS comparison ('' to skip)")
     ap.add_argument("--mrs-iters", type=int, default=60000)
+    ap.add_argument("--extra", type=int, default=1, help="1: also report the band-friendly grid, R-MAT and batched workloads")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -311,12 +429,17 @@ def main():
     sx = 8 if dt == P.F64 else 4
 
     A, alpha, x, desc = workload(args.workload)
-    T, Wc = TUNED.get(args.workload, (0, 0))
-    if args.T >= 0:
-        T, Wc = args.T, args.W
     t0 = time.perf_counter()
     perm, bw0, bw1 = P.pars3_reorder(A.n, A.rowptr, A.col)
     t_rcm = time.perf_counter() - t0
+    t_tune = None
+    if args.T >= 0:
+        T, Wc = args.T, args.W
+    else:   # cut points from the autotuner (untimed preprocessing)
+        t0 = time.perf_counter()
+        tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=dt, k=1, dtypes=P.dtype_bit(dt))
+        t_tune = time.perf_counter() - t0
+        T, Wc = tune["T"], tune["W"]
     t0 = time.perf_counter()
     h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=Wc, dtypes=P.dtype_bit(dt))
     t_split = time.perf_counter() - t0
@@ -391,6 +514,7 @@ def main():
     if args.mrs and args.workload == "cfg1":
         mrs = mrs_section(A, perm, info["T"], info["W"], [float(a) for a in args.mrs.split(",")], args.mrs_iters)
     launches_per_spmv = 1 + (1 if info["halo_targets"] + info["long_rows"] > 0 else 0)
+    extra = extra_section(args, peak) if (args.extra and rank == 0) else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
@@ -416,7 +540,8 @@ def main():
             "gpu_launches": launches_per_spmv * REPEATS * args.steps,
             "mrs": mrs,
             "clocks": clk,
-            "preprocess_s": {"rcm": t_rcm, "split": t_split, "upload": t_up},
+            "preprocess_s": {"rcm": t_rcm, "autotune": t_tune, "split": t_split, "upload": t_up},
+            "other_workloads": extra,
             "spmv_us": {"mean": 1e6 * avg_spmv_s, "median": 1e6 * statistics.median(spmv_ms) / 1e3,
                         "min": 1e3 * min(spmv_ms)},
             "kernel_source_hash": khash,

@@ -1,0 +1,165 @@
+// autotune.cu -- pars3_autotune: choose the cut points (T, W) of the 3-way
+// split (Sec. 3.1.2: the tile a thread block owns and the middle bandwidth)
+// by timing pars3_spmm on the current device.
+//
+// The search is coordinate-wise over powers of two, so that a matrix is
+// split at most about ten times:
+//   1. W = 32, T in {512, 1024, 2048, 4096}            -> T1
+//   2. T = T1, W in {64, ..., min(T1, w_max)}          -> W2
+//   3. W = W2, T in {T1 / 2, 2 T1} not yet timed       -> best
+// w_max is the reordered bandwidth rounded up to a power of two, capped like
+// the default rule (1024 with F64 packed, else 2048): a middle band wider
+// than the matrix's band holds no more entries.  A candidate replaces the
+// incumbent only when it is at least 2 % faster, so near-ties keep the
+// smaller band and the earlier tile size.  Candidates the layout cannot
+// hold (shared memory) are skipped.  The matrix is reordered and sorted
+// once; each candidate re-runs only the cut-dependent stages of the split,
+// is uploaded, timed (3 warm-up products, then the median of 3 groups of 8
+// products measured with CUDA events) and freed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+using namespace pars3;
+
+namespace {
+
+struct Timer {
+    int32_t n = 0, dtype = 0, k = 1;
+    const pars3_handle *tmpl = nullptr;   // reordered matrix; candidates re-cut it
+    void *X = nullptr, *Y = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+
+    // microseconds per product, or +inf when the candidate cannot be laid out
+    int time(int32_t T, int32_t W, double *us) {
+        *us = INFINITY;
+        pars3_handle *h = nullptr;
+        int rc = split_recut(tmpl, T, W, &h);
+        if (rc == PARS3_EUNSUPPORTED) return PARS3_OK;
+        if (rc != PARS3_OK) return rc;
+        rc = pars3_upload(h, st);
+        if (rc == PARS3_ENOMEM) {
+            pars3_free(h);
+            return PARS3_OK;
+        }
+        std::vector<float> groups;
+        for (int it = 0; rc == PARS3_OK && it < 3; ++it) rc = pars3_spmm(h, dtype, 1.0, k, X, Y, st);
+        for (int g = 0; rc == PARS3_OK && g < 3; ++g) {
+            cudaEventRecord(e0, st);
+            for (int it = 0; rc == PARS3_OK && it < 8; ++it) rc = pars3_spmm(h, dtype, 1.0, k, X, Y, st);
+            cudaEventRecord(e1, st);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) rc = cuda_status(e);
+            float ms = 0.f;
+            if (rc == PARS3_OK) {
+                e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) rc = cuda_status(e);
+            }
+            groups.push_back(ms);
+        }
+        if (rc == PARS3_OK) rc = pars3_check(h, st);
+        pars3_free(h);
+        if (rc == PARS3_EUNSUPPORTED) return PARS3_OK;
+        if (rc != PARS3_OK) return rc;
+        std::sort(groups.begin(), groups.end());
+        *us = 1e3 * groups[1] / 8.0;
+        return PARS3_OK;
+    }
+};
+
+int32_t pow2_ceil(int64_t v) {
+    int32_t p = 32;
+    while (p < v && p < (1 << 15)) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+extern "C" int pars3_autotune(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                              const int32_t *perm, const pars3_split_params *base, int32_t dtype, int32_t k,
+                              pars3_split_params *best, double *best_us) {
+    if (!best || n < 0 || !rowptr || k < 1 || k > 32 || dtype < 0 || dtype >= kNumDtypes) return PARS3_EINVAL;
+    int rc = validate_lower(n, rowptr, col);
+    if (rc != PARS3_OK) return rc;
+    Timer tm;
+    tm.n = n;
+    tm.dtype = dtype;
+    tm.k = k;
+    pars3_split_params b0{};
+    if (base) b0 = *base;
+    if (b0.dtypes == 0) b0.dtypes = PARS3_DTYPE_BIT(PARS3_F64);
+    b0.dtypes |= PARS3_DTYPE_BIT(dtype);
+    *best = b0;
+    if (best_us) *best_us = 0.0;
+    if (n == 0) {
+        best->T = 1024;
+        best->W = 32;
+        return PARS3_OK;
+    }
+
+    const int32_t wcap = (b0.dtypes & PARS3_DTYPE_BIT(PARS3_F64)) ? 1024 : 2048;
+    pars3_handle *tmpl = nullptr;
+    {
+        pars3_split_params p0 = b0;
+        p0.T = 1024;
+        p0.W = 32;
+        rc = pars3_split(n, rowptr, col, val, perm, &p0, &tmpl);
+        if (rc != PARS3_OK) return rc;
+    }
+    tm.tmpl = tmpl;
+    const int32_t wmax = std::min(pow2_ceil(tmpl->bw), wcap);
+
+    const size_t vsz = dtype == PARS3_F64 ? 8 : 4;
+    const size_t bytes = std::max<size_t>(16, static_cast<size_t>(n) * k * vsz);
+    cudaError_t e = cudaStreamCreateWithFlags(&tm.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&tm.X, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&tm.Y, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tm.X, 0, bytes, tm.st);
+    if (e == cudaSuccess) e = cudaEventCreate(&tm.e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&tm.e1);
+    rc = cuda_status(e);
+
+    std::vector<std::pair<int32_t, int32_t>> tried;
+    int32_t bT = 0, bW = 0;
+    double bus = INFINITY;
+    auto consider = [&](int32_t T, int32_t W) {
+        if (rc != PARS3_OK || W > T || T > 32768) return;
+        for (auto &c : tried)
+            if (c.first == T && c.second == W) return;
+        tried.emplace_back(T, W);
+        double us;
+        rc = tm.time(T, W, &us);
+        if (rc == PARS3_OK && us < 0.98 * bus) {
+            bus = us;
+            bT = T;
+            bW = W;
+        }
+    };
+    for (int32_t T : {512, 1024, 2048, 4096}) consider(T, 32);
+    const int32_t T1 = bT;
+    if (T1 > 0)
+        for (int32_t W = 64; W <= std::min(T1, wmax); W <<= 1) consider(T1, W);
+    if (T1 > 0) {
+        const int32_t W2 = bW;
+        consider(std::max(T1 / 2, W2), W2);
+        consider(T1 * 2, W2);
+    }
+
+    if (tm.e0) cudaEventDestroy(tm.e0);
+    if (tm.e1) cudaEventDestroy(tm.e1);
+    if (tm.X) cudaFree(tm.X);
+    if (tm.Y) cudaFree(tm.Y);
+    if (tm.st) cudaStreamDestroy(tm.st);
+    pars3_free(tmpl);
+    if (rc != PARS3_OK) return rc;
+    if (bT == 0) return PARS3_EUNSUPPORTED;
+    best->T = bT;
+    best->W = bW;
+    if (best_us) *best_us = bus;
+    return PARS3_OK;
+}

@@ -71,9 +71,11 @@ static void counting_sort(std::vector<int32_t> &idx, int64_t nkeys, Key key) {
     idx.swap(out);
 }
 
-static int canonical_split(pars3_handle *h, const int32_t *rowptr, const int32_t *col,
-                           const double *val) {
-    const int32_t n = h->n, T = h->T, W = h->W;
+// Stage 1 of the canonical split (independent of the cut points): apply
+// the permutation, re-triangularize (an entry whose orientation flips is
+// stored negated) and sort by (row, col) into h->rowptr/col/val.
+static void canonical_reorder(pars3_handle *h, const int32_t *rowptr, const int32_t *col, const double *val) {
+    const int32_t n = h->n;
     const int64_t nnz = h->nnz;
     std::vector<int32_t> pinv(n);
     for (int32_t k = 0; k < n; ++k) pinv[h->perm[k]] = k;
@@ -87,24 +89,37 @@ static int canonical_split(pars3_handle *h, const int32_t *rowptr, const int32_t
             else       { r[e] = b; c[e] = a; v[e] = -val[k]; }
         }
     }
-    // sort by (row, col): stable by col, then stable by row
-    std::vector<int32_t> ord(nnz);
-    for (int64_t e = 0; e < nnz; ++e) ord[e] = static_cast<int32_t>(e);
-    counting_sort(ord, n, [&](int32_t e) { return c[e]; });
-    counting_sort(ord, n, [&](int32_t e) { return r[e]; });
+    // sort by (row, col): bucket by row (one counting pass), then sort each
+    // row's columns (short segments, no duplicates after validation)
     h->rowptr.assign(static_cast<size_t>(n) + 1, 0);
+    for (int64_t e = 0; e < nnz; ++e) ++h->rowptr[r[e] + 1];
+    for (int32_t i = 0; i < n; ++i) h->rowptr[i + 1] += h->rowptr[i];
     h->col.resize(nnz);
     h->val.resize(nnz);
-    std::vector<int32_t> row_of(nnz);
-    for (int64_t q = 0; q < nnz; ++q) {
-        int32_t e = ord[q];
-        h->col[q] = c[e];
-        h->val[q] = v[e];
-        row_of[q] = r[e];
-        ++h->rowptr[r[e] + 1];
+    {
+        // (col, source position) pairs bucketed by row, then each row sorted
+        std::vector<std::pair<int32_t, int32_t>> pr(nnz);
+        std::vector<int32_t> fill(h->rowptr.begin(), h->rowptr.end() - 1);
+        for (int64_t e = 0; e < nnz; ++e) pr[fill[r[e]]++] = {c[e], static_cast<int32_t>(e)};
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t b = h->rowptr[i], en = h->rowptr[i + 1];
+            if (en - b > 1) std::sort(pr.begin() + b, pr.begin() + en);
+        }
+        for (int64_t q = 0; q < nnz; ++q) {
+            h->col[q] = pr[q].first;
+            h->val[q] = v[pr[q].second];
+        }
     }
-    for (int32_t i = 0; i < n; ++i) h->rowptr[i + 1] += h->rowptr[i];
-    { std::vector<int32_t>().swap(r); std::vector<int32_t>().swap(c); std::vector<double>().swap(v); }
+}
+
+// Stage 2 (for the cut points h->T, h->W): class of every stored entry,
+// per-tile middle lists in (col, row) order, outer lists in CSR and CSC order.
+static void canonical_classify(pars3_handle *h) {
+    const int32_t n = h->n, T = h->T, W = h->W;
+    const int64_t nnz = h->nnz;
+    std::vector<int32_t> row_of(nnz);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t e = h->rowptr[i]; e < h->rowptr[i + 1]; ++e) row_of[e] = i;
     // classify
     h->cls.resize(nnz);
     h->counts[0] = h->counts[1] = h->counts[2] = 0;
@@ -115,27 +130,31 @@ static int canonical_split(pars3_handle *h, const int32_t *rowptr, const int32_t
         h->cls[e] = k;
         ++h->counts[k];
     }
-    // per-tile middle lists in (col, row) order: CSR order is (row, col);
-    // stable by col gives (col, row), stable by tile gives (tile, col, row)
+    // per-tile middle lists in (col, row) order: the middle entries of a tile
+    // are a run of CSR positions in (row, col) order; sort each run by
+    // (col, row) (positions increase with row inside a column)
     std::vector<int32_t> mid, outer;
     mid.reserve(h->counts[0] + h->counts[1]);
     outer.reserve(h->counts[2]);
-    for (int64_t e = 0; e < nnz; ++e) {
-        if (h->cls[e] != 2) mid.push_back(static_cast<int32_t>(e));
-        else outer.push_back(static_cast<int32_t>(e));
-    }
-    counting_sort(mid, n, [&](int32_t e) { return h->col[e]; });
-    counting_sort(mid, h->ntiles, [&](int32_t e) { return row_of[e] / T; });
     h->tile_ptr.assign(static_cast<size_t>(h->ntiles) + 1, 0);
-    for (int32_t e : mid) ++h->tile_ptr[row_of[e] / T + 1];
-    for (int32_t t = 0; t < h->ntiles; ++t) h->tile_ptr[t + 1] += h->tile_ptr[t];
+    for (int32_t t = 0; t < h->ntiles; ++t) {
+        const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+        const size_t m0 = mid.size();
+        for (int32_t e = h->rowptr[r0]; e < h->rowptr[r1]; ++e) {
+            if (h->cls[e] != 2) mid.push_back(e);
+            else outer.push_back(e);
+        }
+        std::sort(mid.begin() + m0, mid.end(), [&](int32_t x, int32_t y) {
+            return h->col[x] != h->col[y] ? h->col[x] < h->col[y] : x < y;
+        });
+        h->tile_ptr[t + 1] = static_cast<int32_t>(mid.size());
+    }
     h->tile_list.swap(mid);
     h->outer_csr = outer;
     counting_sort(outer, n, [&](int32_t e) { return h->col[e]; });
     h->outer_csc.swap(outer);
     h->bw = 0;
     for (int64_t e = 0; e < nnz; ++e) h->bw = std::max<int64_t>(h->bw, row_of[e] - h->col[e]);
-    return PARS3_OK;
 }
 
 void dtype_sizes(int dtype, uint32_t *vsz, uint32_t *xsz, uint32_t *asz) {
@@ -474,6 +493,41 @@ int64_t model_bytes(const pars3_handle *h, int dtype) {
 
 }  // namespace pars3
 
+namespace pars3 {
+
+// A handle with the same reordered matrix as src (perm, band CSR, packed
+// precisions, long-row threshold) and the cut points (T, W): only the
+// cut-dependent stages run.  Used by the autotuner.
+int split_recut(const pars3_handle *src, int32_t T, int32_t W, pars3_handle **out) {
+    *out = nullptr;
+    if (!is_pow2(T) || !is_pow2(W) || W < 32 || W > T || T > 32768) return PARS3_EINVAL;
+    pars3_handle *h = nullptr;
+    try {
+        h = new pars3_handle();
+        h->n = src->n;
+        h->nnz = src->nnz;
+        h->dtypes = src->dtypes;
+        h->long_row = src->long_row;
+        h->perm = src->perm;
+        h->rowptr = src->rowptr;
+        h->col = src->col;
+        h->val = src->val;
+        h->T = T;
+        h->W = W;
+        h->ntiles = h->n > 0 ? (h->n + T - 1) / T : 0;
+        canonical_classify(h);
+        const int rc = build_layout(h);
+        if (rc != PARS3_OK) { delete h; return rc; }
+    } catch (const std::bad_alloc &) {
+        delete h;
+        return PARS3_ENOMEM;
+    }
+    *out = h;
+    return PARS3_OK;
+}
+
+}  // namespace pars3
+
 using namespace pars3;
 
 extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
@@ -523,8 +577,9 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
         h->W = prm.W;
         h->ntiles = n > 0 ? (n + prm.T - 1) / prm.T : 0;
         h->long_row = prm.long_row > 0 ? prm.long_row : 0;
-        rc = canonical_split(h, rowptr, col, val);
-        if (rc == PARS3_OK) rc = build_layout(h);
+        canonical_reorder(h, rowptr, col, val);
+        canonical_classify(h);
+        rc = build_layout(h);
         if (rc != PARS3_OK) { delete h; return rc; }
     } catch (const std::bad_alloc &) {
         delete h;

@@ -15,7 +15,7 @@ constexpr int kAlignFull = 16;         // full-path tile segments: 64 B for int3
 constexpr int kBlock = 512;            // threads of the tile kernel (one block per row tile or long chunk)
 constexpr int kLongChunk = 4096;       // entries per long-row chunk (one block each)
 constexpr int kLongMin = 256;          // shortest row moved to the long path to balance tiles
-constexpr int kSellMax = 32;           // longer full-path rows go to the long path
+constexpr int kSellMax = 128;          // longer full-path rows go to the long path
 constexpr int kSlice = 32;             // rows per sliced-ELL slice (one warp)
 constexpr int kSmemLimit = 227 * 1024; // opt-in shared memory per block on sm_100/sm_103
 
@@ -123,6 +123,7 @@ int validate_lower(int32_t n, const int32_t *rowptr, const int32_t *col);
 int64_t bandwidth(int32_t n, const int32_t *rowptr, const int32_t *col, const int32_t *pinv);
 
 // host_split.cpp
+int split_recut(const pars3_handle *src, int32_t T, int32_t W, pars3_handle **out);
 void auto_cut(int64_t bw, int32_t w_min, int32_t w_cap, int32_t t_min, int32_t *T, int32_t *W);
 int build_layout(pars3_handle *h);
 int smem_bytes_for(const pars3_handle *h, int dtype);

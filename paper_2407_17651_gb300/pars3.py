@@ -312,17 +312,19 @@ def pars3_mrs(h: Handle, alpha: float, b, x, rtol: float = 1e-10, max_iter: int 
     return r.as_dict()
 
 
-def pars3_autotune(n: int, rowptr, col, val, perm, dtype: int = F64, k: int = 1, dtypes: int = 0,
-                   T: int = 0, W: int = 0):
+def pars3_autotune(n: int, rowptr, col, val, perm=None, dtype: int = F64, k: int = 1, dtypes: int = 0,
+                   T: int = 0, W: int = 0, long_row: int = 0):
+    """Cut points (T, W) chosen by timing pars3_spmm with k right-hand sides
+    on the current device; returns dict(T, W, dtypes, long_row, us)."""
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     ci = np.ascontiguousarray(col, dtype=np.int32)
     v = np.ascontiguousarray(val, dtype=np.float64)
-    pm = np.ascontiguousarray(perm, dtype=np.int32)
-    base = pars3_split_params(T=T, W=W, dtypes=dtypes)
+    pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+    base = pars3_split_params(T=T, W=W, dtypes=dtypes, long_row=long_row)
     best = pars3_split_params()
     us = C.c_double()
-    _chk(lib().pars3_autotune(int(n), _p(rp), _p(ci), _p(v), _p(pm), C.byref(base), int(dtype), int(k),
-                              C.byref(best), C.byref(us)), "pars3_autotune")
+    _chk(lib().pars3_autotune(int(n), _p(rp), _p(ci), _p(v), None if pm is None else _p(pm), C.byref(base),
+                              int(dtype), int(k), C.byref(best), C.byref(us)), "pars3_autotune")
     return dict(T=best.T, W=best.W, dtypes=best.dtypes, long_row=best.long_row, us=us.value)
 
 
