@@ -155,6 +155,10 @@ def workload(name: str):
     elif name == "cfg0":
         A, alpha, x = W.config0()
         desc = "grid2d 200x100, U(-1,1) values, alpha=0"
+    elif name == "grid2d":
+        A = W.grid((2048, 1024), "normal", W.SEED_BASE + 5, name="grid2d_2048x1024")
+        alpha, x = 0.5, W.vector("uniform", A.n, W.SEED_BASE + 5)
+        desc = "grid2d 2048x1024 (band-friendly: RCM bandwidth ~1024), N(0,1), alpha=0.5"
     else:
         raise SystemExit(f"unknown workload {name}")
     return A, alpha, x, desc

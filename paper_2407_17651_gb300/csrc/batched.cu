@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -29,7 +30,7 @@ __device__ __forceinline__ int unit_matrix(const int32_t *upre, int count, int u
     return lo;
 }
 
-template <typename VT, typename XT, typename AT, int LPR>
+template <typename VT, typename XT, typename AT, int LPR, int NV>
 __global__ void __launch_bounds__(kBlock, 2) batched_kernel(const SpmvArgs<VT, XT, AT> *__restrict__ args,
                                                              const int32_t *__restrict__ upre, int count,
                                                              int total, int k) {
@@ -55,8 +56,8 @@ __global__ void __launch_bounds__(kBlock, 2) batched_kernel(const SpmvArgs<VT, X
                 long_block<VT, XT, AT>(a, item - a.ntiles, smem, a.x);
             }
         } else {
-            if (item < a.ntiles) spmm_tile<VT, XT, AT, LPR>(a, k, item, smem);
-            else spmm_long<VT, XT, AT, LPR>(a, k, item - a.ntiles);
+            if (item < a.ntiles) spmm_tile<VT, XT, AT, LPR, NV>(a, k, item, smem);
+            else spmm_long<VT, XT, AT, LPR, NV>(a, k, item - a.ntiles);
         }
     }
 }
@@ -169,20 +170,20 @@ static int upload_vec(void **dst, const std::vector<T> &v) {
     return cuda_status(e);
 }
 
-template <typename VT, typename XT, typename AT, int LPR>
+template <typename VT, typename XT, typename AT, int LPR, int NV>
 static int enqueue(BatchCache &C, int count, int64_t total_units, int64_t total_fold, int smem, int k,
                    cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(batched_kernel<VT, XT, AT, LPR>,
+    static std::atomic<int> configured{0};
+    if (!configured.load()) {
+        cudaError_t e = cudaFuncSetAttribute(batched_kernel<VT, XT, AT, LPR, NV>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kSmemLimit - static_cast<int>(sizeof(SpmvArgs<VT, XT, AT>)) - 64);
         if (e != cudaSuccess) return cuda_status(e);
-        configured = true;
+        configured.store(1);
     }
     const int grid = static_cast<int>(std::min<int64_t>(total_units, 2LL * sm_count()));
     if (grid > 0)
-        batched_kernel<VT, XT, AT, LPR><<<grid, kBlock, smem, st>>>(
+        batched_kernel<VT, XT, AT, LPR, NV><<<grid, kBlock, smem, st>>>(
             static_cast<const SpmvArgs<VT, XT, AT> *>(C.args), static_cast<const int32_t *>(C.upre), count,
             static_cast<int>(total_units), k);
     if (total_fold > 0) {
@@ -193,6 +194,24 @@ static int enqueue(BatchCache &C, int count, int64_t total_units, int64_t total_
             static_cast<const int64_t *>(C.fpre), count, total_fold, k);
     }
     return cuda_status(cudaGetLastError());
+}
+
+template <typename VT, typename XT, typename AT, int NV>
+static int enqueue_lpr(int lpr, BatchCache &C, int count, int64_t nu, int64_t nfold, int smem, int k,
+                       cudaStream_t st) {
+    switch (lpr) {
+        case 1: return enqueue<VT, XT, AT, 1, NV>(C, count, nu, nfold, smem, k, st);
+        case 2: return enqueue<VT, XT, AT, 2, NV>(C, count, nu, nfold, smem, k, st);
+        case 4: return enqueue<VT, XT, AT, 4, NV>(C, count, nu, nfold, smem, k, st);
+        case 8: return enqueue<VT, XT, AT, 8, NV>(C, count, nu, nfold, smem, k, st);
+        case 16:
+            if constexpr (NV <= 2) return enqueue<VT, XT, AT, 16, NV>(C, count, nu, nfold, smem, k, st);
+            return PARS3_EINVAL;
+        case 32:
+            if constexpr (NV == 1) return enqueue<VT, XT, AT, 32, NV>(C, count, nu, nfold, smem, k, st);
+            return PARS3_EINVAL;
+        default: return PARS3_EINVAL;
+    }
 }
 
 template <typename VT, typename XT, typename AT>
@@ -243,12 +262,17 @@ static int run_batched(BatchCache &C, pars3_handle *const *hs, int count, int dt
         C.dtype = dtype;
         C.k = k;
     }
+    // 16-byte lanes when k is a multiple of the vector and every X, Y is 16-byte aligned
+    constexpr int V = 16 / static_cast<int>(sizeof(XT));
+    bool aligned = true;
+    for (int m = 0; m < count; ++m)
+        aligned = aligned && ((reinterpret_cast<uintptr_t>(X[m]) | reinterpret_cast<uintptr_t>(Y[m])) & 15u) == 0;
+    const int nv = (aligned && spmm_nv<XT>(k) == V) ? V : 1;
+    const int lpr = spmm_lpr(k, nv);
+    const int64_t nu = upre.back(), nfold = fpre.back();
     auto launch = [&](cudaStream_t s) {
-        if (k <= 2) return enqueue<VT, XT, AT, 2>(C, count, upre.back(), fpre.back(), smem, k, s);
-        if (k <= 4) return enqueue<VT, XT, AT, 4>(C, count, upre.back(), fpre.back(), smem, k, s);
-        if (k <= 8) return enqueue<VT, XT, AT, 8>(C, count, upre.back(), fpre.back(), smem, k, s);
-        if (k <= 16) return enqueue<VT, XT, AT, 16>(C, count, upre.back(), fpre.back(), smem, k, s);
-        return enqueue<VT, XT, AT, 32>(C, count, upre.back(), fpre.back(), smem, k, s);
+        if (nv == V) return enqueue_lpr<VT, XT, AT, V>(lpr, C, count, nu, nfold, smem, k, s);
+        return enqueue_lpr<VT, XT, AT, 1>(lpr, C, count, nu, nfold, smem, k, s);
     };
     if (!capture) return launch(st);
     if (!C.exec) {

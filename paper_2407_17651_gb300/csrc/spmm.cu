@@ -12,11 +12,11 @@
 
 namespace pars3 {
 
-template <typename VT, typename XT, typename AT, int LPR>
+template <typename VT, typename XT, typename AT, int LPR, int NV>
 __global__ void __launch_bounds__(kBlock, 2) spmm_kernel(const SpmvArgs<VT, XT, AT> a, int k) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (static_cast<int>(blockIdx.x) < a.ntiles) spmm_tile<VT, XT, AT, LPR>(a, k, blockIdx.x, smem);
-    else spmm_long<VT, XT, AT, LPR>(a, k, blockIdx.x - a.ntiles);
+    if (static_cast<int>(blockIdx.x) < a.ntiles) spmm_tile<VT, XT, AT, LPR, NV>(a, k, blockIdx.x, smem);
+    else spmm_long<VT, XT, AT, LPR, NV>(a, k, blockIdx.x - a.ntiles);
 }
 
 // y[row, c] += halo sum + long-row partial sums (chunk order), one thread per
@@ -55,7 +55,7 @@ int spmm_smem_bytes(const pars3_handle *h, int dtype) {
         spmm_layout(h->T, h->W, static_cast<uint32_t>(round_up(h->L.max_tile_half, kAlignHalf)), vsz).total);
 }
 
-template <typename VT, typename XT, typename AT, int LPR>
+template <typename VT, typename XT, typename AT, int LPR, int NV>
 static int launch_spmm_lpr(const pars3_handle *h, int dtype, double alpha, int k, const void *X, void *Y,
                            void *halo, void *lpart, cudaStream_t st) {
     const Layout &L = h->L;
@@ -97,13 +97,13 @@ static int launch_spmm_lpr(const pars3_handle *h, int dtype, double alpha, int k
     const int smem = spmm_smem_bytes(h, dtype);
     static std::atomic<int> configured{0};
     if (!configured.load()) {
-        cudaError_t e = cudaFuncSetAttribute(spmm_kernel<VT, XT, AT, LPR>,
+        cudaError_t e = cudaFuncSetAttribute(spmm_kernel<VT, XT, AT, LPR, NV>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
         if (e != cudaSuccess) return cuda_status(e);
         configured.store(1);
     }
     const int grid = h->ntiles + a.nchunks;
-    if (grid > 0) spmm_kernel<VT, XT, AT, LPR><<<grid, kBlock, smem, st>>>(a, k);
+    if (grid > 0) spmm_kernel<VT, XT, AT, LPR, NV><<<grid, kBlock, smem, st>>>(a, k);
     const int nf = static_cast<int>(L.fold_row.size());
     if (nf > 0) {
         const int64_t total = static_cast<int64_t>(nf) * k;
@@ -116,14 +116,32 @@ static int launch_spmm_lpr(const pars3_handle *h, int dtype, double alpha, int k
     return cuda_status(cudaGetLastError());
 }
 
+template <typename VT, typename XT, typename AT, int NV>
+static int launch_spmm_nv(const pars3_handle *h, int dtype, double alpha, int k, const void *X, void *Y,
+                          void *halo, void *lpart, cudaStream_t st) {
+    switch (spmm_lpr(k, NV)) {
+        case 1: return launch_spmm_lpr<VT, XT, AT, 1, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+        case 2: return launch_spmm_lpr<VT, XT, AT, 2, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+        case 4: return launch_spmm_lpr<VT, XT, AT, 4, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+        case 8: return launch_spmm_lpr<VT, XT, AT, 8, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+        case 16:
+            if constexpr (NV <= 2) return launch_spmm_lpr<VT, XT, AT, 16, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+            return PARS3_EINVAL;
+        case 32:
+            if constexpr (NV == 1) return launch_spmm_lpr<VT, XT, AT, 32, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+            return PARS3_EINVAL;
+        default: return PARS3_EINVAL;
+    }
+}
+
+// 16-byte lanes when k is a multiple of the vector and X, Y are 16-byte aligned
 template <typename VT, typename XT, typename AT>
 static int launch_spmm_typed(const pars3_handle *h, int dtype, double alpha, int k, const void *X, void *Y,
                              void *halo, void *lpart, cudaStream_t st) {
-    if (k <= 2) return launch_spmm_lpr<VT, XT, AT, 2>(h, dtype, alpha, k, X, Y, halo, lpart, st);
-    if (k <= 4) return launch_spmm_lpr<VT, XT, AT, 4>(h, dtype, alpha, k, X, Y, halo, lpart, st);
-    if (k <= 8) return launch_spmm_lpr<VT, XT, AT, 8>(h, dtype, alpha, k, X, Y, halo, lpart, st);
-    if (k <= 16) return launch_spmm_lpr<VT, XT, AT, 16>(h, dtype, alpha, k, X, Y, halo, lpart, st);
-    return launch_spmm_lpr<VT, XT, AT, 32>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) == 0;
+    constexpr int V = 16 / static_cast<int>(sizeof(XT));
+    if (aligned && spmm_nv<XT>(k) == V) return launch_spmm_nv<VT, XT, AT, V>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+    return launch_spmm_nv<VT, XT, AT, 1>(h, dtype, alpha, k, X, Y, halo, lpart, st);
 }
 
 int launch_spmm(const pars3_handle *h, int dtype, double alpha, int k, const void *X, void *Y, void *halo,

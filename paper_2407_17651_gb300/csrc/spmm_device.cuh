@@ -2,15 +2,18 @@
 // Y = (alpha I + S) X (X, Y row-major, k <= 32), shared by the single-matrix
 // launch (spmm.cu) and the batched persistent launch (batched.cu).
 //
-// Lanes run over the k columns: a group of LPR = next_pow2(k) lanes owns one
-// row, so every gather of a row of X is a coalesced read of k consecutive
-// values.  The x window is not staged (k times T+W values would not fit);
-// middle entries gather X rows through L2 like the outer ones.  Each stored
-// middle entry is still read once and used twice (Eqs. 2-6): for its row
-// and, through the (column, row) list, for the mirrored column sum.  The
-// tile's middle entries, row pointers and (column, row) order are staged by
-// TMA; a per-entry row index and the row -> sliced-ELL lane map are built in
-// shared memory.
+// A group of LPR lanes owns one row; each lane holds NV consecutive columns
+// (NV = 16 bytes of the vector type when k is a multiple of it, else 1), so a
+// row of X is gathered with 16-byte coalesced loads and a warp keeps 32/LPR
+// rows in flight.  Groups walk the tile's rows in sliced-ELL order (slice by
+// slice, lane by lane), so neighbouring groups read neighbouring slots of the
+// full-storage arrays and rows of similar length run side by side.  The x
+// window is not staged (k times T+W values would not fit); middle entries
+// gather X rows through L2 like the outer ones.  Each stored middle entry is
+// still read once and used twice (Eqs. 2-6): for its row and, through the
+// (column, row) list, for the mirrored column sum.  The tile's middle
+// entries, row pointers and (column, row) order are staged by TMA; a
+// per-entry row index is built in shared memory.
 #pragma once
 
 #include "spmv_kernels.cuh"
@@ -18,7 +21,7 @@
 namespace pars3 {
 
 struct SpmmLayout {
-    uint32_t hrp, hval, hcol, cperm, hrow, rowpos, cs, ce, mbar, total;
+    uint32_t hrp, hval, hcol, cperm, hrow, cs, ce, mbar, total;
 };
 
 // T: tile rows, W: window, Mh: half-path entries of the largest tile
@@ -29,15 +32,135 @@ PARS3_HD SpmmLayout spmm_layout(uint32_t T, uint32_t W, uint32_t Mh, uint32_t vs
     s.hcol = align128(s.hval + Mh * vsz);
     s.cperm = align128(s.hcol + Mh * 2u);
     s.hrow = align128(s.cperm + Mh * 2u);
-    s.rowpos = align128(s.hrow + Mh * 2u);
-    s.cs = align128(s.rowpos + T * 4u);
+    s.cs = align128(s.hrow + Mh * 2u);
     s.ce = align128(s.cs + (T + W) * 2u);
     s.mbar = align128(s.ce + (T + W) * 2u);
     s.total = align128(s.mbar + 8u);
     return s;
 }
 
-template <typename VT, typename XT, typename AT, int LPR>
+// NV consecutive elements of a row of X (a 16-byte vector when NV > 1)
+template <typename XT, int NV> struct XVec;
+template <typename XT> struct XVec<XT, 1> {
+    static __device__ __forceinline__ void ld(const XT *p, XT *o) { o[0] = __ldg(p); }
+    static __device__ __forceinline__ void st(XT *p, const XT *o) { p[0] = o[0]; }
+};
+template <> struct XVec<float, 4> {
+    static __device__ __forceinline__ void ld(const float *p, float *o) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float *o) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <> struct XVec<double, 2> {
+    static __device__ __forceinline__ void ld(const double *p, double *o) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double *o) {
+        *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+    }
+};
+
+// elements per lane for k columns of XT: a 16-byte vector when it divides k
+template <typename XT>
+PARS3_HD int spmm_nv(int k) {
+    const int v = 16 / static_cast<int>(sizeof(XT));
+    return (k % v == 0) ? v : 1;
+}
+
+// lanes per row (a power of two) for k columns held NV to a lane
+PARS3_HD int spmm_lpr(int k, int nv) {
+    const int lanes = (k + nv - 1) / nv;
+    int lpr = 1;
+    while (lpr < lanes) lpr <<= 1;
+    return lpr;
+}
+
+// entries in flight per lane group (fewer with fp64 or vector lanes, which
+// need more registers per entry)
+template <typename AT, int NV> constexpr int spmm_unroll() { return (NV == 1 && sizeof(AT) == 4) ? 8 : 4; }
+
+// acc[0..NV) += sum_m v[base + m*stride] * X[col[base + m*stride], c0..c0+NV)
+// for m < len, in m order.  Every lane of a group loads the same value and
+// column (L1 broadcast) and its own NV columns of the X row.
+template <typename VT, typename XT, typename AT, int NV>
+__device__ __forceinline__ void spmm_strided_sum(const VT *__restrict__ val, const int32_t *__restrict__ col,
+                                                 int64_t base, int64_t stride, int len, const XT *__restrict__ X,
+                                                 int k, int c0, bool on, AT *acc) {
+    constexpr int U = spmm_unroll<AT, NV>();
+    for (int m0 = 0; m0 < len; m0 += U) {
+        AT v[U];
+        int j[U];
+        XT xv[U][NV];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u] = AT(0);
+            j[u] = 0;
+            if (m0 + u < len) {
+                const int64_t q = base + static_cast<int64_t>(m0 + u) * stride;
+                v[u] = static_cast<AT>(Val<VT>::ld(val + q));
+                j[u] = __ldg(col + q);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (on && m0 + u < len) {
+                XVec<XT, NV>::ld(X + static_cast<int64_t>(j[u]) * k + c0, xv[u]);
+            } else {
+#pragma unroll
+                for (int w = 0; w < NV; ++w) xv[u][w] = XT(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (m0 + u < len) {
+#pragma unroll
+                for (int w = 0; w < NV; ++w) acc[w] += v[u] * static_cast<AT>(xv[u][w]);
+            }
+    }
+}
+
+// acc[w] += hval[e] * X[xbase + xidx[e], c0 + w] over the staged middle
+// entries e = order[q] (or e = q when order is null) for q in [q0, q1), in q
+// order.
+template <typename VT, typename XT, typename AT, int NV>
+__device__ __forceinline__ void spmm_smem_sum(const VT *hval, const uint16_t *order, const uint16_t *xidx, int q0,
+                                              int q1, int64_t xbase, const XT *__restrict__ X, int k, int c0,
+                                              bool on, AT *acc) {
+    constexpr int U = spmm_unroll<AT, NV>();
+    for (int m0 = q0; m0 < q1; m0 += U) {
+        AT v[U];
+        XT xv[U][NV];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u] = AT(0);
+            if (m0 + u < q1) {
+                const int e = order ? order[m0 + u] : m0 + u;
+                v[u] = sval<VT>(hval, e);
+                if (on) XVec<XT, NV>::ld(X + (xbase + xidx[e]) * k + c0, xv[u]);
+            }
+            if (!(on && m0 + u < q1)) {
+#pragma unroll
+                for (int w = 0; w < NV; ++w) xv[u][w] = XT(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (m0 + u < q1) {
+#pragma unroll
+                for (int w = 0; w < NV; ++w) acc[w] += v[u] * static_cast<AT>(xv[u][w]);
+            }
+    }
+}
+
+template <typename VT, typename XT, typename AT, int LPR, int NV>
 __device__ __forceinline__ void spmm_tile(const SpmvArgs<VT, XT, AT> &a, int k, int t, unsigned char *smem) {
     const SpmmLayout L = spmm_layout(a.T, a.W, a.Mh, sizeof(VT));
     uint16_t *hrp = reinterpret_cast<uint16_t *>(smem + L.hrp);
@@ -45,7 +168,6 @@ __device__ __forceinline__ void spmm_tile(const SpmvArgs<VT, XT, AT> &a, int k, 
     uint16_t *hcol = reinterpret_cast<uint16_t *>(smem + L.hcol);
     uint16_t *cperm = reinterpret_cast<uint16_t *>(smem + L.cperm);
     uint16_t *hrow = reinterpret_cast<uint16_t *>(smem + L.hrow);
-    uint32_t *rowpos = reinterpret_cast<uint32_t *>(smem + L.rowpos);
     uint16_t *cs = reinterpret_cast<uint16_t *>(smem + L.cs);
     uint16_t *ce = reinterpret_cast<uint16_t *>(smem + L.ce);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
@@ -55,105 +177,105 @@ __device__ __forceinline__ void spmm_tile(const SpmvArgs<VT, XT, AT> &a, int k, 
     const int hb = a.hoff[t], hm = a.hcnt[t];
     const uint32_t hmp = static_cast<uint32_t>((hm + kAlignHalf - 1) / kAlignHalf * kAlignHalf);
     const uint32_t rpb = static_cast<uint32_t>(a.T + 8) * 2u;
-    if (tid == 0) {
-        mbar_init(mbar, 1);
-        fence_mbar_init();
-        uint32_t tx = rpb + (hm > 0 ? hmp * (sizeof(VT) + 4u) : 0u);
-        mbar_arrive_expect_tx(mbar, tx);
-        bulk_g2s(hrp, a.hrp + static_cast<size_t>(t) * (a.T + 8), rpb, mbar);
-        if (hm > 0) {
+    const bool staged = hm > 0;   // block-uniform
+    if (staged) {
+        if (tid == 0) {
+            mbar_init(mbar, 1);
+            fence_mbar_init();
+            mbar_arrive_expect_tx(mbar, rpb + hmp * (sizeof(VT) + 4u));
+            bulk_g2s(hrp, a.hrp + static_cast<size_t>(t) * (a.T + 8), rpb, mbar);
             bulk_g2s(hval, a.hval + hb, hmp * sizeof(VT), mbar);
             bulk_g2s(hcol, a.hcol + hb, hmp * 2u, mbar);
             bulk_g2s(cperm, a.hcperm + hb, hmp * 2u, mbar);
         }
+        for (int p = tid; p < nr + a.W; p += P) {
+            cs[p] = 0;
+            ce[p] = 0;
+        }
+        __syncthreads();   // the barrier is initialised before anyone waits on it
+        mbar_wait_bounded(mbar, 0, a.err);
+        __syncthreads();
+        if (tid == 0) mbar_inval(mbar);
+        for (int r = tid; r < nr; r += P)
+            for (int e = hrp[r]; e < hrp[r + 1]; ++e) hrow[e] = static_cast<uint16_t>(r);
+        for (int q = tid; q < hm; q += P) {
+            const int key = hcol[cperm[q]];
+            if (q == 0 || hcol[cperm[q - 1]] != key) cs[key] = static_cast<uint16_t>(q);
+            if (q == hm - 1 || hcol[cperm[q + 1]] != key) ce[key] = static_cast<uint16_t>(q + 1);
+        }
+        __syncthreads();
     }
-    for (int p = tid; p < nr + a.W; p += P) {
-        cs[p] = 0;
-        ce[p] = 0;
-    }
-    // row -> (slice, lane) of the sliced-ELL rows of this tile
-    const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
-    for (int q = tid; q < (s1 - s0) * kSlice; q += P) {
-        const uint32_t meta = __ldg(a.sl_meta + static_cast<int64_t>(s0) * kSlice + q);
-        const uint32_t rl = meta & 0xffffu;
-        if (rl != 0xffffu) rowpos[rl] = static_cast<uint32_t>(q);
-    }
-    __syncthreads();
-    mbar_wait_bounded(mbar, 0, a.err);
-    __syncthreads();
-    if (tid == 0) mbar_inval(mbar);
-    for (int r = tid; r < nr; r += P)
-        for (int e = hrp[r]; e < hrp[r + 1]; ++e) hrow[e] = static_cast<uint16_t>(r);
-    for (int q = tid; q < hm; q += P) {
-        const int key = hcol[cperm[q]];
-        if (q == 0 || hcol[cperm[q - 1]] != key) cs[key] = static_cast<uint16_t>(q);
-        if (q == hm - 1 || hcol[cperm[q + 1]] != key) ce[key] = static_cast<uint16_t>(q + 1);
-    }
-    __syncthreads();
 
-    const int g = tid / LPR, c = tid % LPR, ng = P / LPR;
-    const bool on = c < k;
-    for (int r = g; r < nr; r += ng) {
-        const int64_t row = static_cast<int64_t>(r0 + r);
-        AT acc = on ? a.alpha * static_cast<AT>(a.x[row * k + c]) : AT(0);
-        const uint32_t pos = rowpos[r];
-        const int s = static_cast<int>(pos >> 5), l = static_cast<int>(pos & 31u);
-        const uint32_t meta = __ldg(a.sl_meta + (static_cast<int64_t>(s0) + s) * kSlice + l);
+    const int g = tid / LPR, c0 = (tid % LPR) * NV, ng = P / LPR;
+    const bool on = c0 < k;
+    const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
+    const int nslot = (s1 - s0) * kSlice;
+    for (int q = g; q < nslot; q += ng) {
+        const int s = q >> 5, l = q & 31;
+        const uint32_t meta = __ldg(a.sl_meta + static_cast<int64_t>(s0) * kSlice + q);
+        const int rl = static_cast<int>(meta & 0xffffu);
+        if (rl == 0xffff) continue;   // padding lane of the tile's last slice
         const int len = static_cast<int>(meta >> 16);
+        const int64_t row = static_cast<int64_t>(r0 + rl);
+        AT acc[NV];
+        {
+            XT xr[NV];
+            if (on) XVec<XT, NV>::ld(a.x + row * k + c0, xr);
+#pragma unroll
+            for (int w = 0; w < NV; ++w) acc[w] = on ? a.alpha * static_cast<AT>(xr[w]) : AT(0);
+        }
         const int64_t base = static_cast<int64_t>(__ldg(a.sl_ent + s0 + s)) + l;
-        for (int m = 0; m < len; ++m) {
-            const int64_t q = base + static_cast<int64_t>(m) * kSlice;
-            const AT v = Val<VT>::ld(a.fval + q);
-            const int j = __ldg(a.fcol + q);
-            if (on) acc += v * static_cast<AT>(__ldg(a.x + static_cast<int64_t>(j) * k + c));
-        }
-        if (hm > 0) {
-            for (int e = hrp[r]; e < hrp[r + 1]; ++e) {
-                const AT v = sval<VT>(hval, e);
-                const int64_t j = wb + hcol[e];
-                if (on) acc += v * static_cast<AT>(__ldg(a.x + j * k + c));
+        spmm_strided_sum<VT, XT, AT, NV>(a.fval, a.fcol, base, kSlice, len, a.x, k, c0, on, acc);
+        if (staged) {
+            spmm_smem_sum<VT, XT, AT, NV>(hval, nullptr, hcol, hrp[rl], hrp[rl + 1], wb, a.x, k, c0, on, acc);
+            const int p = rl + a.W;
+            if (ce[p] > cs[p]) {
+                AT cm[NV];
+#pragma unroll
+                for (int w = 0; w < NV; ++w) cm[w] = AT(0);
+                spmm_smem_sum<VT, XT, AT, NV>(hval, cperm, hrow, cs[p], ce[p], r0, a.x, k, c0, on, cm);
+#pragma unroll
+                for (int w = 0; w < NV; ++w) acc[w] = acc[w] - cm[w];
             }
-            const int p = r + a.W;
-            AT cm = AT(0);
-            for (int q = cs[p]; q < ce[p]; ++q) {
-                const int e = cperm[q];
-                const AT v = sval<VT>(hval, e);
-                if (on) cm += v * static_cast<AT>(__ldg(a.x + static_cast<int64_t>(r0 + hrow[e]) * k + c));
-            }
-            if (ce[p] > cs[p]) acc = acc - cm;
         }
-        if (on) a.y[row * k + c] = static_cast<XT>(acc);
+        if (on) {
+            XT out[NV];
+#pragma unroll
+            for (int w = 0; w < NV; ++w) out[w] = static_cast<XT>(acc[w]);
+            XVec<XT, NV>::st(a.y + row * k + c0, out);
+        }
     }
+    if (!staged) return;
     const int g0 = a.hhoff[t], g1 = a.hhoff[t + 1];
     for (int h = g0 + g; h < g1; h += ng) {
         const int p = a.hhrow[h] - wb;
-        AT cm = AT(0);
-        for (int q = cs[p]; q < ce[p]; ++q) {
-            const int e = cperm[q];
-            const AT v = sval<VT>(hval, e);
-            if (on) cm += v * static_cast<AT>(__ldg(a.x + static_cast<int64_t>(r0 + hrow[e]) * k + c));
-        }
-        if (on) a.halo[static_cast<int64_t>(h) * k + c] = -cm;
+        AT cm[NV];
+#pragma unroll
+        for (int w = 0; w < NV; ++w) cm[w] = AT(0);
+        spmm_smem_sum<VT, XT, AT, NV>(hval, cperm, hrow, cs[p], ce[p], r0, a.x, k, c0, on, cm);
+        if (on)
+#pragma unroll
+            for (int w = 0; w < NV; ++w) a.halo[static_cast<int64_t>(h) * k + c0 + w] = -cm[w];
     }
 }
 
 // Long-row chunk: one lane group per row touched, entries read in order.
-template <typename VT, typename XT, typename AT, int LPR>
+template <typename VT, typename XT, typename AT, int LPR, int NV>
 __device__ __forceinline__ void spmm_long(const SpmvArgs<VT, XT, AT> &a, int k, int cidx) {
     const int tid = threadIdx.x, P = blockDim.x;
     const int beg = a.lcbeg[cidx], end = a.lcend[cidx];
     const int l0 = a.lcfirst[cidx], nrc = a.lcrows[cidx];
-    const int g = tid / LPR, c = tid % LPR, ng = P / LPR;
-    const bool on = c < k;
+    const int g = tid / LPR, c0 = (tid % LPR) * NV, ng = P / LPR;
+    const bool on = c0 < k;
     for (int u = g; u < nrc; u += ng) {
         const int e0 = max(a.lrp[l0 + u], beg), e1 = min(a.lrp[l0 + u + 1], end);
-        AT acc = AT(0);
-        for (int e = e0; e < e1; ++e) {
-            const AT v = Val<VT>::ld(a.lval + e);
-            const int j = __ldg(a.lcol + e);
-            if (on) acc += v * static_cast<AT>(__ldg(a.x + static_cast<int64_t>(j) * k + c));
-        }
-        if (on) a.lpart[static_cast<int64_t>(a.lcslot[cidx] + u) * k + c] = acc;
+        AT acc[NV];
+#pragma unroll
+        for (int w = 0; w < NV; ++w) acc[w] = AT(0);
+        spmm_strided_sum<VT, XT, AT, NV>(a.lval, a.lcol, e0, 1, max(e1 - e0, 0), a.x, k, c0, on, acc);
+        if (on)
+#pragma unroll
+            for (int w = 0; w < NV; ++w) a.lpart[static_cast<int64_t>(a.lcslot[cidx] + u) * k + c0 + w] = acc[w];
     }
 }
 

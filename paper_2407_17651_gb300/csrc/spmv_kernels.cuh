@@ -277,43 +277,68 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     const uint32_t hmp = static_cast<uint32_t>((hm + kAlignHalf - 1) / kAlignHalf * kAlignHalf);
     const uint32_t rpb = static_cast<uint32_t>(a.T + 8) * 2u;
 
-    // 0. the copy engine stages the x window and the middle entries
-    if (tid == 0) {
+    // 0. the copy engine stages the x window and the middle entries (a tile
+    // without middle entries needs neither)
+    const bool staged = hm > 0;
+    if (staged && tid == 0) {
         mbar_init(mbar, 1);
         fence_mbar_init();
-        uint32_t tx = nbulk + rpb;
-        if (hm > 0) tx += hmp * (sizeof(VT) + 4u);
+        const uint32_t tx = nbulk + rpb + hmp * (sizeof(VT) + 4u);
         mbar_arrive_expect_tx(mbar, tx);
         if (nbulk > 0) bulk_g2s(xs + (wlo - wb), xop + wlo, nbulk, mbar);
         bulk_g2s(hrp, a.hrp + static_cast<size_t>(t) * (a.T + 8), rpb, mbar);
-        if (hm > 0) {
-            bulk_g2s(hval, a.hval + hb, hmp * sizeof(VT), mbar);
-            bulk_g2s(hcol, a.hcol + hb, hmp * 2u, mbar);
-            bulk_g2s(cperm, a.hcperm + hb, hmp * 2u, mbar);
-        }
+        bulk_g2s(hval, a.hval + hb, hmp * sizeof(VT), mbar);
+        bulk_g2s(hcol, a.hcol + hb, hmp * 2u, mbar);
+        bulk_g2s(cperm, a.hcperm + hb, hmp * 2u, mbar);
     }
-    for (int g = wlo + static_cast<int>(nbulk / sizeof(XT)) + tid; g < r1; g += P) xs[g - wb] = xop[g];
-    if (hm > 0)
+    if (staged) {
+        for (int g = wlo + static_cast<int>(nbulk / sizeof(XT)) + tid; g < r1; g += P) xs[g - wb] = xop[g];
         for (int p = tid; p < nr + a.W; p += P) {
             cs[p] = 0;
             ce[p] = 0;
         }
+    }
     __syncthreads();   // the barrier is initialised before anyone waits on it
 
     // 1. full pass (sliced ELL) straight from HBM while the copy runs
     const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
-    for (int s = s0 + warp; s < s1; s += nwarps) {
-        const uint32_t meta = __ldg(a.sl_meta + static_cast<int64_t>(s) * kSlice + lane);
-        const int rl = static_cast<int>(meta & 0xffffu), len = static_cast<int>(meta >> 16);
-        if (rl != 0xffff) {
-            const AT start = epi.start(xop, r0 + rl);
-            rowacc[rl] = slice_row_sum<VT, XT, AT>(a.fval, a.fcol, static_cast<int64_t>(__ldg(a.sl_ent + s)) + lane,
-                                                   len, xop, start);
+    {
+        // the next slice's metadata is fetched while the current one runs
+        // (fp32 / bf16 values; with fp64 the extra registers cost more than
+        // the overlap gains)
+        constexpr bool kPrefetch = sizeof(AT) == 4;
+        int s = s0 + warp;
+        uint32_t meta_n = 0u;
+        int ent_n = 0;
+        if (kPrefetch && s < s1) {
+            meta_n = __ldg(a.sl_meta + static_cast<int64_t>(s) * kSlice + lane);
+            ent_n = __ldg(a.sl_ent + s);
+        }
+        for (; s < s1; s += nwarps) {
+            uint32_t meta;
+            int ent;
+            if (kPrefetch) {
+                meta = meta_n;
+                ent = ent_n;
+                if (s + nwarps < s1) {
+                    meta_n = __ldg(a.sl_meta + static_cast<int64_t>(s + nwarps) * kSlice + lane);
+                    ent_n = __ldg(a.sl_ent + s + nwarps);
+                }
+            } else {
+                meta = __ldg(a.sl_meta + static_cast<int64_t>(s) * kSlice + lane);
+                ent = __ldg(a.sl_ent + s);
+            }
+            const int rl = static_cast<int>(meta & 0xffffu), len = static_cast<int>(meta >> 16);
+            if (rl != 0xffff) {
+                const AT start = epi.start(xop, r0 + rl);
+                rowacc[rl] = slice_row_sum<VT, XT, AT>(a.fval, a.fcol, static_cast<int64_t>(ent) + lane, len, xop,
+                                                       start);
+            }
         }
     }
-    mbar_wait_bounded(mbar, 0, a.err);
+    if (staged) mbar_wait_bounded(mbar, 0, a.err);
     __syncthreads();
-    if (tid == 0) mbar_inval(mbar);
+    if (staged && tid == 0) mbar_inval(mbar);
 
     double *red = reinterpret_cast<double *>(smem + L.red);
     if (hm == 0) {
@@ -407,8 +432,13 @@ __device__ __forceinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c,
     }
 }
 
+// Blocks per SM the tile kernels are compiled for: fp64 needs its 64
+// registers per thread; fp32 / bf16 fit 40 and run three 512-thread blocks.
+template <typename AT>
+constexpr int tile_min_blocks() { return sizeof(AT) == 8 ? 2 : 3; }
+
 template <typename VT, typename XT, typename AT>
-__global__ void __launch_bounds__(kBlock, 2) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
+__global__ void __launch_bounds__(kBlock, tile_min_blocks<AT>()) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (static_cast<int>(blockIdx.x) < a.ntiles) {
         EpiSpmv<XT, AT> epi{a.alpha, a.y};

@@ -102,3 +102,27 @@ def test_spmm_rejects_bad_k():
     with pytest.raises(P.Pars3Error) as e:
         P.pars3_spmm(h, P.F64, 1.0, X, Y)
     assert e.value.code == P.EINVAL
+
+
+@pytest.mark.parametrize("dtype", [P.F64, P.F32], ids=["f64", "f32"])
+def test_spmm_unaligned_blocks_use_scalar_lanes(dtype):
+    """X, Y not 16-byte aligned: the product falls back to one column per
+    lane and gives the same bits as the 16-byte-lane product."""
+    A = W.grid_plus_random((14, 15, 16), 0.01, "normal", 21)
+    perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=512, W=64, dtypes=7)
+    P.pars3_upload(h)
+    k = 8
+    vt = torch.float64 if dtype == P.F64 else torch.float32
+    X = torch.from_numpy(W.vector("uniform", (A.n, k), 22)[perm]).to("cuda", vt)
+    Y = torch.empty_like(X)
+    P.pars3_spmm(h, dtype, 0.7, X, Y)
+    buf_x = torch.empty(A.n * k + 1, dtype=vt, device="cuda")
+    buf_y = torch.empty(A.n * k + 1, dtype=vt, device="cuda")
+    Xu = buf_x[1:].view(A.n, k)
+    Yu = buf_y[1:].view(A.n, k)
+    Xu.copy_(X)
+    assert Xu.data_ptr() % 16 != 0
+    P.pars3_spmm(h, dtype, 0.7, Xu, Yu)
+    torch.cuda.synchronize()
+    assert torch.equal(Y, Yu)
