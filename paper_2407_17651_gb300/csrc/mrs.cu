@@ -31,43 +31,6 @@ namespace pars3 {
 constexpr int kRedBlock = 256;
 constexpr int kMaxRedBlocks = 1024;
 
-// deterministic block sum of one double per thread (warp butterflies, then
-// warps in order)
-__device__ __forceinline__ double block_sum(double v, double *red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < nw; ++w) s += red[w];
-    return s;   // valid on thread 0
-}
-
-// Last block of a grid to arrive: sums part[0..count) in a fixed order.
-// Returns true (on every thread of that block) and leaves the sum in *out
-// (thread 0).
-__device__ __forceinline__ bool last_block_sum(unsigned *ticket, const double *part, int count, double *red,
-                                               double *out) {
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    double v = 0.0;
-    for (int i = threadIdx.x; i < count; i += blockDim.x) v += __ldcg(part + i);
-    const double s = block_sum(v, red);
-    if (threadIdx.x == 0) {
-        *out = s;
-        *ticket = 0u;
-    }
-    return true;
-}
-
 // Fold of MRS iteration j: w_j[r] += (halo + long-row partials) / beta_{j-1}
 // for the rows the tile kernel left open, their squared norms, then (last
 // block) beta_j from all partial norms and the Givens step.
@@ -82,7 +45,7 @@ __global__ void __launch_bounds__(kRedBlock) fold_mrs_kernel(
     MrsState *st = m.st;
     const int j = st->j + 1;
     XT *y = m.w[j % 3];
-    const AT scale = static_cast<AT>(1.0 / st->beta[(j - 1) & 3]);
+    const AT scale = static_cast<AT>(st->e_scale);   // 1 / beta_{j-1}
     double nrm = 0.0;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nitems; f += gridDim.x * blockDim.x) {
         const int r = frow[f];
@@ -100,24 +63,7 @@ __global__ void __launch_bounds__(kRedBlock) fold_mrs_kernel(
     if (threadIdx.x == 0) m.part[ntiles + blockIdx.x] = bs;
     double tot = 0.0;
     if (!last_block_sum(&st->ticket, m.part, ntiles + gridDim.x, red, &tot)) return;
-    if (threadIdx.x != 0) return;
-    const double beta = sqrt(tot);
-    const double gam = st->gamma;
-    const double rho = hypot(gam, beta);
-    const double c = gam / rho, s = beta / rho;
-    const int k = j & 3;
-    st->beta[k] = beta;
-    st->rho[k] = rho;
-    st->c[k] = c;
-    st->s[k] = s;
-    st->tau[k] = c * st->t;
-    const double tn = -s * st->t;
-    st->t = tn;
-    st->gamma = st->alpha / c;
-    st->j = j;
-    const int done = (fabs(tn) <= st->tol) || (beta == 0.0) || (j >= st->jmax);
-    st->done = done;
-    if (in_graph) cudaGraphSetConditional(cond, done ? 0u : 1u);
+    if (threadIdx.x == 0) mrs_step(st, tot, cond, in_graph);
 }
 
 // Start of an inner solve on rhs r scaled by inv: w_0 = r*inv, w_{-1} = 0,
@@ -161,19 +107,21 @@ __global__ void __launch_bounds__(kRedBlock) mrs_init_kernel(int n, const double
     st->j = 0;
     st->jmax = jmax;
     st->done = b0 == 0.0;
+    mrs_next_coeffs(st);
 }
 
 // After the last iteration J: p_J = (w_{J-1}/beta_{J-1} - R[J-2,J] p_{J-2}) / rho_J,
-// x += tau_J p_J.
+// x += tau_J p_J.  These are the lagged-update scalars of iteration J + 1,
+// already in the state (mrs_next_coeffs).
 template <typename XT, typename AT>
 __global__ void mrs_finish_kernel(int n, const MrsVectors<XT> m) {
     const MrsState *st = m.st;
     const int J = st->j;
     if (J < 1) return;
-    const AT inv_b = static_cast<AT>(1.0 / st->beta[(J - 1) & 3]);
-    const AT rr = static_cast<AT>(J >= 3 ? -st->s[(J - 2) & 3] * st->beta[(J - 1) & 3] : 0.0);
-    const AT inv_rho = static_cast<AT>(1.0 / st->rho[J & 3]);
-    const AT tau = static_cast<AT>(st->tau[J & 3]);
+    const AT inv_b = static_cast<AT>(st->e_inv_b2);
+    const AT rr = static_cast<AT>(st->e_r3);
+    const AT inv_rho = static_cast<AT>(st->e_inv_rho);
+    const AT tau = static_cast<AT>(st->e_tau);
     const XT *wv = m.w[(J + 2) % 3];
     const XT *pp = m.p[(J + 1) % 3];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -320,6 +268,14 @@ static SpmvArgs<VT, XT, AT> spmv_args(const pars3_handle *h, int dtype) {
     return a;
 }
 
+// largest dynamic shared memory of a launch (the fused kernel also has a
+// little static shared memory, which counts against the same per-block limit)
+template <typename VT, typename XT, typename AT, bool S, bool F>
+static cudaError_t set_mrs_smem(int) {
+    return cudaFuncSetAttribute(tile_kernel_mrs<VT, XT, AT, S, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSmemLimit - 1024);
+}
+
 // Capture the loop body (tile kernel in Lanczos mode + MRS fold) once as
 // the body of a while-node; the condition is set by the fold kernel.
 template <typename VT, typename XT, typename AT>
@@ -343,9 +299,26 @@ static int build_graph(pars3_handle *h, int dtype, MrsWork &W) {
     m.fold_bits = W.fold_bits;
     m.part = W.part;
     const SpmvArgs<VT, XT, AT> a = spmv_args<VT, XT, AT>(h, dtype);
-    const int smem = smem_bytes_for(h, dtype);
-    cudaError_t e = cudaFuncSetAttribute(tile_kernel_mrs<VT, XT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemLimit);
+    // tile kernel with the epilogue vectors staged in shared memory when
+    // they fit next to the tile's own staging area, else unstaged
+    uint32_t vsz, xsz, asz;
+    dtype_sizes(dtype, &vsz, &xsz, &asz);
+    const uint32_t tile_total =
+        smem_layout(h->T, h->W, static_cast<uint32_t>(round_up(h->L.max_tile_half, kAlignHalf)), vsz, xsz, asz).total;
+    const uint32_t staged_bytes = align128(tile_total) + 3u * EpiMrs<XT, AT, true>::slice_bytes(h->T);
+    constexpr uint32_t kStaticSlack = 1024;   // static shared memory of the fused kernel
+    const bool stage = staged_bytes + kStaticSlack <= static_cast<uint32_t>(kSmemLimit);
+    const int smem = stage ? std::max(smem_bytes_for(h, dtype), static_cast<int>(staged_bytes)) : smem_bytes_for(h, dtype);
+    const Layout &L = h->L;
+    // fusing the step into the tile kernel saves a launch per iteration in
+    // fp64 (measured 2 %) but costs 8 % in fp32, where the separate fold wins
+    const bool fused = sizeof(AT) == 8 && L.fold_row.empty() && L.lcbeg.empty() &&
+                       smem + static_cast<int>(kStaticSlack) <= kSmemLimit;
+    cudaError_t e = cudaSuccess;
+    if (stage && fused) e = set_mrs_smem<VT, XT, AT, true, true>(smem);
+    else if (stage) e = set_mrs_smem<VT, XT, AT, true, false>(smem);
+    else if (fused) e = set_mrs_smem<VT, XT, AT, false, true>(smem);
+    else e = set_mrs_smem<VT, XT, AT, false, false>(smem);
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaGraphCreate(&G.graph, 0);
     if (e != cudaSuccess) return cuda_status(e);
@@ -362,12 +335,16 @@ static int build_graph(pars3_handle *h, int dtype, MrsWork &W) {
     e = cudaStreamBeginCaptureToGraph(W.capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_status(e);
     const int grid = h->ntiles + a.nchunks;
-    tile_kernel_mrs<VT, XT, AT><<<grid, kBlock, smem, W.capture>>>(a, m);
-    const Layout &L = h->L;
+    if (stage && fused) tile_kernel_mrs<VT, XT, AT, true, true><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
+    else if (stage) tile_kernel_mrs<VT, XT, AT, true, false><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
+    else if (fused) tile_kernel_mrs<VT, XT, AT, false, true><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
+    else tile_kernel_mrs<VT, XT, AT, false, false><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
     const DevLayout &D = h->D;
-    fold_mrs_kernel<XT, AT><<<fold_blocks(h), kRedBlock, 0, W.capture>>>(
-        static_cast<int>(L.fold_row.size()), D.fold_row, D.fold_halo, D.fold_long, static_cast<const AT *>(D.halo),
-        D.lc0, D.lc1, D.lcfirst, D.lcslot, static_cast<const AT *>(D.lpart), m, h->ntiles, G.cond, 1);
+    if (!fused)
+        fold_mrs_kernel<XT, AT><<<fold_blocks(h), kRedBlock, 0, W.capture>>>(
+            static_cast<int>(L.fold_row.size()), D.fold_row, D.fold_halo, D.fold_long,
+            static_cast<const AT *>(D.halo), D.lc0, D.lc1, D.lcfirst, D.lcslot, static_cast<const AT *>(D.lpart), m,
+            h->ntiles, G.cond, 1);
     cudaGraph_t captured = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(W.capture, &captured);
     if (e == cudaSuccess) e = cudaGetLastError();

@@ -161,6 +161,7 @@ __device__ __forceinline__ AT half_row_warp(int e0, int e1, const VT *hval, cons
 // alpha x_r and is stored as y_r.
 template <typename XT, typename AT>
 struct EpiSpmv {
+    static constexpr bool kStage = false;   // reads no vectors at the end of the tile
     AT alpha;
     XT *y;
     __device__ __forceinline__ AT start(const XT *__restrict__ x, int r) const {
@@ -168,6 +169,10 @@ struct EpiSpmv {
     }
     __device__ __forceinline__ void finish(int r, AT v) { y[r] = static_cast<XT>(v); }
     __device__ __forceinline__ void end_block(int, double *) {}
+    __device__ __forceinline__ void bind(int, int, unsigned char *) {}
+    __device__ __forceinline__ uint32_t stage_bytes(int, int) const { return 0u; }
+    __device__ __forceinline__ void stage_issue(int, int, unsigned char *, uint64_t *) {}
+    __device__ __forceinline__ void stage_tail(int, int, unsigned char *, int, int) {}
 };
 
 // fp64 scalars of the MRS recurrence, kept on the device.  Per-iteration
@@ -177,10 +182,29 @@ struct MrsState {
     double gamma;      // gamma_{j+1}
     double t;          // t_{j+1}
     double alpha, tol;
+    // epilogue coefficients of the next iteration (see mrs_next_coeffs)
+    double e_scale, e_coef, e_inv_b2, e_r3, e_inv_rho, e_tau;
     int32_t j;         // last completed iteration
     int32_t jmax, done, pad;
     uint32_t ticket, pad2;
 };
+
+// Scalars of iteration j = st->j + 1, computed once by the thread that
+// finished iteration j - 1 (fp64 divisions are costly on this part, so no
+// other thread repeats them): w_j = raw / beta_{j-1} + (beta_{j-1} /
+// beta_{j-2}) w_{j-2}; lagged p_{j-1} = (w_{j-2} / beta_{j-2} - R[j-3,j-1]
+// p_{j-3}) / rho_{j-1} with R[j-3,j-1] = -s_{j-3} beta_{j-2}; x += tau_{j-1} p_{j-1}.
+__device__ __forceinline__ void mrs_next_coeffs(MrsState *st) {
+    const int j = st->j + 1;
+    const double b1 = st->beta[(j - 1) & 3];
+    const double b2 = j >= 2 ? st->beta[(j - 2) & 3] : 1.0;
+    st->e_scale = 1.0 / b1;
+    st->e_coef = j >= 2 ? b1 / b2 : 0.0;
+    st->e_inv_b2 = 1.0 / b2;
+    st->e_r3 = j >= 4 ? -st->s[(j - 3) & 3] * b2 : 0.0;
+    st->e_inv_rho = j >= 2 ? 1.0 / st->rho[(j - 1) & 3] : 0.0;
+    st->e_tau = j >= 2 ? st->tau[(j - 1) & 3] : 0.0;
+}
 
 // Lanczos epilogue of MRS iteration j (the tile kernel computes the raw
 // product S w_{j-1}): w_j = (S w_{j-1}) / beta_{j-1} + (beta_{j-1} /
@@ -188,8 +212,80 @@ struct MrsState {
 // w_{j-1}/beta_{j-1}), its squared norm over rows the fold does not touch,
 // and the lagged update of iteration j-1: p_{j-1} = (v_{j-1} - R[j-3,j-1]
 // p_{j-3}) / rho_{j-1}, x += tau_{j-1} p_{j-1}.
-template <typename XT, typename AT>
+// deterministic block sum of one double per thread (warp butterflies, then
+// warps in order)
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) s += red[w];
+    return s;   // valid on thread 0
+}
+
+// Last block of a grid to arrive: sums part[0..count) in a fixed order.
+// Returns true (on every thread of that block) and leaves the sum in *out
+// (thread 0).  Each block's partial was written by its thread 0, which
+// makes it visible device-wide before taking a ticket.
+__device__ __forceinline__ bool last_block_sum(unsigned *ticket, const double *part, int count, double *red,
+                                               double *out) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double v = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) v += __ldcg(part + i);
+    const double s = block_sum(v, red);
+    if (threadIdx.x == 0) {
+        *out = s;
+        *ticket = 0u;
+    }
+    return true;
+}
+
+
+// One step of the scalar recurrence after iteration j's norm ||w_j||^2 = tot
+// is known (one thread): beta_j, the Givens rotation, tau_j, t_{j+1},
+// gamma_{j+1}, the stop test and the next iteration's epilogue scalars; in a
+// graph, the while-node condition.
+__device__ __forceinline__ void mrs_step(MrsState *st, double tot, cudaGraphConditionalHandle cond, int in_graph) {
+    const int j = st->j + 1;
+    const double beta = sqrt(tot);
+    const double gam = st->gamma;
+    const double rho = hypot(gam, beta);
+    const double c = gam / rho, s = beta / rho;
+    const int k = j & 3;
+    st->beta[k] = beta;
+    st->rho[k] = rho;
+    st->c[k] = c;
+    st->s[k] = s;
+    st->tau[k] = c * st->t;
+    const double tn = -s * st->t;
+    st->t = tn;
+    st->gamma = st->alpha / c;
+    st->j = j;
+    const int done = (fabs(tn) <= st->tol) || (beta == 0.0) || (j >= st->jmax);
+    st->done = done;
+    mrs_next_coeffs(st);   // also the final lagged update uses them
+    if (in_graph) cudaGraphSetConditional(cond, done ? 0u : 1u);
+}
+
+template <typename XT, typename AT, bool S>
 struct EpiMrs {
+    // With S, the tile's slices of w_{j-2}, p_{j-3} and x are bulk-copied
+    // into shared memory at the start of the block (with the other staged
+    // data), so the epilogue reads them without a round trip to HBM at the
+    // end; without S (tiles too large for the extra shared memory) they are
+    // read from global memory.
+    static constexpr bool kStage = S;
     XT *y;
     const XT *wpp, *pold;
     XT *pnew, *xsol;
@@ -198,17 +294,61 @@ struct EpiMrs {
     AT scale, coef, inv_b2, r3, inv_rho, tau;
     bool lag;
     double nrm;
+    int r0;
+    const XT *s_wpp, *s_pold, *s_x;   // staged slices (tile-local index)
+    static PARS3_HD uint32_t slice_bytes(int T) {
+        return (static_cast<uint32_t>(T) * sizeof(XT) + 127u) & ~127u;
+    }
+    // bytes the bulk copies move (16-byte multiple of each slice)
+    __device__ __forceinline__ uint32_t stage_bytes(int, int nr) const {
+        const uint32_t b = (static_cast<uint32_t>(nr) * sizeof(XT)) & ~15u;
+        return (lag ? 3u : 1u) * b;
+    }
+    __device__ __forceinline__ void bind(int rr0, int T, unsigned char *area) {
+        r0 = rr0;
+        if (S) {
+            s_wpp = reinterpret_cast<const XT *>(area);
+            s_pold = reinterpret_cast<const XT *>(area + slice_bytes(T));
+            s_x = reinterpret_cast<const XT *>(area + 2u * slice_bytes(T));
+        } else {   // unstaged: the slices are the global vectors themselves
+            s_wpp = wpp + rr0;
+            s_pold = pold + rr0;
+            s_x = xsol + rr0;
+        }
+    }
+    __device__ __forceinline__ void stage_issue(int rr0, int nr, unsigned char *area, uint64_t *mbar) {
+        const uint32_t b = (static_cast<uint32_t>(nr) * sizeof(XT)) & ~15u;
+        if (b == 0) return;
+        bulk_g2s(const_cast<XT *>(s_wpp), wpp + rr0, b, mbar);
+        if (lag) {
+            bulk_g2s(const_cast<XT *>(s_pold), pold + rr0, b, mbar);
+            bulk_g2s(const_cast<XT *>(s_x), xsol + rr0, b, mbar);
+        }
+    }
+    // rows past the last 16-byte boundary of the slice: plain loads
+    __device__ __forceinline__ void stage_tail(int rr0, int nr, unsigned char *, int tid, int P) {
+        const int first = static_cast<int>(((static_cast<uint32_t>(nr) * sizeof(XT)) & ~15u) / sizeof(XT));
+        for (int q = first + tid; q < nr; q += P) {
+            const_cast<XT *>(s_wpp)[q] = wpp[rr0 + q];
+            if (lag) {
+                const_cast<XT *>(s_pold)[q] = pold[rr0 + q];
+                const_cast<XT *>(s_x)[q] = xsol[rr0 + q];
+            }
+        }
+    }
     __device__ __forceinline__ AT start(const XT *__restrict__, int) const { return AT(0); }
     __device__ __forceinline__ void finish(int r, AT raw) {
+        const int q = r - r0;
         AT w = raw * scale;
-        if (coef != AT(0)) w += coef * static_cast<AT>(wpp[r]);
+        const AT wp = static_cast<AT>(s_wpp[q]);
+        if (coef != AT(0)) w += coef * wp;
         const XT wx = static_cast<XT>(w);
         y[r] = wx;
         if (!((__ldg(fold_bits + (r >> 5)) >> (r & 31)) & 1u)) nrm += static_cast<double>(wx) * static_cast<double>(wx);
         if (lag) {
-            const AT pv = (static_cast<AT>(wpp[r]) * inv_b2 - r3 * static_cast<AT>(pold[r])) * inv_rho;
+            const AT pv = (wp * inv_b2 - r3 * static_cast<AT>(s_pold[q])) * inv_rho;
             pnew[r] = static_cast<XT>(pv);
-            xsol[r] = static_cast<XT>(static_cast<AT>(xsol[r]) + tau * pv);
+            xsol[r] = static_cast<XT>(static_cast<AT>(s_x[q]) + tau * pv);
         }
     }
     // fixed-order block sum of the thread norms into part[t]
@@ -228,13 +368,11 @@ struct EpiMrs {
     }
 };
 
-template <typename XT, typename AT>
-__device__ __forceinline__ EpiMrs<XT, AT> make_mrs_epi(const MrsState *st, XT *const *wr, XT *const *pr, XT *xsol,
+template <typename XT, typename AT, bool S>
+__device__ __forceinline__ EpiMrs<XT, AT, S> make_mrs_epi(const MrsState *st, XT *const *wr, XT *const *pr, XT *xsol,
                                                        const uint32_t *fold_bits, double *part, const XT **xop) {
-    EpiMrs<XT, AT> e;
+    EpiMrs<XT, AT, S> e;
     const int j = st->j + 1;
-    const double b1 = st->beta[(j - 1) & 3];
-    const double b2 = j >= 2 ? st->beta[(j - 2) & 3] : 1.0;
     *xop = wr[(j + 2) % 3];
     e.y = wr[j % 3];
     e.wpp = wr[(j + 1) % 3];
@@ -243,13 +381,13 @@ __device__ __forceinline__ EpiMrs<XT, AT> make_mrs_epi(const MrsState *st, XT *c
     e.xsol = xsol;
     e.fold_bits = fold_bits;
     e.part = part;
-    e.scale = static_cast<AT>(1.0 / b1);
-    e.coef = static_cast<AT>(j >= 2 ? b1 / b2 : 0.0);
+    e.scale = static_cast<AT>(st->e_scale);
+    e.coef = static_cast<AT>(st->e_coef);
     e.lag = j >= 2;
-    e.inv_b2 = static_cast<AT>(1.0 / b2);
-    e.r3 = static_cast<AT>(j >= 4 ? -st->s[(j - 3) & 3] * b2 : 0.0);
-    e.inv_rho = static_cast<AT>(j >= 2 ? 1.0 / st->rho[(j - 1) & 3] : 0.0);
-    e.tau = static_cast<AT>(j >= 2 ? st->tau[(j - 1) & 3] : 0.0);
+    e.inv_b2 = static_cast<AT>(st->e_inv_b2);
+    e.r3 = static_cast<AT>(st->e_r3);
+    e.inv_rho = static_cast<AT>(st->e_inv_rho);
+    e.tau = static_cast<AT>(st->e_tau);
     e.nrm = 0.0;
     return e;
 }
@@ -278,26 +416,34 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     const uint32_t rpb = static_cast<uint32_t>(a.T + 8) * 2u;
 
     // 0. the copy engine stages the x window and the middle entries (a tile
-    // without middle entries needs neither)
-    const bool staged = hm > 0;
+    // without middle entries needs neither), and the vectors the epilogue
+    // reads (Lanczos mode)
+    const bool stage_half = hm > 0;
+    const bool staged = stage_half || Epi::kStage;   // block-uniform
+    epi.bind(r0, a.T, smem + align128(L.total));
     if (staged && tid == 0) {
         mbar_init(mbar, 1);
         fence_mbar_init();
-        const uint32_t tx = nbulk + rpb + hmp * (sizeof(VT) + 4u);
+        uint32_t tx = epi.stage_bytes(r0, nr);
+        if (stage_half) tx += nbulk + rpb + hmp * (sizeof(VT) + 4u);
         mbar_arrive_expect_tx(mbar, tx);
-        if (nbulk > 0) bulk_g2s(xs + (wlo - wb), xop + wlo, nbulk, mbar);
-        bulk_g2s(hrp, a.hrp + static_cast<size_t>(t) * (a.T + 8), rpb, mbar);
-        bulk_g2s(hval, a.hval + hb, hmp * sizeof(VT), mbar);
-        bulk_g2s(hcol, a.hcol + hb, hmp * 2u, mbar);
-        bulk_g2s(cperm, a.hcperm + hb, hmp * 2u, mbar);
+        if (stage_half) {
+            if (nbulk > 0) bulk_g2s(xs + (wlo - wb), xop + wlo, nbulk, mbar);
+            bulk_g2s(hrp, a.hrp + static_cast<size_t>(t) * (a.T + 8), rpb, mbar);
+            bulk_g2s(hval, a.hval + hb, hmp * sizeof(VT), mbar);
+            bulk_g2s(hcol, a.hcol + hb, hmp * 2u, mbar);
+            bulk_g2s(cperm, a.hcperm + hb, hmp * 2u, mbar);
+        }
+        if constexpr (Epi::kStage) epi.stage_issue(r0, nr, smem + align128(L.total), mbar);
     }
-    if (staged) {
+    if (stage_half) {
         for (int g = wlo + static_cast<int>(nbulk / sizeof(XT)) + tid; g < r1; g += P) xs[g - wb] = xop[g];
         for (int p = tid; p < nr + a.W; p += P) {
             cs[p] = 0;
             ce[p] = 0;
         }
     }
+    if constexpr (Epi::kStage) epi.stage_tail(r0, nr, smem + align128(L.total), tid, P);
     __syncthreads();   // the barrier is initialised before anyone waits on it
 
     // 1. full pass (sliced ELL) straight from HBM while the copy runs
@@ -461,13 +607,23 @@ struct MrsVectors {
     double *part;
 };
 
-template <typename VT, typename XT, typename AT>
-__global__ void __launch_bounds__(kBlock, 2) tile_kernel_mrs(const SpmvArgs<VT, XT, AT> a, const MrsVectors<XT> m) {
+// With FUSED (no halo targets and no long rows, so nothing is left for a
+// fold), the last tile block to finish also reduces the partial norms and
+// runs the scalar step, and the loop body is this one launch.
+template <typename VT, typename XT, typename AT, bool S, bool FUSED>
+__global__ void __launch_bounds__(kBlock, 2) tile_kernel_mrs(const SpmvArgs<VT, XT, AT> a, const MrsVectors<XT> m,
+                                                            cudaGraphConditionalHandle cond) {
     extern __shared__ __align__(128) unsigned char smem[];
     const XT *xop = nullptr;
-    EpiMrs<XT, AT> epi = make_mrs_epi<XT, AT>(m.st, m.w, m.p, m.xsol, m.fold_bits, m.part, &xop);
+    EpiMrs<XT, AT, S> epi = make_mrs_epi<XT, AT, S>(m.st, m.w, m.p, m.xsol, m.fold_bits, m.part, &xop);
     if (static_cast<int>(blockIdx.x) < a.ntiles) tile_block<VT, XT, AT>(a, blockIdx.x, smem, xop, epi);
     else long_block<VT, XT, AT>(a, blockIdx.x - a.ntiles, smem, xop);
+    if constexpr (FUSED) {
+        __shared__ double red[32];
+        double tot = 0.0;
+        if (last_block_sum(&m.st->ticket, m.part, a.ntiles, red, &tot) && threadIdx.x == 0)
+            mrs_step(m.st, tot, cond, 1);
+    }
 }
 
 // One thread per receiving row: y[row] += halo sum, then the row's long-row
