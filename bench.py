@@ -318,20 +318,30 @@ def run_reference(args, ws, rank):
 
 
 def cpu_baseline(A, alpha, x, budget_s: float):
+    """The oracle on one host core: its full-storage row-sum SpMV (the
+    value) and the paper's serial SSS pair-update SpMV (Sec. 3.1.1, the
+    denominator of the paper's speedups), each on a bounded sample."""
     import oracle as O
     F = O.Full(A)
     F.apply(alpha, x)
-    t0 = time.perf_counter()
-    cnt = 0
-    while True:
-        F.apply(alpha, x)
-        cnt += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or cnt >= REPEATS:
-            break
-    gbs = alg_bytes(A.n, A.nnz, 8, 8) * cnt / el / 1e9
-    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{cnt} full-storage fp64 SpMVs of the whole matrix ({el:.1f} s, single thread)"}
+
+    def timed(fn, budget):
+        t0 = time.perf_counter()
+        cnt = 0
+        while True:
+            fn()
+            cnt += 1
+            el = time.perf_counter() - t0
+            if el >= budget or cnt >= REPEATS:
+                return cnt, el
+
+    cnt, el = timed(lambda: F.apply(alpha, x), budget_s)
+    ub = alg_bytes(A.n, A.nnz, 8, 8)
+    c2, e2 = timed(lambda: O.spmv_sss(A, alpha, x), max(budget_s / 4, 0.05))
+    return {"value": ub * cnt / el / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{cnt} full-storage fp64 SpMVs of the whole matrix ({el:.1f} s, single thread)",
+            "serial_sss": {"value": ub * c2 / e2 / 1e9, "unit": "GB/s", "us_per_product": 1e6 * e2 / c2,
+                           "sample": f"{c2} serial SSS pair-update SpMVs (Sec. 3.1.1), single thread"}}
 
 
 def mrs_section(A, perm, T, Wc, alphas, budget_iters: int):
@@ -404,6 +414,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg1")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--k", type=int, default=1, help="right-hand sides (k > 1 times pars3_spmm on an n x k block)")
     ap.add_argument("--T", type=int, default=-1, help="tile rows (default: pars3_autotune)")
     ap.add_argument("--W", type=int, default=-1, help="middle bandwidth (with --T)")
     ap.add_argument("--e2e-steps", type=int, default=1)
@@ -441,7 +452,8 @@ def main():
         T, Wc = args.T, args.W
     else:   # cut points from the autotuner (untimed preprocessing)
         t0 = time.perf_counter()
-        tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=dt, k=1, dtypes=P.dtype_bit(dt))
+        tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=dt, k=max(1, args.k),
+                                dtypes=P.dtype_bit(dt))
         t_tune = time.perf_counter() - t0
         T, Wc = tune["T"], tune["W"]
     t0 = time.perf_counter()
@@ -452,16 +464,29 @@ def main():
     t_up = time.perf_counter() - t0
     info = P.pars3_info_get(h)
 
-    xp = torch.from_numpy(x[perm]).to("cuda", vt)
+    k = max(1, args.k)
+    if k == 1:
+        xp = torch.from_numpy(x[perm]).to("cuda", vt)
+    else:   # the workload's x in column 0, further columns from the same generator
+        import workloads as W
+        Xk = W.vector("uniform", (A.n, k), W.SEED_BASE + 1, stream=91)
+        Xk[:, 0] = x
+        xp = torch.from_numpy(np.ascontiguousarray(Xk[perm])).to("cuda", vt)
     y = torch.empty_like(xp)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+
+    def product():
+        if k == 1:
+            P.pars3_spmv(h, dt, alpha, xp, y, stream)
+        else:
+            P.pars3_spmm(h, dt, alpha, xp, y, stream)
 
     def step(evs=None):
         for r in range(REPEATS):
             if evs is not None:
                 evs[r].record(stream)
-            P.pars3_spmv(h, dt, alpha, xp, y, stream)
+            product()
         if evs is not None:
             evs[REPEATS].record(stream)
 
@@ -489,17 +514,17 @@ def main():
     spmv_ms = [evs[s][r].elapsed_time(evs[s][r + 1]) for s in range(args.steps) for r in range(REPEATS)]
     tot_s = sum(step_ms) / 1e3
     tot_s = max_over_ranks(ws, tot_s)
-    ub = alg_bytes(A.n, A.nnz, sv, sx)
+    ub = alg_bytes(A.n, A.nnz, sv, sx, k)
     value = ub * REPEATS * args.steps * ws / tot_s / 1e9
     peak, peak_kind = measured_peaks()
     avg_spmv_s = statistics.mean(spmv_ms) / 1e3
     achieved = ub / avg_spmv_s / 1e9
     khash = kernel_source_hash()
-    traffic = traffic_from_profile(khash, 1.0) if (dt == P.F64 and args.workload == "cfg1") else None
+    traffic = traffic_from_profile(khash, 1.0) if (dt == P.F64 and args.workload == "cfg1" and k == 1) else None
 
     # end to end through the host-buffer entry point (original numbering)
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and k == 1:
         xh = torch.from_numpy(x.astype(np.float64 if dt == P.F64 else np.float32)).pin_memory().numpy()
         yh = torch.empty(A.n, dtype=vt).pin_memory().numpy()
         P.pars3_spmv_host(h, dt, alpha, xh, yh)
@@ -515,7 +540,7 @@ def main():
 
     cpu = cpu_baseline(A, alpha, x, args.cpu_budget) if (rank == 0 and ws == 1) else None
     mrs = None
-    if args.mrs and args.workload == "cfg1":
+    if args.mrs and args.workload == "cfg1" and k == 1:
         mrs = mrs_section(A, perm, info["T"], info["W"], [float(a) for a in args.mrs.split(",")], args.mrs_iters)
     launches_per_spmv = 1 + (1 if info["halo_targets"] + info["long_rows"] > 0 else 0)
     extra = extra_section(args, peak) if (args.extra and rank == 0) else None
@@ -525,7 +550,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "pct_hbm_peak": value / ws / peak,
-            "config": {"workload": f"{args.workload}: {desc}", "n": A.n, "nnz_stored": A.nnz, "alpha": alpha,
+            "config": {"workload": f"{args.workload}: {desc}" + (f", k = {k} right-hand sides" if k > 1 else ""),
+                       "n": A.n, "nnz_stored": A.nnz, "alpha": alpha, "k": k,
                        "repeats_per_step": REPEATS, "T": info["T"], "W": info["W"],
                        "rcm_bandwidth": bw1, "original_bandwidth": bw0,
                        "half_entries": info["half_entries"], "full_entries": info["full_entries"],

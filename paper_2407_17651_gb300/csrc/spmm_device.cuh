@@ -39,32 +39,48 @@ PARS3_HD SpmmLayout spmm_layout(uint32_t T, uint32_t W, uint32_t Mh, uint32_t vs
     return s;
 }
 
-// NV consecutive elements of a row of X (a 16-byte vector when NV > 1)
+// L2 policy for the gathered rows of X: kept (evict-last) while the matrix
+// and Y stream through L2 with evict-first, so a row of X that several rows
+// of the tile reference is read from HBM once.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// NV consecutive elements of a row of X (a 16-byte vector when NV > 1):
+// gathers with the keep policy, stores of Y streaming (evict-first)
 template <typename XT, int NV> struct XVec;
-template <typename XT> struct XVec<XT, 1> {
-    static __device__ __forceinline__ void ld(const XT *p, XT *o) { o[0] = __ldg(p); }
-    static __device__ __forceinline__ void st(XT *p, const XT *o) { p[0] = o[0]; }
+template <> struct XVec<float, 1> {
+    static __device__ __forceinline__ void ld(const float *p, float *o, uint64_t pol) {
+        asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(o[0]) : "l"(p), "l"(pol));
+    }
+    static __device__ __forceinline__ void st(float *p, const float *o) { __stcs(p, o[0]); }
+};
+template <> struct XVec<double, 1> {
+    static __device__ __forceinline__ void ld(const double *p, double *o, uint64_t pol) {
+        asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(o[0]) : "l"(p), "l"(pol));
+    }
+    static __device__ __forceinline__ void st(double *p, const double *o) { __stcs(p, o[0]); }
 };
 template <> struct XVec<float, 4> {
-    static __device__ __forceinline__ void ld(const float *p, float *o) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-        o[0] = v.x;
-        o[1] = v.y;
-        o[2] = v.z;
-        o[3] = v.w;
+    static __device__ __forceinline__ void ld(const float *p, float *o, uint64_t pol) {
+        asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3])
+                     : "l"(p), "l"(pol));
     }
     static __device__ __forceinline__ void st(float *p, const float *o) {
-        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(o[0], o[1], o[2], o[3]));
     }
 };
 template <> struct XVec<double, 2> {
-    static __device__ __forceinline__ void ld(const double *p, double *o) {
-        const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
-        o[0] = v.x;
-        o[1] = v.y;
+    static __device__ __forceinline__ void ld(const double *p, double *o, uint64_t pol) {
+        asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                     : "=d"(o[0]), "=d"(o[1])
+                     : "l"(p), "l"(pol));
     }
     static __device__ __forceinline__ void st(double *p, const double *o) {
-        *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+        __stcs(reinterpret_cast<double2 *>(p), make_double2(o[0], o[1]));
     }
 };
 
@@ -95,6 +111,7 @@ __device__ __forceinline__ void spmm_strided_sum(const VT *__restrict__ val, con
                                                  int64_t base, int64_t stride, int len, const XT *__restrict__ X,
                                                  int k, int c0, bool on, AT *acc) {
     constexpr int U = spmm_unroll<AT, NV>();
+    const uint64_t pol = l2_keep_policy();
     for (int m0 = 0; m0 < len; m0 += U) {
         AT v[U];
         int j[U];
@@ -105,14 +122,14 @@ __device__ __forceinline__ void spmm_strided_sum(const VT *__restrict__ val, con
             j[u] = 0;
             if (m0 + u < len) {
                 const int64_t q = base + static_cast<int64_t>(m0 + u) * stride;
-                v[u] = static_cast<AT>(Val<VT>::ld(val + q));
-                j[u] = __ldg(col + q);
+                v[u] = static_cast<AT>(Val<VT>::ld_stream(val + q));
+                j[u] = __ldcs(col + q);
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (on && m0 + u < len) {
-                XVec<XT, NV>::ld(X + static_cast<int64_t>(j[u]) * k + c0, xv[u]);
+                XVec<XT, NV>::ld(X + static_cast<int64_t>(j[u]) * k + c0, xv[u], pol);
             } else {
 #pragma unroll
                 for (int w = 0; w < NV; ++w) xv[u][w] = XT(0);
@@ -135,6 +152,7 @@ __device__ __forceinline__ void spmm_smem_sum(const VT *hval, const uint16_t *or
                                               int q1, int64_t xbase, const XT *__restrict__ X, int k, int c0,
                                               bool on, AT *acc) {
     constexpr int U = spmm_unroll<AT, NV>();
+    const uint64_t pol = l2_keep_policy();
     for (int m0 = q0; m0 < q1; m0 += U) {
         AT v[U];
         XT xv[U][NV];
@@ -144,7 +162,7 @@ __device__ __forceinline__ void spmm_smem_sum(const VT *hval, const uint16_t *or
             if (m0 + u < q1) {
                 const int e = order ? order[m0 + u] : m0 + u;
                 v[u] = sval<VT>(hval, e);
-                if (on) XVec<XT, NV>::ld(X + (xbase + xidx[e]) * k + c0, xv[u]);
+                if (on) XVec<XT, NV>::ld(X + (xbase + xidx[e]) * k + c0, xv[u], pol);
             }
             if (!(on && m0 + u < q1)) {
 #pragma unroll
@@ -220,7 +238,7 @@ __device__ __forceinline__ void spmm_tile(const SpmvArgs<VT, XT, AT> &a, int k, 
         AT acc[NV];
         {
             XT xr[NV];
-            if (on) XVec<XT, NV>::ld(a.x + row * k + c0, xr);
+            if (on) XVec<XT, NV>::ld(a.x + row * k + c0, xr, l2_keep_policy());
 #pragma unroll
             for (int w = 0; w < NV; ++w) acc[w] = on ? a.alpha * static_cast<AT>(xr[w]) : AT(0);
         }
