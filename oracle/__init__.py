@@ -58,17 +58,17 @@ def _L():
             P = C.c_void_p
             i32, i64, f64 = C.c_int32, C.c_int64, C.c_double
             lib.orc_validate.argtypes = [i32, P, P]
-            lib.orc_full_csr.argtypes = [i32, P, P, P, P, P, P]
+            lib.orc_full_csr.argtypes = [i32, P, P, P, f64, P, P, P]
             lib.orc_spmv_full.argtypes = [i32, f64, P, P, P, P, P]
             lib.orc_spmv_full.restype = None
             lib.orc_spmm_full.argtypes = [i32, i32, f64, P, P, P, P, P]
             lib.orc_spmm_full.restype = None
-            lib.orc_spmv_sss.argtypes = [i32, f64, P, P, P, P, P]
+            lib.orc_spmv_sss.argtypes = [i32, f64, f64, P, P, P, P, P]
             lib.orc_spmv_sss.restype = None
             lib.orc_bandwidth.argtypes = [i32, P, P, P]
             lib.orc_bandwidth.restype = i64
             lib.orc_rcm.argtypes = [i32, P, P, i32, P, P, P]
-            lib.orc_split.argtypes = [i32, P, P, P, P, i32, i32, P, P, P, P, P, P, P, P, P]
+            lib.orc_split.argtypes = [i32, P, P, P, f64, P, i32, i32, P, P, P, P, P, P, P, P, P]
             lib.orc_auto_cut.argtypes = [i64, i32, i32, i32, P, P]
             lib.orc_auto_cut.restype = None
             _lib = lib
@@ -96,15 +96,17 @@ def validate(A) -> int:
 
 
 class Full:
-    """Full-storage CSR of S = L - L^T."""
+    """Full-storage CSR of S = L + mirror L^T (mirror -1: skew-symmetric, the
+    paper's case; +1: symmetric)."""
 
-    def __init__(self, A):
+    def __init__(self, A, mirror: float = -1.0):
         rp, ci, v = _csr(A)
         self.n = A.n
         self.rowptr = np.zeros(A.n + 1, dtype=np.int64)
         self.col = np.zeros(2 * ci.shape[0], dtype=np.int32)
         self.val = np.zeros(2 * ci.shape[0], dtype=np.float64)
-        rc = _L().orc_full_csr(A.n, _p(rp), _p(ci), _p(v), _p(self.rowptr), _p(self.col), _p(self.val))
+        rc = _L().orc_full_csr(A.n, _p(rp), _p(ci), _p(v), float(mirror), _p(self.rowptr), _p(self.col),
+                               _p(self.val))
         if rc != 0:
             raise MemoryError("orc_full_csr")
 
@@ -139,26 +141,26 @@ class Full:
         return Y
 
 
-def spmv_full(A, alpha: float, x: np.ndarray) -> np.ndarray:
+def spmv_full(A, alpha: float, x: np.ndarray, mirror: float = -1.0) -> np.ndarray:
     """y = (alpha I + S) x through the full-storage CSR of the unreordered S."""
-    return Full(A).apply(alpha, x)
+    return Full(A, mirror).apply(alpha, x)
 
 
-def spmv_sss(A, alpha: float, x: np.ndarray) -> np.ndarray:
+def spmv_sss(A, alpha: float, x: np.ndarray, mirror: float = -1.0) -> np.ndarray:
     """The serial SSS skew SpMV of Sec. 3.1.1 (pair update of Eqs. 2-6)."""
     rp, ci, v = _csr(A)
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty(A.n, dtype=np.float64)
-    _L().orc_spmv_sss(A.n, float(alpha), _p(rp), _p(ci), _p(v), _p(x), _p(y))
+    _L().orc_spmv_sss(A.n, float(alpha), float(mirror), _p(rp), _p(ci), _p(v), _p(x), _p(y))
     return y
 
 
-def dense(A) -> np.ndarray:
-    """Dense S = L - L^T (brute force for tiny n)."""
+def dense(A, mirror: float = -1.0) -> np.ndarray:
+    """Dense S = L + mirror L^T (brute force for tiny n)."""
     S = np.zeros((A.n, A.n), dtype=np.float64)
     rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
     S[rows, A.col] = A.val
-    S[A.col, rows] = -A.val
+    S[A.col, rows] = mirror * A.val
     return S
 
 
@@ -192,7 +194,7 @@ def rcm(A, guard: bool = True):
 # O3 split
 # ---------------------------------------------------------------------------
 
-def split(A, perm, T: int, W: int) -> dict:
+def split(A, perm, T: int, W: int, mirror: float = -1.0) -> dict:
     """Canonical 3-way split (see orc_split in oracle.c)."""
     rp, ci, v = _csr(A)
     n, nnz = A.n, ci.shape[0]
@@ -204,7 +206,7 @@ def split(A, perm, T: int, W: int) -> dict:
         tile_ptr=np.zeros(ntiles + 1, dtype=np.int32), tile_list=np.zeros(nnz, dtype=np.int32),
         outer_csr=np.zeros(nnz, dtype=np.int32), outer_csc=np.zeros(nnz, dtype=np.int32),
         counts=np.zeros(3, dtype=np.int64))
-    rc = _L().orc_split(n, _p(rp), _p(ci), _p(v), _p(perm), int(T), int(W),
+    rc = _L().orc_split(n, _p(rp), _p(ci), _p(v), float(mirror), _p(perm), int(T), int(W),
                         _p(out["rowptr"]), _p(out["col"]), _p(out["val"]), _p(out["cls"]),
                         _p(out["tile_ptr"]), _p(out["tile_list"]), _p(out["outer_csr"]),
                         _p(out["outer_csc"]), _p(out["counts"]))

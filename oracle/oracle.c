@@ -13,9 +13,14 @@
  * half storage of Sec. 3): row pointers rp[n+1], sorted unique column
  * indices ci[nnz] with ci < row, values v[nnz].  All arithmetic is FP64.
  *
+ * The mirror sign m is -1 for the skew-symmetric S = L - L^T of the paper
+ * and +1 for the symmetric S = L + L^T, to which the paper says the same
+ * method applies (abstract; Sec. 5): the stored l_ij acts as s_ij = l_ij
+ * and s_ji = m l_ij.
+ *
  * Functions:
  *   orc_validate     input checks (strict lower, sorted, unique, in range)
- *   orc_full_csr     full storage of S = L - L^T           (Sec. 1, Eq. 1)
+ *   orc_full_csr     full storage of S = L + m L^T         (Sec. 1, Eq. 1)
  *   orc_spmv_full    y = (alpha I + S) x by plain row sums   (Sec. 1)
  *   orc_spmv_sss     the serial SSS skew SpMV baseline       (Sec. 3.1.1)
  *   orc_rcm          reverse Cuthill-McKee ordering          (Sec. 1, 3.1.2)
@@ -59,7 +64,7 @@ int orc_validate(int32_t n, const int32_t *rp, const int32_t *ci)
 /* Full-storage CSR of S = L - L^T (Eq. 1: A = -A^T; Sec. 1: CRS stores every
  * nonzero).  Row i holds s_ij = l_ij for j < i and s_ij = -l_ji for j > i,
  * columns ascending.  frp has n+1 entries, fci/fv have 2*nnz entries. */
-int orc_full_csr(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
+int orc_full_csr(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double mirror,
                  int64_t *frp, int32_t *fci, double *fv)
 {
     int64_t *fill = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
@@ -81,13 +86,13 @@ int orc_full_csr(int32_t n, const int32_t *rp, const int32_t *ci, const double *
             fill[i]++;
         }
     }
-    /* then the mirrored upper part: row j receives (j, i, -l_ij); visiting i
+    /* then the mirrored upper part: row j receives (j, i, m l_ij); visiting i
      * in increasing order keeps the columns of row j ascending */
     for (int32_t i = 0; i < n; i++)
         for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
             int32_t j = ci[k];
             fci[fill[j]] = i;
-            fv[fill[j]] = -v[k];
+            fv[fill[j]] = mirror * v[k];
             fill[j]++;
         }
     free(fill);
@@ -122,7 +127,7 @@ void orc_spmm_full(int32_t n, int32_t k, double alpha, const int64_t *frp, const
 /* The paper's serial baseline (Sec. 3.1.1, adapted to skew symmetry, with the
  * pair update of Eqs. 2-6): every stored l_ij is read once and used twice,
  * y_i += l_ij x_j and y_j += (-l_ij) x_i. */
-void orc_spmv_sss(int32_t n, double alpha, const int32_t *rp, const int32_t *ci,
+void orc_spmv_sss(int32_t n, double alpha, double mirror, const int32_t *rp, const int32_t *ci,
                   const double *v, const double *x, double *y)
 {
     for (int32_t i = 0; i < n; i++) y[i] = alpha * x[i];
@@ -131,7 +136,7 @@ void orc_spmv_sss(int32_t n, double alpha, const int32_t *rp, const int32_t *ci,
             int32_t j = ci[k];
             double a = v[k];
             y[i] += a * x[j];          /* Eq. 3 and Eq. 5 */
-            y[j] += (-a) * x[i];       /* Eq. 2, Eq. 4 and Eq. 6 */
+            y[j] += (mirror * a) * x[i];   /* Eq. 2, Eq. 4 and Eq. 6 (m = -1) */
         }
 }
 
@@ -291,7 +296,7 @@ static int cmp_entry_cr(const void *pa, const void *pb)
  *  - counts[0..2]: number of entries of each class.
  * Arrays are caller-allocated: brp[n+1], bci/bv/cls[nnz], tile_ptr[ntiles+1],
  * tile_list[nnz], outer_csr/outer_csc[nnz]. */
-int orc_split(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
+int orc_split(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double mirror,
               const int32_t *perm, int32_t T, int32_t W,
               int32_t *brp, int32_t *bci, double *bv, uint8_t *cls,
               int32_t *tile_ptr, int32_t *tile_list, int32_t *outer_csr, int32_t *outer_csc,
@@ -313,7 +318,7 @@ int orc_split(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
         for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
             int32_t a = pinv[i], b = pinv[ci[k]];
             if (a > b) { tr[m].r = a; tr[m].c = b; tr[m].v = v[k]; }
-            else       { tr[m].r = b; tr[m].c = a; tr[m].v = -v[k]; }
+            else       { tr[m].r = b; tr[m].c = a; tr[m].v = mirror * v[k]; }
             m++;
         }
     qsort(tr, (size_t)nnz, sizeof(orc_trip), cmp_trip_rc);
