@@ -186,7 +186,8 @@ def time_products(P, torch, h, dt, alpha, xp, y, flush, reps=50, groups=5):
 def extra_section(args, peak):
     """The other workloads, each reported beside the headline: a
     band-friendly 2D grid (2048 x 1024, RCM bandwidth about 1024: the
-    half-storage middle band holds the matrix), the R-MAT matrix in FP64 and
+    half-storage middle band holds the matrix), the headline matrix as a
+    symmetric operator, the R-MAT matrix in FP64 and
     FP32 (cut points from pars3_autotune), and the batched workload (64
     uneven grids, k in {1, 4, 16, 32}, FP32 and FP64, one persistent launch
     replayed from a CUDA graph, cut points from pars3_autotune per matrix)."""
@@ -198,14 +199,15 @@ def extra_section(args, peak):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     both = P.dtype_bit(P.F64) | P.dtype_bit(P.F32)
 
-    def single(name, A, alpha, x, desc):
+    def single(name, A, alpha, x, desc, symmetric=False):
         t0 = time.perf_counter()
         perm, bw0, bw1 = P.pars3_reorder(A.n, A.rowptr, A.col)
         t_rcm = time.perf_counter() - t0
         t0 = time.perf_counter()
         tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=P.F64, k=1, dtypes=both)
         t_tune = time.perf_counter() - t0
-        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=tune["T"], W=tune["W"], dtypes=both)
+        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=tune["T"], W=tune["W"], dtypes=both,
+                          symmetric=symmetric)
         P.pars3_upload(h)
         info = P.pars3_info_get(h)
         row = {"workload": desc, "n": A.n, "nnz_stored": A.nnz, "alpha": alpha, "rcm_bandwidth": bw1,
@@ -229,6 +231,11 @@ def extra_section(args, peak):
     single("grid2d", A, 0.5, W.vector("uniform", A.n, W.SEED_BASE + 5),
            "grid2d 2048x1024 (band-friendly: RCM bandwidth ~1024), N(0,1), alpha=0.5")
     out["grid2d"]["section_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    A, alpha, x = W.config1()
+    single("cfg1_symmetric", A, alpha, x, "the 128^3 + 1% matrix as the symmetric S = L + L^T "
+           "(PARS3_SPLIT_SYMMETRIC), alpha=0.5", symmetric=True)
+    out["cfg1_symmetric"]["section_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     A, alpha, x = W.config2()
     single("cfg2", A, alpha, x, "R-MAT scale 22, 20M stored, U(-1,1), alpha=0, cut points autotuned")

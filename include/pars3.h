@@ -61,6 +61,9 @@ extern "C" {
 
 /* ---------------------------------------------------------------- flags */
 #define PARS3_RCM_GUARD 1 /* pars3_reorder: return the identity when RCM would widen the band */
+#define PARS3_SPLIT_SYMMETRIC 1 /* pars3_split_params.flags: S = L + L^T (the symmetric variant the
+                                   paper's method also covers, abstract and Sec. 5) instead of the
+                                   skew-symmetric S = L - L^T */
 
 typedef struct pars3_handle pars3_handle;
 
@@ -75,7 +78,8 @@ typedef struct {
     int32_t W;          /* middle bandwidth: stored (i, j) with i - j <= W are middle entries */
     int32_t dtypes;     /* bit mask of PARS3_DTYPE_BIT(d) value precisions to pack (0 = F64 only) */
     int32_t long_row;   /* full-storage row length above which a row is processed in chunks (0 = default) */
-    int32_t reserved[4];
+    int32_t flags;      /* 0 (skew-symmetric) or PARS3_SPLIT_SYMMETRIC */
+    int32_t reserved[3];
 } pars3_split_params;
 
 /* Read-only view of a handle's canonical split (host memory owned by the
@@ -88,7 +92,7 @@ typedef struct {
     const int32_t *perm;         /* [n] new -> old */
     const int32_t *rowptr;       /* [n+1] strict-lower CSR of P S P^T */
     const int32_t *col;          /* [nnz] */
-    const double *val;           /* [nnz] (mirrored entries carry the flipped sign) */
+    const double *val;           /* [nnz] (skew: an entry whose orientation flipped carries the flipped sign) */
     const uint8_t *cls;          /* [nnz] 0 middle-local, 1 middle-halo, 2 outer */
     const int32_t *tile_ptr;     /* [ntiles+1] */
     const int32_t *tile_list;    /* [counts0+counts1] middle entries of each tile, (column, row) order */
@@ -110,6 +114,8 @@ typedef struct {
     int64_t device_bytes;        /* device memory held by the handle after upload */
     int64_t bytes_per_spmv[3];   /* modelled DRAM bytes of one pars3_spmv per precision */
     int64_t bandwidth;           /* max i - j of the reordered lower triangle */
+    int32_t symmetric;           /* 1 for a PARS3_SPLIT_SYMMETRIC handle */
+    int32_t reserved;
 } pars3_info;
 
 /* MRS options (Sec. 1: minimal residual method for shifted skew systems,
@@ -219,8 +225,9 @@ int pars3_spmm_batched(pars3_handle *const *hs, int32_t count, int32_t dtype, co
  * and norms in fp64).  The inner loop runs as a CUDA graph with a
  * device-side while-condition; the host only syncs once per refinement
  * cycle.  alpha must be nonzero.  res may be NULL.  Errors: EINVAL, ESTATE,
- * EUNSUPPORTED, ENOCONV (limit reached; x holds the best iterate), ECUDA,
- * ETIMEOUT. */
+ * EUNSUPPORTED (also for a PARS3_SPLIT_SYMMETRIC handle: the recurrence
+ * needs a skew-symmetric S), ENOCONV (limit reached; x holds the best
+ * iterate), ECUDA, ETIMEOUT. */
 int pars3_mrs(const pars3_handle *h, double alpha, const double *b, double *x,
               const pars3_mrs_opts *opts, pars3_mrs_result *res, void *stream);
 

@@ -160,6 +160,7 @@ static SpmvArgs<VT, XT, AT> make_args(const pars3_handle *h, int dtype, double a
     a.y = static_cast<XT *>(Y);
     a.alpha = static_cast<AT>(alpha);
     a.err = D.err;
+    a.sym = h->symmetric;
     return a;
 }
 

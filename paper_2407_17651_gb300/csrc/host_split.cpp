@@ -86,7 +86,7 @@ static void canonical_reorder(pars3_handle *h, const int32_t *rowptr, const int3
         for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k, ++e) {
             int32_t a = pinv[i], b = pinv[col[k]];
             if (a > b) { r[e] = a; c[e] = b; v[e] = val[k]; }
-            else       { r[e] = b; c[e] = a; v[e] = -val[k]; }
+            else       { r[e] = b; c[e] = a; v[e] = h->symmetric ? val[k] : -val[k]; }
         }
     }
     // sort by (row, col): bucket by row (one counting pass), then sort each
@@ -447,7 +447,7 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
         for (size_t q = 0; q < m; ++q) {
             const int32_t s = src[q];
             if (s == 0) continue;
-            const double a = s > 0 ? h->val[s - 1] : -h->val[-s - 1];
+            const double a = s > 0 ? h->val[s - 1] : (h->symmetric ? h->val[-s - 1] : -h->val[-s - 1]);
             const float f = static_cast<float>(a);
             if (!v64.empty()) v64[q] = a;
             if (!v32.empty()) v32[q] = f;
@@ -508,6 +508,7 @@ int split_recut(const pars3_handle *src, int32_t T, int32_t W, pars3_handle **ou
         h->nnz = src->nnz;
         h->dtypes = src->dtypes;
         h->long_row = src->long_row;
+        h->symmetric = src->symmetric;
         h->perm = src->perm;
         h->rowptr = src->rowptr;
         h->col = src->col;
@@ -544,6 +545,7 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
     if (p) prm = *p;
     if (prm.dtypes == 0) prm.dtypes = PARS3_DTYPE_BIT(PARS3_F64);
     if (prm.dtypes & ~7) return PARS3_EINVAL;
+    if (prm.flags & ~PARS3_SPLIT_SYMMETRIC) return PARS3_EINVAL;
     if ((prm.T == 0) != (prm.W == 0)) return PARS3_EINVAL;
     pars3_handle *h = nullptr;
     try {
@@ -551,6 +553,7 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
         h->n = n;
         h->nnz = nnz;
         h->dtypes = prm.dtypes;
+        h->symmetric = (prm.flags & PARS3_SPLIT_SYMMETRIC) ? 1 : 0;
         h->perm.resize(n);
         if (perm) {
             std::vector<uint8_t> seen(n, 0);
@@ -635,6 +638,7 @@ extern "C" int pars3_info_get(const pars3_handle *h, pars3_info *o) {
     }
     o->device_bytes = h->D.bytes;
     o->bandwidth = h->bw;
+    o->symmetric = h->symmetric;
     return PARS3_OK;
 }
 
@@ -645,6 +649,7 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
     const Layout &L = h->L;
     const int32_t n = h->n, T = h->T, W = h->W;
     const bool has64 = (h->dtypes & PARS3_DTYPE_BIT(PARS3_F64)) != 0;
+    const double mirror = h->symmetric ? 1.0 : -1.0;
     try {
         struct E { int32_t r, c; double v; };
         std::vector<E> want, got;
@@ -652,7 +657,7 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
         for (int32_t i = 0; i < n; ++i)
             for (int32_t e = h->rowptr[i]; e < h->rowptr[i + 1]; ++e) {
                 want.push_back({i, h->col[e], h->val[e]});
-                want.push_back({h->col[e], i, -h->val[e]});
+                want.push_back({h->col[e], i, mirror * h->val[e]});
             }
         got.reserve(2 * h->nnz);
         for (int32_t t = 0; t < h->ntiles; ++t) {
@@ -666,7 +671,7 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
                     if (j < std::max(wb, 0) || j >= i || i - j > W) return PARS3_EINVAL;
                     const double a = has64 ? L.hval64[L.hoff[t] + q] : 0.0;
                     got.push_back({i, j, a});
-                    got.push_back({j, i, -a});
+                    got.push_back({j, i, mirror * a});
                 }
             for (int32_t q = 0; q < L.hcnt[t]; ++q) {
                 const uint16_t e = L.hcperm[L.hoff[t] + q];

@@ -100,6 +100,7 @@ struct pars3_handle {
     int32_t T = 0, W = 0, ntiles = 0;
     int32_t dtypes = 0;
     int32_t long_row = 0;
+    int32_t symmetric = 0;           // S = L + L^T instead of L - L^T (mirror sign +1)
     int64_t bw = 0;
     // canonical split (host)
     std::vector<int32_t> perm, rowptr, col;

@@ -265,6 +265,7 @@ static SpmvArgs<VT, XT, AT> spmv_args(const pars3_handle *h, int dtype) {
     a.y = nullptr;
     a.alpha = AT(0);
     a.err = D.err;
+    a.sym = h->symmetric;
     return a;
 }
 
@@ -454,6 +455,7 @@ extern "C" int pars3_mrs(const pars3_handle *hc, double alpha, const double *b, 
     if (inner < 0 || inner >= kNumDtypes) return PARS3_EINVAL;
     if (!(h->dtypes & PARS3_DTYPE_BIT(PARS3_F64)) || !(h->dtypes & PARS3_DTYPE_BIT(inner))) return PARS3_EUNSUPPORTED;
     if (!h->uploaded) return PARS3_ESTATE;
+    if (h->symmetric) return PARS3_EUNSUPPORTED;   // the recurrence needs a skew-symmetric S
     if (h->n > 0 && (!b || !x || (reinterpret_cast<uintptr_t>(b) & 15u) || (reinterpret_cast<uintptr_t>(x) & 15u)))
         return PARS3_EINVAL;
     pars3_mrs_result r{};

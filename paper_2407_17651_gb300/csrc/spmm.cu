@@ -94,6 +94,7 @@ static int launch_spmm_lpr(const pars3_handle *h, int dtype, double alpha, int k
     a.y = static_cast<XT *>(Y);
     a.alpha = static_cast<AT>(alpha);
     a.err = D.err;
+    a.sym = h->symmetric;
     const int smem = spmm_smem_bytes(h, dtype);
     static std::atomic<int> configured{0};
     if (!configured.load()) {

@@ -253,7 +253,7 @@ __device__ __forceinline__ void spmm_tile(const SpmvArgs<VT, XT, AT> &a, int k, 
                 for (int w = 0; w < NV; ++w) cm[w] = AT(0);
                 spmm_smem_sum<VT, XT, AT, NV>(hval, cperm, hrow, cs[p], ce[p], r0, a.x, k, c0, on, cm);
 #pragma unroll
-                for (int w = 0; w < NV; ++w) acc[w] = acc[w] - cm[w];
+                for (int w = 0; w < NV; ++w) acc[w] = a.sym ? acc[w] + cm[w] : acc[w] - cm[w];
             }
         }
         if (on) {
@@ -273,7 +273,7 @@ __device__ __forceinline__ void spmm_tile(const SpmvArgs<VT, XT, AT> &a, int k, 
         spmm_smem_sum<VT, XT, AT, NV>(hval, cperm, hrow, cs[p], ce[p], r0, a.x, k, c0, on, cm);
         if (on)
 #pragma unroll
-            for (int w = 0; w < NV; ++w) a.halo[static_cast<int64_t>(h) * k + c0 + w] = -cm[w];
+            for (int w = 0; w < NV; ++w) a.halo[static_cast<int64_t>(h) * k + c0 + w] = a.sym ? cm[w] : -cm[w];
     }
 }
 

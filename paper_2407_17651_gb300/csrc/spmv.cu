@@ -61,6 +61,7 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     a.y = static_cast<XT *>(y);
     a.alpha = static_cast<AT>(alpha);
     a.err = D.err;
+    a.sym = h->symmetric;
     const int smem = smem_bytes_for(h, dtype);
     static std::atomic<int> configured{0};
     if (!configured.load()) {

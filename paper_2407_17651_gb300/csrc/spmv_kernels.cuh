@@ -56,6 +56,7 @@ struct SpmvArgs {
     XT *y;
     AT alpha;
     int32_t *err;
+    int32_t sym;   // 1: S = L + L^T (mirrored sums added), 0: S = L - L^T (subtracted)
 };
 
 template <typename VT> __device__ __forceinline__ typename Val<VT>::acc sval(const VT *p, int e);
@@ -530,14 +531,14 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
         const int k0 = cs[p], k1 = ce[p];
         AT c = AT(0);
         for (int k = k0; k < k1; ++k) c += qq[cperm[k]];
-        epi.finish(r0 + r, k1 > k0 ? rowacc[r] - c : rowacc[r]);
+        epi.finish(r0 + r, k1 > k0 ? (a.sym ? rowacc[r] + c : rowacc[r] - c) : rowacc[r]);
     }
     const int g0 = a.hhoff[t], g1 = a.hhoff[t + 1];
     for (int h = g0 + tid; h < g1; h += P) {
         const int p = a.hhrow[h] - wb;
         AT c = AT(0);
         for (int k = cs[p]; k < ce[p]; ++k) c += qq[cperm[k]];
-        a.halo[h] = -c;
+        a.halo[h] = a.sym ? c : -c;
     }
     epi.end_block(t, red);
 }

@@ -162,3 +162,31 @@ def test_invalid_inputs():
     assert P.lib().pars3_spmv(h, 0, 1.0, None, None, None) == P.ESTATE
     assert P.lib().pars3_spmv(h, 2, 1.0, None, None, None) == P.EUNSUPPORTED
     assert P.pars3_strerror(P.ENOTSKEW).startswith("input is not")
+
+
+@pytest.mark.parametrize("idx", range(9))
+@pytest.mark.parametrize("TW", [(32, 32), (1024, 256)])
+def test_symmetric_split_bit_exact(idx, TW):
+    """PARS3_SPLIT_SYMMETRIC: an entry whose orientation flips keeps its
+    sign; the split is the oracle's with mirror sign +1, bit for bit."""
+    A = list(_mats())[idx]
+    T, Wc = TW
+    perm = O.rcm(A)[0] if idx % 2 else np.random.default_rng(idx).permutation(A.n).astype(np.int32)
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=Wc, dtypes=7, symmetric=True)
+    ex = P.pars3_split_export(h)
+    so = O.split(A, perm, T, Wc, mirror=+1.0)
+    for k in KEYS:
+        assert np.array_equal(ex[k], so[k]), k
+    assert P.pars3_layout_check(h) == 0
+    assert P.pars3_info_get(h)["symmetric"] == 1
+
+
+def test_split_rejects_unknown_flags():
+    A = list(_mats())[0]
+    prm = P.pars3_split_params(T=64, W=32, dtypes=1, flags=2)
+    out = P.C.c_void_p()
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.col, dtype=np.int32)
+    v = np.ascontiguousarray(A.val, dtype=np.float64)
+    rc = P.lib().pars3_split(A.n, P._p(rp), P._p(ci), P._p(v), None, P.C.byref(prm), P.C.byref(out))
+    assert rc == P.EINVAL
