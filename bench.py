@@ -227,6 +227,10 @@ def extra_section(args, peak):
         out[name] = row
 
     t0 = time.perf_counter()
+    A, alpha, x = W.config0()
+    single("cfg0", A, alpha, x, "grid2d 200x100 (n = 20,000), U(-1,1), alpha=0 (small: latency-bound, report us)")
+    out["cfg0"]["section_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
     A = W.grid((2048, 1024), "normal", W.SEED_BASE + 5, name="grid2d_2048x1024")
     single("grid2d", A, 0.5, W.vector("uniform", A.n, W.SEED_BASE + 5),
            "grid2d 2048x1024 (band-friendly: RCM bandwidth ~1024), N(0,1), alpha=0.5")
