@@ -23,7 +23,8 @@
  *   orc_full_csr     full storage of S = L + m L^T         (Sec. 1, Eq. 1)
  *   orc_spmv_full    y = (alpha I + S) x by plain row sums   (Sec. 1)
  *   orc_spmv_sss     the serial SSS skew SpMV baseline       (Sec. 3.1.1)
- *   orc_rcm          reverse Cuthill-McKee ordering          (Sec. 1, 3.1.2)
+ *   orc_rcm          reverse Cuthill-McKee ordering          (Sec. 1, 3.1.2),
+ *                    optionally from George-Liu pseudo-peripheral starts
  *   orc_bandwidth    max |p^-1(i) - p^-1(j)| over stored pairs (Table 1)
  *   orc_split        3-way band split, canonical form        (Sec. 3.1.2)
  *   orc_auto_cut     default cut point W (and tile T)        (Sec. 3.1.2, Fig. 8)
@@ -182,9 +183,59 @@ int64_t orc_bandwidth(int32_t n, const int32_t *rp, const int32_t *ci, const int
  * they are enqueued; (4) the concatenated visit order is the Cuthill-McKee
  * order, reversed as a whole it is RCM; (5) with guard != 0, when the RCM
  * bandwidth exceeds the original one, the identity is returned instead. */
-int orc_rcm(int32_t n, const int32_t *rp, const int32_t *ci, int32_t guard,
+/* Level structure rooted at r (breadth-first search over the whole graph,
+ * which reaches exactly r's component): returns the eccentricity of r (the
+ * index of the last level) and, in *last_min, the vertex of the last level
+ * with the smallest (degree, index).  dist[] is -1 on entry and on exit. */
+static int32_t orc_last_level(const int64_t *arp, const int32_t *adj, const int32_t *deg, int32_t r,
+                              int32_t *dist, int32_t *queue, int32_t *last_min)
+{
+    int32_t head = 0, tail = 0;
+    dist[r] = 0;
+    queue[tail++] = r;
+    while (head < tail) {
+        int32_t v = queue[head++];
+        for (int64_t k = arp[v]; k < arp[v + 1]; k++)
+            if (dist[adj[k]] < 0) {
+                dist[adj[k]] = dist[v] + 1;
+                queue[tail++] = adj[k];
+            }
+    }
+    int32_t ecc = dist[queue[tail - 1]];
+    int32_t best = -1;
+    for (int32_t q = 0; q < tail; q++) {
+        int32_t v = queue[q];
+        if (dist[v] == ecc && (best < 0 || deg[v] < deg[best] || (deg[v] == deg[best] && v < best))) best = v;
+    }
+    for (int32_t q = 0; q < tail; q++) dist[queue[q]] = -1;
+    *last_min = best;
+    return ecc;
+}
+
+/* George-Liu pseudo-peripheral vertex of r's component: from r, take the
+ * last level's smallest (degree, index) vertex x; while x is strictly more
+ * eccentric than r, move r to x and repeat. */
+static int32_t orc_pseudo_peripheral(const int64_t *arp, const int32_t *adj, const int32_t *deg, int32_t r,
+                                     int32_t *dist, int32_t *queue)
+{
+    int32_t x;
+    int32_t e = orc_last_level(arp, adj, deg, r, dist, queue, &x);
+    for (;;) {
+        int32_t y;
+        int32_t ex = orc_last_level(arp, adj, deg, x, dist, queue, &y);
+        if (ex <= e) return r;
+        r = x;
+        e = ex;
+        x = y;
+    }
+}
+
+/* flags: bit 0 (1) the identity guard, bit 1 (2) start each component at a
+ * pseudo-peripheral vertex found from the (degree, index) candidate. */
+int orc_rcm(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flags,
             int32_t *perm, int64_t *bw_before, int64_t *bw_after)
 {
+    const int32_t guard = flags & 1, peripheral = flags & 2;
     if (n < 0) return ORC_EINVAL;
     size_t nn = (size_t)(n > 0 ? n : 1);
     int64_t nnz = rp[n];
@@ -196,10 +247,14 @@ int orc_rcm(int32_t n, const int32_t *rp, const int32_t *ci, int32_t guard,
     int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * nn);
     char *seen = (char *)calloc(nn, 1);
     int64_t *fill = (int64_t *)calloc(nn, sizeof(int64_t));
-    if (!arp || !adj || !deg || !by_deg || !cm || !tmp || !seen || !fill) {
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * nn);
+    if (!arp || !adj || !deg || !by_deg || !cm || !tmp || !seen || !fill || !dist || !queue) {
         free(arp); free(adj); free(deg); free(by_deg); free(cm); free(tmp); free(seen); free(fill);
+        free(dist); free(queue);
         return ORC_ENOMEM;
     }
+    for (int32_t i = 0; i < n; i++) dist[i] = -1;
     /* (1) adjacency lists of the symmetric pattern */
     for (int32_t i = 0; i < n; i++)
         for (int32_t k = rp[i]; k < rp[i + 1]; k++) { deg[i]++; deg[ci[k]]++; }
@@ -220,6 +275,7 @@ int orc_rcm(int32_t n, const int32_t *rp, const int32_t *ci, int32_t guard,
     while (count < n) {
         while (seen[by_deg[next_start]]) next_start++;
         int32_t s = by_deg[next_start];
+        if (peripheral && deg[s] > 0) s = orc_pseudo_peripheral(arp, adj, deg, s, dist, queue);
         seen[s] = 1;
         cm[count++] = s;
         /* (3) breadth-first search, the cm array doubles as the FIFO queue */
@@ -249,6 +305,7 @@ int orc_rcm(int32_t n, const int32_t *rp, const int32_t *ci, int32_t guard,
     if (bw_before) *bw_before = b0;
     if (bw_after) *bw_after = b1;
     free(arp); free(adj); free(deg); free(by_deg); free(cm); free(tmp); free(seen); free(fill);
+    free(dist); free(queue);
     return ORC_OK;
 }
 
