@@ -61,6 +61,10 @@ extern "C" {
 
 /* ---------------------------------------------------------------- flags */
 #define PARS3_RCM_GUARD 1 /* pars3_reorder: return the identity when RCM would widen the band */
+#define PARS3_RCM_PERIPHERAL 2 /* pars3_reorder: start each component at a George-Liu pseudo-peripheral
+                                  vertex (from the (degree, index) candidate, move to the smallest
+                                  (degree, index) vertex of the last BFS level while that strictly
+                                  increases the eccentricity) */
 #define PARS3_SPLIT_SYMMETRIC 1 /* pars3_split_params.flags: S = L + L^T (the symmetric variant the
                                    paper's method also covers, abstract and Sec. 5) instead of the
                                    skew-symmetric S = L - L^T */

@@ -49,7 +49,54 @@ int64_t bandwidth(int32_t n, const int32_t *rowptr, const int32_t *col, const in
     return bw;
 }
 
-static int rcm_core(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t *perm) {
+// Level structure rooted at r: eccentricity of r, and in *last_min the vertex
+// of the last level with the smallest (degree, index).  dist is -1 on entry
+// and on exit; queue holds the component in breadth-first order.
+static int32_t last_level(const std::vector<int64_t> &aptr, const std::vector<int32_t> &adj,
+                          const std::vector<int32_t> &deg, int32_t r, std::vector<int32_t> &dist,
+                          std::vector<int32_t> &queue, int32_t *last_min) {
+    int32_t head = 0, tail = 0;
+    dist[r] = 0;
+    queue[tail++] = r;
+    while (head < tail) {
+        const int32_t v = queue[head++];
+        for (int64_t k = aptr[v]; k < aptr[v + 1]; ++k) {
+            const int32_t u = adj[k];
+            if (dist[u] < 0) {
+                dist[u] = dist[v] + 1;
+                queue[tail++] = u;
+            }
+        }
+    }
+    const int32_t ecc = dist[queue[tail - 1]];
+    int32_t best = -1;
+    for (int32_t q = tail - 1; q >= 0 && dist[queue[q]] == ecc; --q) {
+        const int32_t v = queue[q];
+        if (best < 0 || deg[v] < deg[best] || (deg[v] == deg[best] && v < best)) best = v;
+    }
+    for (int32_t q = 0; q < tail; ++q) dist[queue[q]] = -1;
+    *last_min = best;
+    return ecc;
+}
+
+// George-Liu: from r, move to the last level's smallest (degree, index)
+// vertex while that is strictly more eccentric.
+static int32_t pseudo_peripheral(const std::vector<int64_t> &aptr, const std::vector<int32_t> &adj,
+                                 const std::vector<int32_t> &deg, int32_t r, std::vector<int32_t> &dist,
+                                 std::vector<int32_t> &queue) {
+    int32_t x;
+    int32_t e = last_level(aptr, adj, deg, r, dist, queue, &x);
+    for (;;) {
+        int32_t y;
+        const int32_t ex = last_level(aptr, adj, deg, x, dist, queue, &y);
+        if (ex <= e) return r;
+        r = x;
+        e = ex;
+        x = y;
+    }
+}
+
+static int rcm_core(int32_t n, const int32_t *rowptr, const int32_t *col, bool peripheral, int32_t *perm) {
     const int64_t nnz = rowptr[n];
     std::vector<int32_t> deg(n, 0);
     for (int32_t i = 0; i < n; ++i) {
@@ -92,10 +139,16 @@ static int rcm_core(int32_t n, const int32_t *rowptr, const int32_t *col, int32_
     }
     std::vector<uint8_t> seen(n, 0);
     std::vector<int32_t> cm(n);
+    std::vector<int32_t> dist, queue;
+    if (peripheral) {
+        dist.assign(n, -1);
+        queue.resize(n);
+    }
     int32_t count = 0, head = 0, next_start = 0;
     while (count < n) {
         while (seen[order[next_start]]) ++next_start;
         int32_t s = order[next_start];
+        if (peripheral && deg[s] > 0) s = pseudo_peripheral(aptr, adj, deg, s, dist, queue);
         seen[s] = 1;
         cm[count++] = s;
         while (head < count) {
@@ -122,7 +175,8 @@ extern "C" int pars3_reorder(int32_t n, const int32_t *rowptr, const int32_t *co
     int rc = validate_lower(n, rowptr, col);
     if (rc != PARS3_OK) return rc;
     try {
-        rc = rcm_core(n, rowptr, col, perm_out);
+        if (flags & ~(PARS3_RCM_GUARD | PARS3_RCM_PERIPHERAL)) return PARS3_EINVAL;
+        rc = rcm_core(n, rowptr, col, (flags & PARS3_RCM_PERIPHERAL) != 0, perm_out);
         if (rc != PARS3_OK) return rc;
         std::vector<int32_t> pinv(n);
         for (int32_t k = 0; k < n; ++k) pinv[perm_out[k]] = k;

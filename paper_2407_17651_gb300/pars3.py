@@ -17,6 +17,7 @@ from . import _build
 
 F64, F32, BF16 = 0, 1, 2
 RCM_GUARD = 1
+RCM_PERIPHERAL = 2
 SPLIT_SYMMETRIC = 1
 
 OK, EINVAL, ENOTSKEW, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, EUNSUPPORTED, ESTATE, ENONFINITE = \

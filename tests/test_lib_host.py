@@ -190,3 +190,32 @@ def test_split_rejects_unknown_flags():
     v = np.ascontiguousarray(A.val, dtype=np.float64)
     rc = P.lib().pars3_split(A.n, P._p(rp), P._p(ci), P._p(v), None, P.C.byref(prm), P.C.byref(out))
     assert rc == P.EINVAL
+
+
+@pytest.mark.parametrize("idx", range(9))
+def test_rcm_peripheral_bit_exact(idx):
+    """PARS3_RCM_PERIPHERAL: the library's pseudo-peripheral starts and the
+    resulting permutation equal the oracle's bit for bit (with and without
+    the guard)."""
+    A = list(_mats())[idx]
+    for guard in (True, False):
+        flags = P.RCM_PERIPHERAL | (P.RCM_GUARD if guard else 0)
+        perm, b0, b1 = P.pars3_reorder(A.n, A.rowptr, A.col, flags=flags)
+        po, o0, o1 = O.rcm(A, guard=guard, peripheral=True)
+        assert np.array_equal(perm, po) and (b0, b1) == (o0, o1)
+
+
+def test_rcm_peripheral_hand_example_and_bad_flags():
+    import json
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "rcm_spider_peripheral.json")))
+    low = sorted({(max(a, b), min(a, b)) for a, b in g["edges"]})
+    rp = np.zeros(g["n"] + 1, dtype=np.int32)
+    for i, _ in low:
+        rp[i + 1] += 1
+    rp = np.cumsum(rp).astype(np.int32)
+    col = np.array([j for _, j in low], dtype=np.int32)
+    perm, b0, b1 = P.pars3_reorder(g["n"], rp, col, flags=P.RCM_GUARD | P.RCM_PERIPHERAL)
+    assert perm.tolist() == g["perm_peripheral"] and (b0, b1) == (g["bw_before"], g["bw_after"])
+    with pytest.raises(P.Pars3Error) as e:
+        P.pars3_reorder(g["n"], rp, col, flags=8)
+    assert e.value.code == P.EINVAL
