@@ -236,6 +236,12 @@ def extra_section(args, peak):
            "grid2d 2048x1024 (band-friendly: RCM bandwidth ~1024), N(0,1), alpha=0.5")
     out["grid2d"]["section_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
+    A = W.fem_grid2d(256, 512, 4, "normal", W.SEED_BASE + 6)
+    single("fem_like", A, 0.5, W.vector("uniform", A.n, W.SEED_BASE + 6),
+           "finite-element-like pattern shaped like the paper's Table 1 matrices: 256 x 512 nodes, 4 unknowns "
+           "each, 9-point coupling (n = 524,288, 34.9 entries per full row, RCM bandwidth 2047), alpha=0.5")
+    out["fem_like"]["section_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
     A, alpha, x = W.config1()
     single("cfg1_symmetric", A, alpha, x, "the 128^3 + 1% matrix as the symmetric S = L + L^T "
            "(PARS3_SPLIT_SYMMETRIC), alpha=0.5", symmetric=True)

@@ -86,6 +86,8 @@ CASES = [
     ("rmat_long", lambda: W.rmat(13, 60000, seed=10), {"T": 256, "Wc": 256, "long_row": 64}),
     ("overfull", lambda: W.banded_skew(4096, 1024, 0.05, 11), {"T": 1024, "Wc": 1024}),
     ("config0", lambda: W.config0()[0], {}),
+    ("fem_half", lambda: W.fem_grid2d(24, 30, 3, "normal", 12), {"T": 256, "Wc": 128}),
+    ("fem_full", lambda: W.fem_grid2d(24, 30, 3, "normal", 12), {"T": 512, "Wc": 32}),
 ]
 
 

@@ -173,6 +173,35 @@ def grid(dims, value_kind: str, seed: int, permute: bool = True, name: str = "")
                      {"dims": list(map(int, dims)), "permuted": permute})
 
 
+def fem_grid2d(a: int, b: int, dofs: int, value_kind: str, seed: int, permute: bool = True,
+               name: str = "") -> SkewMatrix:
+    """A finite-element-like pattern: an a x b grid of nodes with `dofs`
+    unknowns each, every unknown coupled to all unknowns of its node and of
+    the 8 surrounding nodes (9-point stencil).  About 9 * dofs - 1 entries
+    per full row and an RCM bandwidth near (min(a, b) + 1) * dofs: the shape
+    of the paper's benchmark matrices (35-56 entries per row, bandwidth a few
+    thousandths to a few hundredths of n, Table 1)."""
+    nn = a * b
+    n = nn * dofs
+    node = np.arange(nn, dtype=np.int64).reshape(a, b)
+    pu, pv = [node.ravel()], [node.ravel()]   # self pairs (different unknowns of one node)
+    for di, dj in ((0, 1), (1, -1), (1, 0), (1, 1)):
+        i0, i1 = max(0, -di), a - max(0, di)
+        j0, j1 = max(0, -dj), b - max(0, dj)
+        pu.append(node[i0:i1, j0:j1].ravel())
+        pv.append(node[i0 + di:i1 + di, j0 + dj:j1 + dj].ravel())
+    pu = np.concatenate(pu)
+    pv = np.concatenate(pv)
+    k = np.arange(dofs, dtype=np.int64)
+    u = (pu[:, None, None] * dofs + k[None, :, None]).repeat(dofs, axis=2).ravel()
+    v = (pv[:, None, None] * dofs + k[None, None, :]).repeat(dofs, axis=1).ravel()
+    keys = _pairs_to_lower_keys(n, u, v)
+    if permute:
+        keys = _relabel(n, keys, seed)
+    return from_keys(n, keys, value_kind, seed, name or f"fem{a}x{b}x{dofs}",
+                     {"nodes": [int(a), int(b)], "dofs": int(dofs), "permuted": permute})
+
+
 def grid_plus_random(dims, frac_extra: float, value_kind: str, seed: int, name: str = "") -> SkewMatrix:
     """Grid graph plus round(frac_extra * #grid edges) distinct random pairs
     that are neither grid edges nor self loops, then a random relabeling."""
