@@ -29,6 +29,13 @@
  *    legacy default stream).  Calls that launch kernels are asynchronous
  *    with respect to the host unless stated otherwise.
  *  - Integer indices are int32 (n < 2^31, stored nonzeros < 2^31).
+ *  - Threads: different handles may be used from different host threads at
+ *    once; one handle must not be used by two host threads at the same time
+ *    (it grows scratch and caches graphs on first use).  A handle stays on
+ *    the device that was current at pars3_upload(); calls on it must run
+ *    with that device current.
+ *  - With PARS3_SPLIT_SYMMETRIC the same calls apply S = L + L^T (the
+ *    symmetric case the paper's method also covers, abstract and Sec. 5).
  */
 #ifndef PARS3_H
 #define PARS3_H

@@ -174,13 +174,14 @@ static int upload_vec(void **dst, const std::vector<T> &v) {
 template <typename VT, typename XT, typename AT, int LPR, int NV>
 static int enqueue(BatchCache &C, int count, int64_t total_units, int64_t total_fold, int smem, int k,
                    cudaStream_t st) {
-    static std::atomic<int> configured{0};
-    if (!configured.load()) {
+    static std::atomic<uint64_t> configured{0};   // one bit per device
+    const uint64_t dbit = device_bit();
+    if (!(configured.load() & dbit)) {
         cudaError_t e = cudaFuncSetAttribute(batched_kernel<VT, XT, AT, LPR, NV>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kSmemLimit - static_cast<int>(sizeof(SpmvArgs<VT, XT, AT>)) - 64);
         if (e != cudaSuccess) return cuda_status(e);
-        configured.store(1);
+        configured.fetch_or(dbit);
     }
     const int grid = static_cast<int>(std::min<int64_t>(total_units, 2LL * sm_count()));
     if (grid > 0)
@@ -310,7 +311,7 @@ extern "C" int pars3_spmm_batched(pars3_handle *const *hs, int32_t count, int32_
         pars3_handle *h = hs[m];
         if (!h) return PARS3_EINVAL;
         if (!(h->dtypes & PARS3_DTYPE_BIT(dtype))) return PARS3_EUNSUPPORTED;
-        if (!h->uploaded) return PARS3_ESTATE;
+        if (ready_on_device(h) != PARS3_OK) return PARS3_ESTATE;
         if (h->n > 0 && (!X[m] || !Y[m] || X[m] == Y[m])) return PARS3_EINVAL;
         if (k == 1 && ((reinterpret_cast<uintptr_t>(X[m]) | reinterpret_cast<uintptr_t>(Y[m])) & 15u))
             return PARS3_EINVAL;

@@ -12,6 +12,19 @@
 
 namespace pars3 {
 
+int ready_on_device(const pars3_handle *h) {
+    if (!h->uploaded) return PARS3_ESTATE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device) return PARS3_ESTATE;
+    return PARS3_OK;
+}
+
+uint64_t device_bit() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    return 1ull << (dev & 63);
+}
+
 int cuda_status(int e) {
     if (e == cudaSuccess) return PARS3_OK;
     if (e == cudaErrorMemoryAllocation) return PARS3_ENOMEM;
@@ -118,7 +131,7 @@ static int check_call(const pars3_handle *h, int dtype, const void *x, const voi
     if (!h) return PARS3_EINVAL;
     if (dtype < 0 || dtype >= kNumDtypes) return PARS3_EINVAL;
     if (!(h->dtypes & PARS3_DTYPE_BIT(dtype))) return PARS3_EUNSUPPORTED;
-    if (!h->uploaded) return PARS3_ESTATE;
+    if (ready_on_device(h) != PARS3_OK) return PARS3_ESTATE;
     if (h->n > 0 && (!x || !y || !aligned16(x) || !aligned16(y))) return PARS3_EINVAL;
     if (x == y && h->n > 0) return PARS3_EINVAL;
     return PARS3_OK;
@@ -185,7 +198,7 @@ extern "C" void pars3_free(pars3_handle *h) {
 
 extern "C" int pars3_check(const pars3_handle *h, void *stream) {
     if (!h) return PARS3_EINVAL;
-    if (!h->uploaded) return PARS3_ESTATE;
+    if (ready_on_device(h) != PARS3_OK) return PARS3_ESTATE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int32_t v = 0;
     cudaError_t e = cudaMemcpyAsync(&v, h->D.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
@@ -224,7 +237,7 @@ extern "C" int pars3_spmv_host(pars3_handle *h, int32_t dtype, double alpha, con
     if (!h || !x_host || !y_host) return PARS3_EINVAL;
     if (dtype < 0 || dtype >= kNumDtypes) return PARS3_EINVAL;
     if (!(h->dtypes & PARS3_DTYPE_BIT(dtype))) return PARS3_EUNSUPPORTED;
-    if (!h->uploaded) return PARS3_ESTATE;
+    if (ready_on_device(h) != PARS3_OK) return PARS3_ESTATE;
     if (h->n == 0) return PARS3_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t bytes = static_cast<size_t>(h->n) * (dtype == PARS3_F64 ? 8 : 4);

@@ -125,6 +125,11 @@ int64_t bandwidth(int32_t n, const int32_t *rowptr, const int32_t *col, const in
 
 // host_split.cpp
 int split_recut(const pars3_handle *src, int32_t T, int32_t W, pars3_handle **out);
+// bit of the calling thread's current CUDA device (kernel attributes are set
+// once per device and kernel)
+uint64_t device_bit();
+// PARS3_OK when h is uploaded and its device is the current one, else PARS3_ESTATE
+int ready_on_device(const pars3_handle *h);
 void auto_cut(int64_t bw, int32_t w_min, int32_t w_cap, int32_t t_min, int32_t *T, int32_t *W);
 int build_layout(pars3_handle *h);
 int smem_bytes_for(const pars3_handle *h, int dtype);

@@ -454,7 +454,7 @@ extern "C" int pars3_mrs(const pars3_handle *hc, double alpha, const double *b, 
     const int inner = opts->inner;
     if (inner < 0 || inner >= kNumDtypes) return PARS3_EINVAL;
     if (!(h->dtypes & PARS3_DTYPE_BIT(PARS3_F64)) || !(h->dtypes & PARS3_DTYPE_BIT(inner))) return PARS3_EUNSUPPORTED;
-    if (!h->uploaded) return PARS3_ESTATE;
+    if (ready_on_device(h) != PARS3_OK) return PARS3_ESTATE;
     if (h->symmetric) return PARS3_EUNSUPPORTED;   // the recurrence needs a skew-symmetric S
     if (h->n > 0 && (!b || !x || (reinterpret_cast<uintptr_t>(b) & 15u) || (reinterpret_cast<uintptr_t>(x) & 15u)))
         return PARS3_EINVAL;

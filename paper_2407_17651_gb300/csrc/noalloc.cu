@@ -62,7 +62,7 @@ extern "C" int pars3_spmv_noalloc(const pars3_handle *h, int32_t dtype, double a
     if (!h) return PARS3_EINVAL;
     if (dtype < 0 || dtype >= kNumDtypes) return PARS3_EINVAL;
     if (!(h->dtypes & PARS3_DTYPE_BIT(dtype))) return PARS3_EUNSUPPORTED;
-    if (!h->uploaded) return PARS3_ESTATE;
+    if (ready_on_device(h) != PARS3_OK) return PARS3_ESTATE;
     if (h->n == 0) return PARS3_OK;
     if (!x || !y || x == y) return PARS3_EINVAL;
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) return PARS3_EINVAL;

@@ -96,12 +96,13 @@ static int launch_spmm_lpr(const pars3_handle *h, int dtype, double alpha, int k
     a.err = D.err;
     a.sym = h->symmetric;
     const int smem = spmm_smem_bytes(h, dtype);
-    static std::atomic<int> configured{0};
-    if (!configured.load()) {
+    static std::atomic<uint64_t> configured{0};   // one bit per device
+    const uint64_t dbit = device_bit();
+    if (!(configured.load() & dbit)) {
         cudaError_t e = cudaFuncSetAttribute(spmm_kernel<VT, XT, AT, LPR, NV>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
         if (e != cudaSuccess) return cuda_status(e);
-        configured.store(1);
+        configured.fetch_or(dbit);
     }
     const int grid = h->ntiles + a.nchunks;
     if (grid > 0) spmm_kernel<VT, XT, AT, LPR, NV><<<grid, kBlock, smem, st>>>(a, k);
@@ -187,7 +188,7 @@ extern "C" int pars3_spmm(const pars3_handle *hc, int32_t dtype, double alpha, i
     if (!h || k < 1 || k > 32) return PARS3_EINVAL;
     if (dtype < 0 || dtype >= kNumDtypes) return PARS3_EINVAL;
     if (!(h->dtypes & PARS3_DTYPE_BIT(dtype))) return PARS3_EUNSUPPORTED;
-    if (!h->uploaded) return PARS3_ESTATE;
+    if (ready_on_device(h) != PARS3_OK) return PARS3_ESTATE;
     if (h->n == 0) return PARS3_OK;
     if (!X || !Y || X == Y) return PARS3_EINVAL;
     if (k == 1) return pars3_spmv(h, dtype, alpha, X, Y, stream);

@@ -63,12 +63,13 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     a.err = D.err;
     a.sym = h->symmetric;
     const int smem = smem_bytes_for(h, dtype);
-    static std::atomic<int> configured{0};
-    if (!configured.load()) {
+    static std::atomic<uint64_t> configured{0};   // one bit per device
+    const uint64_t dbit = device_bit();
+    if (!(configured.load() & dbit)) {
         cudaError_t e = cudaFuncSetAttribute(tile_kernel<VT, XT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kSmemLimit);
         if (e != cudaSuccess) return cuda_status(e);
-        configured.store(1);
+        configured.fetch_or(dbit);
     }
     const int grid = h->ntiles + a.nchunks;
     if (grid > 0) tile_kernel<VT, XT, AT><<<grid, kBlock, smem, st>>>(a);
