@@ -29,6 +29,7 @@
 namespace pars3 {
 
 constexpr int kRedBlock = 256;
+constexpr int kBodyUnroll = 4;   // MRS iterations per pass of the graph's while node
 constexpr int kMaxRedBlocks = 1024;
 
 // Fold of MRS iteration j: w_j[r] += (halo + long-row partials) / beta_{j-1}
@@ -43,6 +44,10 @@ __global__ void __launch_bounds__(kRedBlock) fold_mrs_kernel(
     int in_graph) {
     __shared__ double red[32];
     MrsState *st = m.st;
+    if (st->done) {   // an unrolled loop body past convergence (or a solve that starts converged)
+        if (in_graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
     const int j = st->j + 1;
     XT *y = m.w[j % 3];
     const AT scale = static_cast<AT>(st->e_scale);   // 1 / beta_{j-1}
@@ -107,7 +112,7 @@ __global__ void __launch_bounds__(kRedBlock) mrs_init_kernel(int n, const double
     st->j = 0;
     st->jmax = jmax;
     st->done = b0 == 0.0;
-    mrs_next_coeffs(st);
+    mrs_next_coeffs(st, 0.0);
 }
 
 // After the last iteration J: p_J = (w_{J-1}/beta_{J-1} - R[J-2,J] p_{J-2}) / rho_J,
@@ -336,16 +341,20 @@ static int build_graph(pars3_handle *h, int dtype, MrsWork &W) {
     e = cudaStreamBeginCaptureToGraph(W.capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_status(e);
     const int grid = h->ntiles + a.nchunks;
-    if (stage && fused) tile_kernel_mrs<VT, XT, AT, true, true><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
-    else if (stage) tile_kernel_mrs<VT, XT, AT, true, false><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
-    else if (fused) tile_kernel_mrs<VT, XT, AT, false, true><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
-    else tile_kernel_mrs<VT, XT, AT, false, false><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
     const DevLayout &D = h->D;
-    if (!fused)
-        fold_mrs_kernel<XT, AT><<<fold_blocks(h), kRedBlock, 0, W.capture>>>(
-            static_cast<int>(L.fold_row.size()), D.fold_row, D.fold_halo, D.fold_long,
-            static_cast<const AT *>(D.halo), D.lc0, D.lc1, D.lcfirst, D.lcslot, static_cast<const AT *>(D.lpart), m,
-            h->ntiles, G.cond, 1);
+    // kBodyUnroll iterations per pass of the while node (each launch returns
+    // at once after convergence), so the node's own cost is paid less often
+    for (int u = 0; u < kBodyUnroll; ++u) {
+        if (stage && fused) tile_kernel_mrs<VT, XT, AT, true, true><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
+        else if (stage) tile_kernel_mrs<VT, XT, AT, true, false><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
+        else if (fused) tile_kernel_mrs<VT, XT, AT, false, true><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
+        else tile_kernel_mrs<VT, XT, AT, false, false><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
+        if (!fused)
+            fold_mrs_kernel<XT, AT><<<fold_blocks(h), kRedBlock, 0, W.capture>>>(
+                static_cast<int>(L.fold_row.size()), D.fold_row, D.fold_halo, D.fold_long,
+                static_cast<const AT *>(D.halo), D.lc0, D.lc1, D.lcfirst, D.lcslot, static_cast<const AT *>(D.lpart),
+                m, h->ntiles, G.cond, 1);
+    }
     cudaGraph_t captured = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(W.capture, &captured);
     if (e == cudaSuccess) e = cudaGetLastError();

@@ -191,28 +191,25 @@ struct MrsState {
 };
 
 // Scalars of iteration j = st->j + 1, computed once by the thread that
-// finished iteration j - 1 (fp64 divisions are costly on this part, so no
-// other thread repeats them): w_j = raw / beta_{j-1} + (beta_{j-1} /
-// beta_{j-2}) w_{j-2}; lagged p_{j-1} = (w_{j-2} / beta_{j-2} - R[j-3,j-1]
-// p_{j-3}) / rho_{j-1} with R[j-3,j-1] = -s_{j-3} beta_{j-2}; x += tau_{j-1} p_{j-1}.
-__device__ __forceinline__ void mrs_next_coeffs(MrsState *st) {
+// finished iteration j - 1 (fp64 division is costly on this part, so no
+// other thread repeats them, and the step reuses reciprocals it already
+// has): w_j = raw / beta_{j-1} + (beta_{j-1} / beta_{j-2}) w_{j-2}; lagged
+// p_{j-1} = (w_{j-2} / beta_{j-2} - R[j-3,j-1] p_{j-3}) / rho_{j-1} with
+// R[j-3,j-1] = -s_{j-3} beta_{j-2}; x += tau_{j-1} p_{j-1}.  inv_rho is
+// 1 / rho_{j-1} (unused for j = 1); the previous e_scale is 1 / beta_{j-2}.
+__device__ __forceinline__ void mrs_next_coeffs(MrsState *st, double inv_rho) {
     const int j = st->j + 1;
     const double b1 = st->beta[(j - 1) & 3];
     const double b2 = j >= 2 ? st->beta[(j - 2) & 3] : 1.0;
+    const double inv_b2 = j >= 2 ? st->e_scale : 1.0;
     st->e_scale = 1.0 / b1;
-    st->e_coef = j >= 2 ? b1 / b2 : 0.0;
-    st->e_inv_b2 = 1.0 / b2;
+    st->e_coef = j >= 2 ? b1 * inv_b2 : 0.0;
+    st->e_inv_b2 = inv_b2;
     st->e_r3 = j >= 4 ? -st->s[(j - 3) & 3] * b2 : 0.0;
-    st->e_inv_rho = j >= 2 ? 1.0 / st->rho[(j - 1) & 3] : 0.0;
+    st->e_inv_rho = j >= 2 ? inv_rho : 0.0;
     st->e_tau = j >= 2 ? st->tau[(j - 1) & 3] : 0.0;
 }
 
-// Lanczos epilogue of MRS iteration j (the tile kernel computes the raw
-// product S w_{j-1}): w_j = (S w_{j-1}) / beta_{j-1} + (beta_{j-1} /
-// beta_{j-2}) w_{j-2} (that is S v_j + beta_{j-1} v_{j-1} with v_j =
-// w_{j-1}/beta_{j-1}), its squared norm over rows the fold does not touch,
-// and the lagged update of iteration j-1: p_{j-1} = (v_{j-1} - R[j-3,j-1]
-// p_{j-3}) / rho_{j-1}, x += tau_{j-1} p_{j-1}.
 // deterministic block sum of one double per thread (warp butterflies, then
 // warps in order)
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -262,7 +259,8 @@ __device__ __forceinline__ void mrs_step(MrsState *st, double tot, cudaGraphCond
     const double beta = sqrt(tot);
     const double gam = st->gamma;
     const double rho = hypot(gam, beta);
-    const double c = gam / rho, s = beta / rho;
+    const double inv_rho = 1.0 / rho;
+    const double c = gam * inv_rho, s = beta * inv_rho;
     const int k = j & 3;
     st->beta[k] = beta;
     st->rho[k] = rho;
@@ -275,7 +273,7 @@ __device__ __forceinline__ void mrs_step(MrsState *st, double tot, cudaGraphCond
     st->j = j;
     const int done = (fabs(tn) <= st->tol) || (beta == 0.0) || (j >= st->jmax);
     st->done = done;
-    mrs_next_coeffs(st);   // also the final lagged update uses them
+    mrs_next_coeffs(st, inv_rho);   // also the final lagged update uses them
     if (in_graph) cudaGraphSetConditional(cond, done ? 0u : 1u);
 }
 
@@ -615,6 +613,10 @@ template <typename VT, typename XT, typename AT, bool S, bool FUSED>
 __global__ void __launch_bounds__(kBlock, 2) tile_kernel_mrs(const SpmvArgs<VT, XT, AT> a, const MrsVectors<XT> m,
                                                             cudaGraphConditionalHandle cond) {
     extern __shared__ __align__(128) unsigned char smem[];
+    if (m.st->done) {   // an unrolled loop body past convergence (or a solve that starts converged)
+        if (FUSED && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
     const XT *xop = nullptr;
     EpiMrs<XT, AT, S> epi = make_mrs_epi<XT, AT, S>(m.st, m.w, m.p, m.xsol, m.fold_bits, m.part, &xop);
     if (static_cast<int>(blockIdx.x) < a.ntiles) tile_block<VT, XT, AT>(a, blockIdx.x, smem, xop, epi);
