@@ -205,7 +205,9 @@ static int enqueue_lpr(int lpr, BatchCache &C, int count, int64_t nu, int64_t nf
         case 1: return enqueue<VT, XT, AT, 1, NV>(C, count, nu, nfold, smem, k, st);
         case 2: return enqueue<VT, XT, AT, 2, NV>(C, count, nu, nfold, smem, k, st);
         case 4: return enqueue<VT, XT, AT, 4, NV>(C, count, nu, nfold, smem, k, st);
-        case 8: return enqueue<VT, XT, AT, 8, NV>(C, count, nu, nfold, smem, k, st);
+        case 8:
+            if constexpr (NV <= 4) return enqueue<VT, XT, AT, 8, NV>(C, count, nu, nfold, smem, k, st);
+            return PARS3_EINVAL;
         case 16:
             if constexpr (NV <= 2) return enqueue<VT, XT, AT, 16, NV>(C, count, nu, nfold, smem, k, st);
             return PARS3_EINVAL;
@@ -264,15 +266,16 @@ static int run_batched(BatchCache &C, pars3_handle *const *hs, int count, int dt
         C.dtype = dtype;
         C.k = k;
     }
-    // 16-byte lanes when k is a multiple of the vector and every X, Y is 16-byte aligned
+    // 32- or 16-byte lanes (spmm_nv) when every X and Y is 16-byte aligned
     constexpr int V = 16 / static_cast<int>(sizeof(XT));
     bool aligned = true;
     for (int m = 0; m < count; ++m)
         aligned = aligned && ((reinterpret_cast<uintptr_t>(X[m]) | reinterpret_cast<uintptr_t>(Y[m])) & 15u) == 0;
-    const int nv = (aligned && spmm_nv<XT>(k) == V) ? V : 1;
+    const int nv = aligned ? spmm_nv<XT>(k) : 1;
     const int lpr = spmm_lpr(k, nv);
     const int64_t nu = upre.back(), nfold = fpre.back();
     auto launch = [&](cudaStream_t s) {
+        if (nv == 2 * V) return enqueue_lpr<VT, XT, AT, 2 * V>(lpr, C, count, nu, nfold, smem, k, s);
         if (nv == V) return enqueue_lpr<VT, XT, AT, V>(lpr, C, count, nu, nfold, smem, k, s);
         return enqueue_lpr<VT, XT, AT, 1>(lpr, C, count, nu, nfold, smem, k, s);
     };

@@ -125,7 +125,9 @@ static int launch_spmm_nv(const pars3_handle *h, int dtype, double alpha, int k,
         case 1: return launch_spmm_lpr<VT, XT, AT, 1, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
         case 2: return launch_spmm_lpr<VT, XT, AT, 2, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
         case 4: return launch_spmm_lpr<VT, XT, AT, 4, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
-        case 8: return launch_spmm_lpr<VT, XT, AT, 8, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+        case 8:
+            if constexpr (NV <= 4) return launch_spmm_lpr<VT, XT, AT, 8, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+            return PARS3_EINVAL;
         case 16:
             if constexpr (NV <= 2) return launch_spmm_lpr<VT, XT, AT, 16, NV>(h, dtype, alpha, k, X, Y, halo, lpart, st);
             return PARS3_EINVAL;
@@ -136,13 +138,15 @@ static int launch_spmm_nv(const pars3_handle *h, int dtype, double alpha, int k,
     }
 }
 
-// 16-byte lanes when k is a multiple of the vector and X, Y are 16-byte aligned
+// 32- or 16-byte lanes (spmm_nv) when X and Y are 16-byte aligned
 template <typename VT, typename XT, typename AT>
 static int launch_spmm_typed(const pars3_handle *h, int dtype, double alpha, int k, const void *X, void *Y,
                              void *halo, void *lpart, cudaStream_t st) {
     const bool aligned = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) == 0;
     constexpr int V = 16 / static_cast<int>(sizeof(XT));
-    if (aligned && spmm_nv<XT>(k) == V) return launch_spmm_nv<VT, XT, AT, V>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+    const int nv = aligned ? spmm_nv<XT>(k) : 1;
+    if (nv == 2 * V) return launch_spmm_nv<VT, XT, AT, 2 * V>(h, dtype, alpha, k, X, Y, halo, lpart, st);
+    if (nv == V) return launch_spmm_nv<VT, XT, AT, V>(h, dtype, alpha, k, X, Y, halo, lpart, st);
     return launch_spmm_nv<VT, XT, AT, 1>(h, dtype, alpha, k, X, Y, halo, lpart, st);
 }
 

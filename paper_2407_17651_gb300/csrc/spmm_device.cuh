@@ -84,10 +84,35 @@ template <> struct XVec<double, 2> {
     }
 };
 
-// elements per lane for k columns of XT: a 16-byte vector when it divides k
+// 32-byte lanes: two adjacent 16-byte vectors
+template <> struct XVec<float, 8> {
+    static __device__ __forceinline__ void ld(const float *p, float *o, uint64_t pol) {
+        XVec<float, 4>::ld(p, o, pol);
+        XVec<float, 4>::ld(p + 4, o + 4, pol);
+    }
+    static __device__ __forceinline__ void st(float *p, const float *o) {
+        XVec<float, 4>::st(p, o);
+        XVec<float, 4>::st(p + 4, o + 4);
+    }
+};
+template <> struct XVec<double, 4> {
+    static __device__ __forceinline__ void ld(const double *p, double *o, uint64_t pol) {
+        XVec<double, 2>::ld(p, o, pol);
+        XVec<double, 2>::ld(p + 2, o + 2, pol);
+    }
+    static __device__ __forceinline__ void st(double *p, const double *o) {
+        XVec<double, 2>::st(p, o);
+        XVec<double, 2>::st(p + 2, o + 2);
+    }
+};
+
+// elements per lane for k columns of XT: 32 bytes (two 16-byte vectors) when
+// k is at least 16 and a multiple of it -- fewer lanes per row, more rows in
+// flight per warp -- else 16 bytes when that divides k, else one element
 template <typename XT>
 PARS3_HD int spmm_nv(int k) {
     const int v = 16 / static_cast<int>(sizeof(XT));
+    if (k >= 16 && k % (2 * v) == 0) return 2 * v;
     return (k % v == 0) ? v : 1;
 }
 
@@ -100,8 +125,11 @@ PARS3_HD int spmm_lpr(int k, int nv) {
 }
 
 // entries in flight per lane group (fewer with fp64 or vector lanes, which
-// need more registers per entry)
-template <typename AT, int NV> constexpr int spmm_unroll() { return (NV == 1 && sizeof(AT) == 4) ? 8 : 4; }
+// need more registers per entry; with 32-byte lanes two, which measured
+// faster than four with the spills four needs)
+template <typename AT, int NV> constexpr int spmm_unroll() {
+    return (NV == 1 && sizeof(AT) == 4) ? 8 : (NV * sizeof(AT) >= 32 ? 2 : 4);
+}
 
 // acc[0..NV) += sum_m v[base + m*stride] * X[col[base + m*stride], c0..c0+NV)
 // for m < len, in m order.  Every lane of a group loads the same value and
