@@ -354,7 +354,9 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
             int64_t tile_ent = 0;
             for (size_t g = 0; g < rows.size(); g += kSlice) {
                 const int32_t width = slen(rows[g]);
-                L.sl_ent.push_back(static_cast<int32_t>(L.sl_ent.back() + static_cast<int64_t>(kSlice) * width));
+                const int64_t next = L.sl_ent.back() + static_cast<int64_t>(kSlice) * width;
+                if (next > INT32_MAX - kSlice) return PARS3_EUNSUPPORTED;   // int32 slot offsets
+                L.sl_ent.push_back(static_cast<int32_t>(next));
                 for (int l = 0; l < kSlice; ++l) {
                     const size_t k = g + l;
                     L.sl_meta.push_back(k < rows.size()
@@ -385,8 +387,10 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
     L.lrp.assign(1, 0);
     for (int32_t i = 0; i < n; ++i)
         if (is_long[i]) {
+            const int64_t next = static_cast<int64_t>(L.lrp.back()) + flen[i];
+            if (next > INT32_MAX - kLongChunk) return PARS3_EUNSUPPORTED;   // int32 entry offsets
             L.lrow.push_back(i);
-            L.lrp.push_back(L.lrp.back() + flen[i]);
+            L.lrp.push_back(static_cast<int32_t>(next));
         }
     const int64_t ltot = L.lrp.back();
     L.lcol.assign(round_up(ltot, kAlignFull), 0);
