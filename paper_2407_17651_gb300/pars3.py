@@ -151,6 +151,19 @@ def _dptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _vec(t, dtype: int, n: int, what: str):
+    """Device pointer of a vector / row-major block for precision `dtype`:
+    fp64 tensors for F64, fp32 tensors for F32 and BF16 (bf16 stores only
+    the matrix values), n rows."""
+    import torch
+    want = torch.float64 if int(dtype) == F64 else torch.float32
+    if t.dtype != want:
+        raise ValueError(f"{what}: expected {want} for precision {dtype}, got {t.dtype}")
+    if t.dim() not in (1, 2) or t.shape[0] != n:
+        raise ValueError(f"{what}: expected {n} rows, got shape {tuple(t.shape)}")
+    return _dptr(t)
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -259,18 +272,23 @@ def pars3_upload(h: Handle, stream=None):
 
 
 def pars3_spmv(h: Handle, dtype: int, alpha: float, x, y, stream=None):
-    _chk(lib().pars3_spmv(h, int(dtype), float(alpha), _dptr(x), _dptr(y), _stream(stream)), "pars3_spmv")
+    _chk(lib().pars3_spmv(h, int(dtype), float(alpha), _vec(x, dtype, h.n, "x"), _vec(y, dtype, h.n, "y"),
+                          _stream(stream)), "pars3_spmv")
 
 
 def pars3_spmv_noalloc(h: Handle, dtype: int, alpha: float, x, y, stream=None):
     """pars3_spmv with its scratch in the library's fixed device array (the call allocates nothing)."""
-    _chk(lib().pars3_spmv_noalloc(h, int(dtype), float(alpha), _dptr(x), _dptr(y), _stream(stream)),
+    _chk(lib().pars3_spmv_noalloc(h, int(dtype), float(alpha), _vec(x, dtype, h.n, "x"), _vec(y, dtype, h.n, "y"),
+                                  _stream(stream)),
          "pars3_spmv_noalloc")
 
 
 def pars3_spmm(h: Handle, dtype: int, alpha: float, X, Y, stream=None):
     k = 1 if X.dim() == 1 else int(X.shape[1])
-    _chk(lib().pars3_spmm(h, int(dtype), float(alpha), k, _dptr(X), _dptr(Y), _stream(stream)), "pars3_spmm")
+    if Y.shape != X.shape:
+        raise ValueError(f"Y: expected shape {tuple(X.shape)}, got {tuple(Y.shape)}")
+    _chk(lib().pars3_spmm(h, int(dtype), float(alpha), k, _vec(X, dtype, h.n, "X"), _vec(Y, dtype, h.n, "Y"),
+                          _stream(stream)), "pars3_spmm")
 
 
 def pars3_spmm_batched(hs, dtype: int, alphas, Xs, Ys, capture: bool = False, stream=None):
@@ -278,6 +296,14 @@ def pars3_spmm_batched(hs, dtype: int, alphas, Xs, Ys, capture: bool = False, st
     k = 1 if Xs[0].dim() == 1 else int(Xs[0].shape[1])
     harr = (C.c_void_p * m)(*[h.ptr for h in hs])
     a = np.ascontiguousarray(alphas, dtype=np.float64)
+    if not (len(Xs) == len(Ys) == len(alphas) == m):
+        raise ValueError("hs, alphas, Xs and Ys must have the same length")
+    for h, X, Y in zip(hs, Xs, Ys):
+        kk = 1 if X.dim() == 1 else int(X.shape[1])
+        if kk != k or Y.shape != X.shape:
+            raise ValueError("every X and Y of a batch must have the batch's k columns")
+        _vec(X, dtype, h.n, "X")
+        _vec(Y, dtype, h.n, "Y")
     xa = (C.c_void_p * m)(*[X.data_ptr() for X in Xs])
     ya = (C.c_void_p * m)(*[Y.data_ptr() for Y in Ys])
     _chk(lib().pars3_spmm_batched(harr, m, int(dtype), _p(a), k, xa, ya, 1 if capture else 0, _stream(stream)),
@@ -286,16 +312,22 @@ def pars3_spmm_batched(hs, dtype: int, alphas, Xs, Ys, capture: bool = False, st
 
 def pars3_permute(h: Handle, dtype: int, src, dst, stream=None):
     k = 1 if src.dim() == 1 else int(src.shape[1])
-    _chk(lib().pars3_permute(h, int(dtype), k, _dptr(src), _dptr(dst), _stream(stream)), "pars3_permute")
+    _chk(lib().pars3_permute(h, int(dtype), k, _vec(src, dtype, h.n, "src"), _vec(dst, dtype, h.n, "dst"),
+                             _stream(stream)), "pars3_permute")
 
 
 def pars3_unpermute(h: Handle, dtype: int, src, dst, stream=None):
     k = 1 if src.dim() == 1 else int(src.shape[1])
-    _chk(lib().pars3_unpermute(h, int(dtype), k, _dptr(src), _dptr(dst), _stream(stream)), "pars3_unpermute")
+    _chk(lib().pars3_unpermute(h, int(dtype), k, _vec(src, dtype, h.n, "src"), _vec(dst, dtype, h.n, "dst"),
+                               _stream(stream)), "pars3_unpermute")
 
 
 def pars3_spmv_host(h: Handle, dtype: int, alpha: float, x_host: np.ndarray, y_host: np.ndarray, stream=None):
     """x_host/y_host: numpy (or pinned torch CPU tensors' numpy views), original numbering."""
+    want = np.float64 if int(dtype) == F64 else np.float32
+    for a, what in ((x_host, "x_host"), (y_host, "y_host")):
+        if a.dtype != want or a.size != h.n or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{what}: expected {h.n} contiguous {np.dtype(want).name} values")
     _chk(lib().pars3_spmv_host(h, int(dtype), float(alpha), C.c_void_p(x_host.ctypes.data),
                                C.c_void_p(y_host.ctypes.data), _stream(stream)), "pars3_spmv_host")
 
@@ -310,7 +342,8 @@ def pars3_mrs(h: Handle, alpha: float, b, x, rtol: float = 1e-10, max_iter: int 
     o = pars3_mrs_opts(rtol=rtol, max_iter=max_iter, inner=inner, inner_rtol=inner_rtol,
                        max_outer=max_outer, check_every=check_every)
     r = pars3_mrs_result()
-    rc = lib().pars3_mrs(h, float(alpha), _dptr(b), _dptr(x), C.byref(o), C.byref(r), _stream(stream))
+    rc = lib().pars3_mrs(h, float(alpha), _vec(b, F64, h.n, "b"), _vec(x, F64, h.n, "x"), C.byref(o), C.byref(r),
+                         _stream(stream))
     if rc != OK and not (rc == ENOCONV and not raise_on_noconv):
         raise Pars3Error(rc, "pars3_mrs")
     return r.as_dict()

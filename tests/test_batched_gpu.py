@@ -154,10 +154,12 @@ def test_batched_errors(members):
     hs = [h for _, _, h in members]
     Xs, Ys, _ = operands(members, P.F64, 4, 1)
     assert P.lib().pars3_spmm_batched(None, 0, P.F64, None, 4, None, None, 0, None) == P.EINVAL
+    X33 = torch.zeros((members[0][0].n, 33), dtype=torch.float64, device="cuda")
     with pytest.raises(P.Pars3Error) as e:   # k = 33 columns
-        P.pars3_spmm_batched(hs[:1], P.F64, [1.0], [torch.zeros((members[0][0].n, 33), dtype=torch.float64,
-                                                                device="cuda")], [Ys[0]])
+        P.pars3_spmm_batched(hs[:1], P.F64, [1.0], [X33], [torch.zeros_like(X33)])
     assert e.value.code == P.EINVAL
+    with pytest.raises(ValueError):   # Y of another shape: caught by the binding
+        P.pars3_spmm_batched(hs[:1], P.F64, [1.0], [X33], [Ys[0]])
     with pytest.raises(P.Pars3Error) as e:   # in place
         P.pars3_spmm_batched(hs[:1], P.F64, [1.0], Xs[:1], Xs[:1])
     assert e.value.code == P.EINVAL

@@ -219,3 +219,23 @@ def test_rcm_peripheral_hand_example_and_bad_flags():
     with pytest.raises(P.Pars3Error) as e:
         P.pars3_reorder(g["n"], rp, col, flags=8)
     assert e.value.code == P.EINVAL
+
+
+def test_binding_rejects_mismatched_vectors():
+    """The binding checks precision, length and layout of vectors before any
+    library call (a wrong element size would otherwise be read silently)."""
+    import torch
+    A = list(_mats())[0]
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val)
+    x64 = torch.zeros(A.n, dtype=torch.float64)
+    x32 = torch.zeros(A.n, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        P._vec(x32, P.F64, A.n, "x")
+    with pytest.raises(ValueError):
+        P._vec(x64, P.F32, A.n, "x")
+    with pytest.raises(ValueError):
+        P._vec(torch.zeros(A.n + 1, dtype=torch.float64), P.F64, A.n, "x")
+    with pytest.raises(ValueError):   # not a CUDA tensor
+        P._vec(x64, P.F64, A.n, "x")
+    with pytest.raises(ValueError):
+        P.pars3_spmv_host(h, P.F64, 1.0, np.zeros(A.n, dtype=np.float32), np.zeros(A.n))
