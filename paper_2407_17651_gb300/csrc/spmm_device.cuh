@@ -256,22 +256,25 @@ __device__ __forceinline__ void spmm_tile(const SpmvArgs<VT, XT, AT> &a, int k, 
     const bool on = c0 < k;
     const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
     const int nslot = (s1 - s0) * kSlice;
-    for (int q = g; q < nslot; q += ng) {
+    const int gw = g % (32 / LPR);
+    for (int qb = g - gw; qb < nslot; qb += ng) {
+        const int q = qb + gw;
         const int s = q >> 5, l = q & 31;
-        const uint32_t meta = __ldg(a.sl_meta + static_cast<int64_t>(s0) * kSlice + q);
+        const uint32_t meta = q < nslot ? __ldg(a.sl_meta + static_cast<int64_t>(s0) * kSlice + q) : 0xffffu;
         const int rl = static_cast<int>(meta & 0xffffu);
-        if (rl == 0xffff) continue;   // padding lane of the tile's last slice
-        const int len = static_cast<int>(meta >> 16);
-        const int64_t row = static_cast<int64_t>(r0 + rl);
+        const bool valid = rl != 0xffff;   // not a padding lane of the tile's last slice
+        const int len = valid ? static_cast<int>(meta >> 16) : 0;
+        const int64_t row = static_cast<int64_t>(r0 + (valid ? rl : 0));
         AT acc[NV];
         {
             XT xr[NV];
-            if (on) XVec<XT, NV>::ld(a.x + row * k + c0, xr, l2_keep_policy());
+            if (on && valid) XVec<XT, NV>::ld(a.x + row * k + c0, xr, l2_keep_policy());
 #pragma unroll
-            for (int w = 0; w < NV; ++w) acc[w] = on ? a.alpha * static_cast<AT>(xr[w]) : AT(0);
+            for (int w = 0; w < NV; ++w) acc[w] = on && valid ? a.alpha * static_cast<AT>(xr[w]) : AT(0);
         }
-        const int64_t base = static_cast<int64_t>(__ldg(a.sl_ent + s0 + s)) + l;
+        const int64_t base = valid ? static_cast<int64_t>(__ldg(a.sl_ent + s0 + s)) + l : 0;
         spmm_strided_sum<VT, XT, AT, NV>(a.fval, a.fcol, base, kSlice, len, a.x, k, c0, on, acc);
+        if (!valid) continue;
         if (staged) {
             spmm_smem_sum<VT, XT, AT, NV>(hval, nullptr, hcol, hrp[rl], hrp[rl + 1], wb, a.x, k, c0, on, acc);
             const int p = rl + a.W;
