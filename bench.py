@@ -615,7 +615,8 @@ def main():
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-                         "kernel": "pars3_spmv (tile kernel + fold kernel), CUDA events per product",
+                         "kernel": ("pars3_spmv (tile kernel + fold kernel)" if k == 1 else
+                                    "pars3_spmm (spmm kernel + fold kernel)") + ", CUDA events per product",
                          "algorithmic_bytes_per_launch": ub,
                          "layout_bytes_per_launch": info["bytes_per_spmv"][dt]},
             "cpu_baseline": cpu,
