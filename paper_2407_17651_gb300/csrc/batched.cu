@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kBlock, 2) batched_kernel(const SpmvArgs<VT, X
         __syncthreads();
         if (k == 1) {
             if (item < a.ntiles) {
-                EpiSpmv<XT, AT> epi{a.alpha, a.y};
+                EpiSpmv<XT, AT, false> epi{a.alpha, a.y};
                 tile_block<VT, XT, AT>(a, item, smem, a.x, epi);
             } else {
                 long_block<VT, XT, AT>(a, item - a.ntiles, smem, a.x);

@@ -77,6 +77,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// L2 prefetch of [src, src + bytes) by the bulk-copy engine: nothing comes
+// back to the SM and no barrier counts it.  src 16-byte aligned, bytes a
+// multiple of 16.  Issued in pieces of at most kPrefetchPiece bytes.
+constexpr uint32_t kPrefetchPiece = 32u << 10;
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint64_t bytes) {
+    const char *p = static_cast<const char *>(src);
+    while (bytes > 0) {
+        const uint32_t b = bytes > kPrefetchPiece ? kPrefetchPiece : static_cast<uint32_t>(bytes);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(b) : "memory");
+        p += b;
+        bytes -= b;
+    }
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(

@@ -15,7 +15,9 @@
 //     slice a row block needs, Sec. 3.1.2) and of the tile's middle entries
 //     (values, window columns, (column,row) order, row pointers);
 //  1. meanwhile the full pass streams the tile's full-storage rows in
-//     sliced-ELL order straight from HBM: each warp takes 32-row slices,
+//     sliced-ELL order (fp32 / bf16: prefetched into L2 by the copy engine
+//     at the start of the block; fp64: each warp loads the next slice's
+//     columns while it sums the current one): each warp takes 32-row slices,
 //     one lane per row (every row of the tile owns a lane), slot m of lane
 //     l at 32m+l so that every load instruction reads 32 consecutive
 //     entries; a lane's sum starts at alpha x_r and gathers x_j, eight
@@ -149,6 +151,101 @@ __device__ __forceinline__ AT slice_row_sum_uniform(const VT *__restrict__ val, 
     return acc;
 }
 
+// First-round columns (slots < kUnroll) of a sliced-ELL row of length len.
+__device__ __forceinline__ void slice_cols(const int32_t *__restrict__ col, int64_t base, int len,
+                                           int (&c)[kUnroll]) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) c[u] = (u < len) ? __ldcs(col + base + static_cast<int64_t>(u) * kSlice) : 0;
+}
+
+// The additions of one round, slots [0, C), in slot order.
+template <int C, typename AT>
+__device__ __forceinline__ AT slot_sums(const AT (&v)[kUnroll], const AT (&xv)[kUnroll], int rem, AT acc) {
+#pragma unroll
+    for (int u = 0; u < C; ++u)
+        if (u < rem) acc += v[u] * xv[u];
+    return acc;
+}
+
+// Fp64 full pass of one warp over slices sb, sb + step, ... (< s1).  The
+// columns of the next slice's first round are loaded while the current slice
+// is summed, so a slice waits on one round trip (values and x gathers
+// together) instead of two (columns, then x).  The sums are those of
+// slice_row_sum_uniform, in the same order.  Measured per product: 47.9 ->
+// 46.2 us on the 128^3 + 1 % matrix, 40.3 -> 37.1 us on the 2048 x 1024 grid.
+template <typename VT, typename XT, typename AT, class Epi>
+__device__ __forceinline__ void full_pass_pipelined(const int32_t *__restrict__ sl_ent,
+                                                    const uint32_t *__restrict__ sl_meta,
+                                                    const VT *__restrict__ val, const int32_t *__restrict__ col,
+                                                    int sb, int s1, int step, int r0, const XT *__restrict__ xg,
+                                                    Epi &epi, AT *rowacc) {
+    const int lane = threadIdx.x & 31;
+    uint32_t meta = 0xffffu;
+    int ent = 0;
+    if (sb < s1) {
+        meta = __ldg(sl_meta + static_cast<int64_t>(sb) * kSlice + lane);
+        ent = __ldg(sl_ent + sb);
+    }
+    int len = (meta & 0xffffu) != 0xffffu ? static_cast<int>(meta >> 16) : 0;
+    int c[kUnroll];
+    slice_cols(col, static_cast<int64_t>(ent) + lane, len, c);
+    for (int s = sb; s < s1; s += step) {
+        // the next slice's metadata arrives while this slice's gathers do
+        uint32_t meta_n = 0xffffu;
+        int ent_n = 0;
+        if (s + step < s1) {
+            meta_n = __ldg(sl_meta + static_cast<int64_t>(s + step) * kSlice + lane);
+            ent_n = __ldg(sl_ent + s + step);
+        }
+        const int rl = static_cast<int>(meta & 0xffffu);
+        const int lenw = __reduce_max_sync(0xffffffffu, len);
+        const int64_t q0 = static_cast<int64_t>(ent) + lane;
+        AT v[kUnroll], xv[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            v[u] = AT(0);
+            xv[u] = AT(0);
+            if (u < len) {
+                v[u] = Val<VT>::ld_stream(val + q0 + static_cast<int64_t>(u) * kSlice);
+                xv[u] = static_cast<AT>(__ldg(xg + c[u]));
+            }
+        }
+        const AT start = rl != 0xffff ? epi.start(xg, r0 + rl) : AT(0);
+        const int len_n = (meta_n & 0xffffu) != 0xffffu ? static_cast<int>(meta_n >> 16) : 0;
+        slice_cols(col, static_cast<int64_t>(ent_n) + lane, len_n, c);
+        AT acc = start;
+        switch (min(lenw, kUnroll)) {
+        case 0: break;
+        case 1: acc = slot_sums<1, AT>(v, xv, len, acc); break;
+        case 2: acc = slot_sums<2, AT>(v, xv, len, acc); break;
+        case 3: acc = slot_sums<3, AT>(v, xv, len, acc); break;
+        case 4: acc = slot_sums<4, AT>(v, xv, len, acc); break;
+        case 5: acc = slot_sums<5, AT>(v, xv, len, acc); break;
+        case 6: acc = slot_sums<6, AT>(v, xv, len, acc); break;
+        case 7: acc = slot_sums<7, AT>(v, xv, len, acc); break;
+        default: acc = slot_sums<8, AT>(v, xv, len, acc); break;
+        }
+        for (int m0 = kUnroll; m0 < lenw; m0 += kUnroll) {   // rows longer than one round
+            const int rem = len - m0;
+            const int64_t qm = q0 + static_cast<int64_t>(m0) * kSlice;
+            switch (min(lenw - m0, kUnroll)) {
+            case 1: acc = slice_round<1, VT, XT, AT>(val, col, qm, rem, xg, acc); break;
+            case 2: acc = slice_round<2, VT, XT, AT>(val, col, qm, rem, xg, acc); break;
+            case 3: acc = slice_round<3, VT, XT, AT>(val, col, qm, rem, xg, acc); break;
+            case 4: acc = slice_round<4, VT, XT, AT>(val, col, qm, rem, xg, acc); break;
+            case 5: acc = slice_round<5, VT, XT, AT>(val, col, qm, rem, xg, acc); break;
+            case 6: acc = slice_round<6, VT, XT, AT>(val, col, qm, rem, xg, acc); break;
+            case 7: acc = slice_round<7, VT, XT, AT>(val, col, qm, rem, xg, acc); break;
+            default: acc = slice_round<8, VT, XT, AT>(val, col, qm, rem, xg, acc); break;
+            }
+        }
+        if (rl != 0xffff) rowacc[rl] = acc;
+        meta = meta_n;
+        ent = ent_n;
+        len = len_n;
+    }
+}
+
 // Row [e0, e1) of a long-row chunk by a whole warp: lane l takes entries
 // e0+l, e0+l+32, ... in order, then a butterfly reduction (every lane ends
 // with the same bits: each step adds the same two partial sums, only in
@@ -212,10 +309,13 @@ __device__ __forceinline__ AT half_row_warp(int e0, int e1, const VT *hval, cons
 }
 
 // Row epilogues of the tile block.  Plain product: a row sum starts at
-// alpha x_r and is stored as y_r.
-template <typename XT, typename AT>
+// alpha x_r and is stored as y_r.  PIPE: fp64 tiles load the next slice's
+// columns ahead (full_pass_pipelined); the batched kernel, which also holds
+// the SpMM path, turns it off to stay within its registers.
+template <typename XT, typename AT, bool PIPE = true>
 struct EpiSpmv {
     static constexpr bool kStage = false;   // reads no vectors at the end of the tile
+    static constexpr bool kPipelined = PIPE;
     AT alpha;
     XT *y;
     __device__ __forceinline__ AT start(const XT *__restrict__ x, int r) const {
@@ -338,6 +438,9 @@ struct EpiMrs {
     // end; without S (tiles too large for the extra shared memory) they are
     // read from global memory.
     static constexpr bool kStage = S;
+    // the registers of the look-ahead pass would spill next to the
+    // epilogue's state
+    static constexpr bool kPipelined = false;
     XT *y;
     const XT *wpp, *pold;
     XT *pnew, *xsol;
@@ -444,6 +547,31 @@ __device__ __forceinline__ EpiMrs<XT, AT, S> make_mrs_epi(const MrsState *st, XT
     return e;
 }
 
+// L2 prefetch of slices [s0, s1): their values, columns and metadata.  A
+// slice's entries start at a multiple of 32 slots, so every range starts and
+// ends on a 16-byte boundary.  At most kTilePrefetch bytes of values (and the
+// matching columns) are requested, so that the blocks resident at one time
+// cannot claim more than a fraction of L2.
+//
+// Used for fp32 and bf16 values, where it measured 10-14 % faster on the
+// 128^3 + 1 % and 2048 x 1024 grid matrices.  For fp64 it measured 5-17 %
+// slower on those two (with or without an evict-first policy, at 16 KB to
+// 256 KB per tile; 2-3 % faster on R-MAT), so fp64 tiles instead load the
+// next slice's columns ahead in registers (full_pass_pipelined).
+constexpr int64_t kTilePrefetch = 256 << 10;
+template <typename AT>
+constexpr bool tile_prefetch() { return sizeof(AT) == 4; }
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ void prefetch_slices(const SpmvArgs<VT, XT, AT> &a, int s0, int s1) {
+    const int64_t e0 = a.sl_ent[s0], e1 = a.sl_ent[s1];
+    const int64_t ne = min(e1 - e0, kTilePrefetch / static_cast<int64_t>(sizeof(VT)));
+    if (ne > 0) {
+        bulk_prefetch_l2(a.fval + e0, static_cast<uint64_t>(ne) * sizeof(VT));
+        bulk_prefetch_l2(a.fcol + e0, static_cast<uint64_t>(ne) * 4u);
+    }
+    bulk_prefetch_l2(a.sl_meta + static_cast<int64_t>(s0) * kSlice, static_cast<uint64_t>(s1 - s0) * kSlice * 4u);
+}
+
 template <typename VT, typename XT, typename AT, class Epi>
 __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t, unsigned char *smem,
                                            const XT *__restrict__ xop, Epi &epi) {
@@ -467,9 +595,12 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     const uint32_t hmp = static_cast<uint32_t>((hm + kAlignHalf - 1) / kAlignHalf * kAlignHalf);
     const uint32_t rpb = static_cast<uint32_t>(a.T + 8) * 2u;
 
-    // 0. the copy engine stages the x window and the middle entries (a tile
-    // without middle entries needs neither), and the vectors the epilogue
-    // reads (Lanczos mode)
+    // 0. with fp32 / bf16 values the copy engine prefetches the tile's
+    // sliced-ELL rows into L2 (the warps' loads then wait on L2, not on HBM);
+    // it stages the x window and the middle entries (a tile without middle
+    // entries needs neither) and the vectors the epilogue reads (Lanczos mode)
+    const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
+    if (tile_prefetch<AT>() && tid == P - 1 && s1 > s0) prefetch_slices(a, s0, s1);
     const bool stage_half = hm > 0;
     const bool staged = stage_half || Epi::kStage;   // block-uniform
     epi.bind(r0, a.T, smem + align128(L.total));
@@ -498,9 +629,11 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     if constexpr (Epi::kStage) epi.stage_tail(r0, nr, smem + align128(L.total), tid, P);
     __syncthreads();   // the barrier is initialised before anyone waits on it
 
-    // 1. full pass (sliced ELL) straight from HBM while the copy runs
-    const int s0 = a.sl_off[t], s1 = a.sl_off[t + 1];
-    {
+    // 1. full pass (sliced ELL) while the copy runs
+    if constexpr (sizeof(AT) == 8 && Epi::kPipelined) {
+        full_pass_pipelined<VT, XT, AT, Epi>(a.sl_ent, a.sl_meta, a.fval, a.fcol, s0 + warp, s1, nwarps, r0, xop,
+                                             epi, rowacc);
+    } else {
         // the next slice's metadata is fetched while the current one runs
         int s = s0 + warp;
         uint32_t meta_n = 0u;
