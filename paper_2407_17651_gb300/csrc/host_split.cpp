@@ -716,6 +716,7 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
         }
         if (!L.lrow.empty() && pos != L.lrp.back()) return PARS3_EINVAL;
         for (size_t l = 0; l < L.lrow.size(); ++l) {
+            if (L.lrp[l + 1] <= L.lrp[l]) return PARS3_EINVAL;   // every long row has an entry
             const int32_t c0 = L.lc0[l], c1 = L.lc1[l];
             if (!(L.lcbeg[c0] <= L.lrp[l] && L.lrp[l] < L.lcend[c0])) return PARS3_EINVAL;
             if (!(L.lcbeg[c1] < L.lrp[l + 1] && L.lrp[l + 1] <= L.lcend[c1])) return PARS3_EINVAL;

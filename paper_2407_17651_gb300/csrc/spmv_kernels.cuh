@@ -728,8 +728,16 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
 }
 
 // Long-row chunk c: entries [lcbeg[c], lcend[c]) of the long list, staged by
-// TMA from the 16-entry boundary below; one warp per row touched, partial
-// sum into the row's slot.
+// TMA from the 16-entry boundary below.  The chunk's entries are split
+// evenly over the warps (contiguous ranges of S entries, S a multiple of 32),
+// whatever the rows: a chunk inside one row of tens of thousands of entries
+// keeps every warp busy.  A warp sums each row piece in its range with
+// row_sum_warp.  A row that lies inside one range is complete and goes to its
+// slot; a row shared by warps wa < ... < wb leaves one partial per warp in
+// shared memory (edge[2w + 1]: the piece of the row that begins in warp w
+// and continues; edge[2w]: the piece of the row that began in an earlier
+// warp), and warp wb adds them in warp order.  Every long row has at least
+// one entry, so the row pointers of a chunk increase strictly.
 template <typename VT, typename XT, typename AT>
 __device__ __forceinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c, unsigned char *smem,
                                            const XT *__restrict__ xop) {
@@ -737,6 +745,7 @@ __device__ __forceinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c,
     VT *fval = reinterpret_cast<VT *>(smem + L.fval);
     int32_t *fcol = reinterpret_cast<int32_t *>(smem + L.fcol);
     uint16_t *flp = reinterpret_cast<uint16_t *>(smem + L.flp);
+    AT *edge = reinterpret_cast<AT *>(smem + L.edge);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
     const int tid = threadIdx.x, P = blockDim.x;
     const int beg = a.lcbeg[c], end = a.lcend[c];
@@ -756,10 +765,36 @@ __device__ __forceinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c,
     __syncthreads();
     if (tid == 0) mbar_inval(mbar);
     const int shift = beg - abeg;
-    const int warp = tid >> 5, nw = P >> 5;
-    for (int u = warp; u < nrc; u += nw) {
-        const AT s = row_sum_warp<VT, XT, AT>(flp[u], flp[u + 1], fcol + shift, fval + shift, xop);
-        if ((tid & 31) == 0) a.lpart[a.lcslot[c] + u] = s;
+    const int warp = tid >> 5, nw = P >> 5, lane = tid & 31;
+    const int cnt = end - beg;
+    const int S = ((cnt + nw - 1) / nw + 31) & ~31;
+    const int lo = min(warp * S, cnt), hi = min(lo + S, cnt);
+    AT *slot = a.lpart + a.lcslot[c];
+    int first = 0;   // the row holding entry lo: the smallest u with flp[u + 1] > lo
+    if (lo < hi) {
+        int ua = 0, ub = nrc - 1;
+        while (ua < ub) {
+            const int mid = (ua + ub) >> 1;
+            if (flp[mid + 1] > lo) ub = mid;
+            else ua = mid + 1;
+        }
+        first = ua;
+        for (int u = first; u < nrc && flp[u] < hi; ++u) {
+            const int r0 = flp[u], r1 = flp[u + 1];
+            const AT s = row_sum_warp<VT, XT, AT>(max(r0, lo), min(r1, hi), fcol + shift, fval + shift, xop);
+            if (lane == 0) {
+                if (r0 < lo) edge[2 * warp] = s;            // began in an earlier warp
+                else if (r1 > hi) edge[2 * warp + 1] = s;   // continues in the next warp
+                else slot[u] = s;                           // complete in this range
+            }
+        }
+    }
+    __syncthreads();
+    if (lo < hi && lane == 0 && flp[first] < lo && flp[first + 1] <= hi) {   // a shared row ends here
+        const int wa = flp[first] / S;
+        AT t = edge[2 * wa + 1];
+        for (int w = wa + 1; w <= warp; ++w) t += edge[2 * w];
+        slot[first] = t;
     }
 }
 
