@@ -20,7 +20,7 @@ struct SmemLayout {
     uint32_t xs, rowacc, hval, q, hcol, cperm, hrp, cs, ce, red, mbar, total;
 };
 struct LongLayout {
-    uint32_t fval, fcol, flp, edge, mbar, total;
+    uint32_t fval, fcol, flp, pstart, ppart, mbar, total;
 };
 
 PARS3_HD uint32_t align128(uint32_t a) { return (a + 127u) & ~127u; }
@@ -46,15 +46,19 @@ PARS3_HD SmemLayout smem_layout(uint32_t T, uint32_t W, uint32_t Mh, uint32_t vs
 }
 
 // F: staged entries of a long-row chunk (with alignment slack); rows of a
-// chunk: at most T; edge: the partial sums of rows shared by two or more
-// warps of the chunk block.
+// chunk: at most T; pstart: the first piece of each row of the chunk; ppart:
+// the partial sums of rows cut into several pieces.
 PARS3_HD LongLayout long_layout(uint32_t T, uint32_t F, uint32_t vsz) {
     LongLayout s;
     s.fval = 0;
     s.fcol = align128(s.fval + F * vsz);
     s.flp = align128(s.fcol + F * 4u);
-    s.edge = align128(s.flp + (T + 8u) * 2u);   // two partial sums per warp (up to 32 warps), fp64-sized
-    s.mbar = align128(s.edge + 64u * 8u);
+    // a chunk touches at most F rows (each has an entry in it); its pieces of
+    // at most 128 entries number at most rows + F / 128
+    const uint32_t R = T < F ? T : F;
+    s.pstart = align128(s.flp + (T + 8u) * 2u);
+    s.ppart = align128(s.pstart + (R + 8u) * 2u);   // fp64-sized partial sums
+    s.mbar = align128(s.ppart + (R + F / 128u + 8u) * 8u);
     s.total = align128(s.mbar + 8u);
     return s;
 }

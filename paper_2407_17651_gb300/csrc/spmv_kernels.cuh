@@ -728,26 +728,34 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
 }
 
 // Long-row chunk c: entries [lcbeg[c], lcend[c]) of the long list, staged by
-// TMA from the 16-entry boundary below.  The chunk's entries are split
-// evenly over the warps (contiguous ranges of S entries, S a multiple of 32),
-// whatever the rows: a chunk inside one row of tens of thousands of entries
-// keeps every warp busy.  A warp sums each row piece in its range with
-// row_sum_warp.  A row that lies inside one range is complete and goes to its
-// slot; a row shared by warps wa < ... < wb leaves one partial per warp in
-// shared memory (edge[2w + 1]: the piece of the row that begins in warp w
-// and continues; edge[2w]: the piece of the row that began in an earlier
-// warp), and warp wb adds them in warp order.  Every long row has at least
-// one entry, so the row pointers of a chunk increase strictly.
+// TMA from the 16-entry boundary below.  Each row of the chunk is cut into
+// pieces of at most kPiece entries, and each piece is summed by a group of
+// eight lanes (four groups per warp, pieces taken in order by the block's
+// groups): lane j of the group takes entries 32 r + 8 m + j of the piece
+// (four in flight), then three butterfly steps inside the group.  A row of
+// one piece writes its slot directly; the pieces of a longer row leave their
+// sums in shared memory and one thread adds them in piece order.  A chunk
+// inside one row of tens of thousands of entries thus keeps 32 groups busy,
+// and a short row costs three fp64 additions for its reduction instead of the
+// five of a whole-warp butterfly (the fp64 pipe is narrow on this part).
+// Every long row has at least one entry, so the row pointers of a chunk
+// increase strictly.  The order of every sum is fixed by the layout.
+// Not inlined: inlined into the tile kernel, this path changed how the
+// compiler laid out the tile path (fp64 tiles of the 128^3 + 1 % matrix,
+// which has no long rows: 46.0 -> 47.9 us per product; 46.2 us not inlined).
+constexpr int kPiece = 128;
 template <typename VT, typename XT, typename AT>
-__device__ __forceinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c, unsigned char *smem,
+__device__ __noinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c, unsigned char *smem,
                                            const XT *__restrict__ xop) {
     const LongLayout L = long_layout(a.T, kLongChunk + 2 * kAlignFull, sizeof(VT));
     VT *fval = reinterpret_cast<VT *>(smem + L.fval);
     int32_t *fcol = reinterpret_cast<int32_t *>(smem + L.fcol);
     uint16_t *flp = reinterpret_cast<uint16_t *>(smem + L.flp);
-    AT *edge = reinterpret_cast<AT *>(smem + L.edge);
+    uint16_t *pstart = reinterpret_cast<uint16_t *>(smem + L.pstart);
+    AT *ppart = reinterpret_cast<AT *>(smem + L.ppart);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
     const int tid = threadIdx.x, P = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int beg = a.lcbeg[c], end = a.lcend[c];
     const int abeg = beg & ~(kAlignFull - 1);
     const uint32_t mp = static_cast<uint32_t>((end - abeg + kAlignFull - 1) / kAlignFull * kAlignFull);
@@ -761,40 +769,78 @@ __device__ __forceinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c,
     }
     for (int u = tid; u <= nrc; u += P) flp[u] = static_cast<uint16_t>(min(max(a.lrp[l0 + u], beg), end) - beg);
     __syncthreads();
+    if (warp == 0) {   // pstart: exclusive prefix sum of the rows' piece counts
+        int carry = 0;
+        for (int b0 = 0; b0 < nrc; b0 += 32) {
+            const int u = b0 + lane;
+            const int v = u < nrc ? (flp[u + 1] - flp[u] + kPiece - 1) / kPiece : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (u < nrc) pstart[u] = static_cast<uint16_t>(carry + incl - v);
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) pstart[nrc] = static_cast<uint16_t>(carry);
+    }
     mbar_wait_bounded(mbar, 0, a.err);
     __syncthreads();
     if (tid == 0) mbar_inval(mbar);
-    const int shift = beg - abeg;
-    const int warp = tid >> 5, nw = P >> 5, lane = tid & 31;
-    const int cnt = end - beg;
-    const int S = ((cnt + nw - 1) / nw + 31) & ~31;
-    const int lo = min(warp * S, cnt), hi = min(lo + S, cnt);
+    const int32_t *col_s = fcol + (beg - abeg);
+    const VT *val_s = fval + (beg - abeg);
     AT *slot = a.lpart + a.lcslot[c];
-    int first = 0;   // the row holding entry lo: the smallest u with flp[u + 1] > lo
-    if (lo < hi) {
-        int ua = 0, ub = nrc - 1;
-        while (ua < ub) {
-            const int mid = (ua + ub) >> 1;
-            if (flp[mid + 1] > lo) ub = mid;
-            else ua = mid + 1;
-        }
-        first = ua;
-        for (int u = first; u < nrc && flp[u] < hi; ++u) {
-            const int r0 = flp[u], r1 = flp[u + 1];
-            const AT s = row_sum_warp<VT, XT, AT>(max(r0, lo), min(r1, hi), fcol + shift, fval + shift, xop);
-            if (lane == 0) {
-                if (r0 < lo) edge[2 * warp] = s;            // began in an earlier warp
-                else if (r1 > hi) edge[2 * warp + 1] = s;   // continues in the next warp
-                else slot[u] = s;                           // complete in this range
+    const int npieces = pstart[nrc];
+    const int grp = tid >> 3, j = tid & 7, ngrp = P >> 3;
+    for (int p0 = 0; p0 < npieces; p0 += ngrp) {   // block-uniform
+        const int p = p0 + grp;
+        int u = 0, e0 = 0, e1 = 0;
+        if (p < npieces) {   // the row of piece p: the largest u with pstart[u] <= p
+            int ua = 0, ub = nrc - 1;
+            while (ua < ub) {
+                const int mid = (ua + ub + 1) >> 1;
+                if (pstart[mid] <= p) ua = mid;
+                else ub = mid - 1;
             }
+            u = ua;
+            e0 = flp[u] + (p - pstart[u]) * kPiece;
+            e1 = min(e0 + kPiece, static_cast<int>(flp[u + 1]));
+        }
+        const int rounds = __reduce_max_sync(0xffffffffu, static_cast<unsigned>((e1 - e0 + 31) >> 5));
+        AT acc = AT(0);
+        for (int r = 0; r < rounds; ++r) {
+            AT v[4], xv[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int e = e0 + 32 * r + 8 * m + j;
+                v[m] = AT(0);
+                xv[m] = AT(0);
+                if (e < e1) {
+                    v[m] = sval<VT>(val_s, e);
+                    xv[m] = static_cast<AT>(__ldg(xop + col_s[e]));
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                if (e0 + 32 * r + 8 * m + j < e1) acc += v[m] * xv[m];
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (p < npieces && j == 0) {
+            if (pstart[u + 1] - pstart[u] == 1) slot[u] = acc;
+            else ppart[p] = acc;
         }
     }
     __syncthreads();
-    if (lo < hi && lane == 0 && flp[first] < lo && flp[first + 1] <= hi) {   // a shared row ends here
-        const int wa = flp[first] / S;
-        AT t = edge[2 * wa + 1];
-        for (int w = wa + 1; w <= warp; ++w) t += edge[2 * w];
-        slot[first] = t;
+    for (int u = tid; u < nrc; u += P) {   // rows of several pieces, in piece order
+        const int q0 = pstart[u], q1 = pstart[u + 1];
+        if (q1 - q0 > 1) {
+            AT t = ppart[q0];
+            for (int q = q0 + 1; q < q1; ++q) t += ppart[q];
+            slot[u] = t;
+        }
     }
 }
 
