@@ -178,7 +178,7 @@ __device__ __forceinline__ void full_pass_pipelined(const int32_t *__restrict__ 
                                                     const uint32_t *__restrict__ sl_meta,
                                                     const VT *__restrict__ val, const int32_t *__restrict__ col,
                                                     int sb, int s1, int step, int r0, const XT *__restrict__ xg,
-                                                    Epi &epi, AT *rowacc) {
+                                                    Epi &epi, AT *rowacc, bool direct) {
     const int lane = threadIdx.x & 31;
     uint32_t meta = 0xffffu;
     int ent = 0;
@@ -239,7 +239,10 @@ __device__ __forceinline__ void full_pass_pipelined(const int32_t *__restrict__ 
             default: acc = slice_round<8, VT, XT, AT>(val, col, qm, rem, xg, acc); break;
             }
         }
-        if (rl != 0xffff) rowacc[rl] = acc;
+        if (rl != 0xffff) {
+            if (direct) epi.finish(r0 + rl, acc);
+            else rowacc[rl] = acc;
+        }
         meta = meta_n;
         ent = ent_n;
         len = len_n;
@@ -316,6 +319,7 @@ template <typename XT, typename AT, bool PIPE = true>
 struct EpiSpmv {
     static constexpr bool kStage = false;   // reads no vectors at the end of the tile
     static constexpr bool kPipelined = PIPE;
+    static constexpr bool kDirect = true;     // finish() only stores y
     AT alpha;
     XT *y;
     __device__ __forceinline__ AT start(const XT *__restrict__ x, int r) const {
@@ -441,6 +445,7 @@ struct EpiMrs {
     // the registers of the look-ahead pass would spill next to the
     // epilogue's state
     static constexpr bool kPipelined = false;
+    static constexpr bool kDirect = false;    // finish() needs the block's staged vectors and norm
     XT *y;
     const XT *wpp, *pold;
     XT *pnew, *xsol;
@@ -603,6 +608,11 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     if (tile_prefetch<AT>() && tid == P - 1 && s1 > s0) prefetch_slices(a, s0, s1);
     const bool stage_half = hm > 0;
     const bool staged = stage_half || Epi::kStage;   // block-uniform
+    // A tile without middle entries whose epilogue only stores y: each lane
+    // stores its row's sum as soon as it has it, and the block needs neither
+    // the row sums in shared memory nor a barrier.  fp64 only: with fp32 /
+    // bf16 the three-blocks-per-SM register budget would spill.
+    const bool direct = sizeof(AT) == 8 && !staged && Epi::kDirect;
     epi.bind(r0, a.T, smem + align128(L.total));
     if (staged && tid == 0) {
         mbar_init(mbar, 1);
@@ -632,7 +642,7 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     // 1. full pass (sliced ELL) while the copy runs
     if constexpr (sizeof(AT) == 8 && Epi::kPipelined) {
         full_pass_pipelined<VT, XT, AT, Epi>(a.sl_ent, a.sl_meta, a.fval, a.fcol, s0 + warp, s1, nwarps, r0, xop,
-                                             epi, rowacc);
+                                             epi, rowacc, direct);
     } else {
         // the next slice's metadata is fetched while the current one runs
         int s = s0 + warp;
@@ -656,17 +666,23 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
                 const AT start = rl != 0xffff ? epi.start(xop, r0 + rl) : AT(0);
                 const AT sum = slice_row_sum_uniform<VT, XT, AT>(a.fval, a.fcol, static_cast<int64_t>(ent) + lane,
                                                                  len, lenw, xop, start);
-                if (rl != 0xffff) rowacc[rl] = sum;
+                if (rl != 0xffff) {
+                    if (direct) epi.finish(r0 + rl, sum);
+                    else rowacc[rl] = sum;
+                }
             } else {
                 const int len = static_cast<int>(meta >> 16);
                 if (rl != 0xffff) {
                     const AT start = epi.start(xop, r0 + rl);
-                    rowacc[rl] = slice_row_sum<VT, XT, AT>(a.fval, a.fcol, static_cast<int64_t>(ent) + lane, len,
+                    const AT sum = slice_row_sum<VT, XT, AT>(a.fval, a.fcol, static_cast<int64_t>(ent) + lane, len,
                                                            xop, start);
+                    if (direct) epi.finish(r0 + rl, sum);
+                    else rowacc[rl] = sum;
                 }
             }
         }
     }
+    if (direct) return;   // every row is complete and stored; nothing staged, nothing to reduce
     if (staged) mbar_wait_bounded(mbar, 0, a.err);
     __syncthreads();
     if (staged && tid == 0) mbar_inval(mbar);
