@@ -249,36 +249,6 @@ __device__ __forceinline__ void full_pass_pipelined(const int32_t *__restrict__ 
     }
 }
 
-// Row [e0, e1) of a long-row chunk by a whole warp: lane l takes entries
-// e0+l, e0+l+32, ... in order, then a butterfly reduction (every lane ends
-// with the same bits: each step adds the same two partial sums, only in
-// swapped operand order).
-template <typename VT, typename XT, typename AT>
-__device__ __forceinline__ AT row_sum_warp(int e0, int e1, const int32_t *col_s, const VT *val_s,
-                                           const XT *__restrict__ xg) {
-    const int lane = threadIdx.x & 31;
-    AT acc = AT(0);
-    for (int base = e0 + lane; base < e1; base += 32 * 4) {
-        AT v[4], xv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = base + 32 * u;
-            v[u] = AT(0);
-            xv[u] = AT(0);
-            if (e < e1) {
-                v[u] = sval<VT>(val_s, e);
-                xv[u] = static_cast<AT>(__ldg(xg + col_s[e]));
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (base + 32 * u < e1) acc += v[u] * xv[u];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return acc;
-}
-
 // Half-storage row of the middle part: returns sum_j l_rj x_j and stores the
 // mirrored products q[e] = l_rj x_r (q may alias the value array: entry e is
 // read before it is overwritten, by the same thread).
