@@ -631,7 +631,11 @@ def main():
                                    + (" + fold kernel" if launches_per_spmv > 1 else " (one launch per product)")
                                    + "; average duration = CUDA-event time of the timed steps / products",
                          "algorithmic_bytes_per_launch": ub,
-                         "layout_bytes_per_launch": info["bytes_per_spmv"][dt]},
+                         "layout_bytes_per_launch": info["bytes_per_spmv"][dt],
+                         # the DRAM bytes the profile counted, over the same average duration: how
+                         # close the kernel's actual traffic runs to the copy ceiling
+                         "traffic_GBps": traffic / avg_spmv_s / 1e9 if traffic else None,
+                         "traffic_frac": traffic / avg_spmv_s / 1e9 / peak if traffic else None},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_spmv * REPEATS * args.steps,
