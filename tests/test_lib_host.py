@@ -123,6 +123,21 @@ def test_layout_routes_long_rows_and_full_tiles():
     assert P.pars3_layout_check(h) == 0
 
 
+@pytest.mark.parametrize("T,long_row", [(32, 1), (256, 2), (4096, 2), (1024, 128)])
+def test_long_row_chunks_cover_every_long_entry(T, long_row):
+    """Chunks of the long-row list: at most 4096 entries and T rows each, every
+    long row with at least one entry, the long rows' entries reconstructing
+    the split (pars3_layout_check), for chunks of one row up to thousands."""
+    A = W.grid((120, 110), "normal", 17)
+    perm, _, _ = P.pars3_reorder(A.n, A.rowptr, A.col)
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=32, long_row=long_row)
+    info = P.pars3_info_get(h)
+    assert info["half_entries"] + (info["full_entries"] + info["long_entries"]) // 2 == A.nnz
+    if long_row < 4:
+        assert info["long_rows"] > A.n // 2 and info["long_chunks"] >= info["long_entries"] // 4096
+    assert P.pars3_layout_check(h) == 0
+
+
 def test_overfull_tile_leaves_the_half_path():
     """A tile whose middle entries do not fit in shared memory is stored in
     full (both triangles) instead; the layout still reconstructs the split."""
