@@ -118,8 +118,7 @@ def test_cfg4_batched_autotuned(dtype, k):
     torch.cuda.synchronize()
     for A, p, X, Y in zip(mats, perms, Xs, Yd):
         F = O.Full(A)
-        Xr = X if dtype == P.F64 else X.astype(np.float32).astype(np.float64)
-        ref, bound = F.apply_block(1.0, Xr), F.abs_bound_block(1.0, Xr)
+        ref, bound = F.apply_block(1.0, X), F.abs_bound_block(1.0, X)   # fp64 oracle on the original X
         y = np.empty_like(ref)
         y[p] = Y.double().cpu().numpy()
         assert np.all(np.abs(y - ref) <= TAU[dtype] * bound + 1e-30)

@@ -1,9 +1,11 @@
 """pars3_spmv_noalloc: the product for callers that cannot have the library
-allocate device memory for scratch; its scratch is a fixed library-wide
-device array.  Checked through the C ABI against pars3_spmv on two calls in
-a row (the second with another x, so that stale scratch contents from the
-first call would show), with the fp64/fp32 tolerance of the parity tests.
-This file is collected last on purpose."""
+allocate device memory for scratch (all device memory already handed to
+another allocator or pool, or a fixed memory budget); its scratch is a fixed
+library-wide device array.  Checked through the C ABI against the fp64
+oracle on the original values, and against pars3_spmv, on two calls in a row
+(the second with another x, so that stale scratch contents from the first
+call would show), with the fp64/fp32 tolerance of the parity tests.  This
+file is collected last on purpose."""
 import numpy as np
 import pytest
 import torch
@@ -35,7 +37,7 @@ def _handle(A, **kw):
     ("rmat_long_rows_and_halo", lambda: W.rmat(13, 60000, seed=10), {"T": 256, "W": 256, "long_row": 64}),
     ("band_halo", lambda: W.banded_skew(20000, 100, 0.3, 3), {"T": 256, "W": 128}),
 ])
-def test_noalloc_matches_spmv_on_two_calls(name, gen, kw):
+def test_noalloc_matches_oracle_on_two_calls(name, gen, kw):
     A = gen()
     h, perm = _handle(A, **kw)
     info = P.pars3_info_get(h)
@@ -46,15 +48,17 @@ def test_noalloc_matches_spmv_on_two_calls(name, gen, kw):
         for call, seed in enumerate((11, 12)):
             x = W.vector("uniform", A.n, seed)
             xp = torch.from_numpy(x[perm]).to("cuda", vt)
-            y_ref = torch.full_like(xp, float("nan"))
+            y_lib = torch.full_like(xp, float("nan"))
             y_new = torch.full_like(xp, float("nan"))
-            P.pars3_spmv(h, dtype, 0.75, xp, y_ref)
             P.pars3_spmv_noalloc(h, dtype, 0.75, xp, y_new)
+            P.pars3_spmv(h, dtype, 0.75, xp, y_lib)
             torch.cuda.synchronize()
             P.pars3_check(h)
             a = y_new.double().cpu().numpy()
-            b = y_ref.double().cpu().numpy()
+            ref = F.apply(0.75, x)[perm]          # fp64 oracle on the original values
             bound = F.abs_bound(0.75, x)[perm]
+            assert np.all(np.abs(a - ref) <= TAU[dtype] * bound + 1e-30), (name, dtype, call)
+            b = y_lib.double().cpu().numpy()
             assert np.all(np.abs(a - b) <= TAU[dtype] * bound + 1e-30), (name, dtype, call)
 
 
