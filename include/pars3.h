@@ -88,9 +88,11 @@ typedef struct {
     int32_t T;          /* row tile: rows [tT, tT+T) are owned by one thread block */
     int32_t W;          /* middle bandwidth: stored (i, j) with i - j <= W are middle entries */
     int32_t dtypes;     /* bit mask of PARS3_DTYPE_BIT(d) value precisions to pack (0 = F64 only) */
-    int32_t long_row;   /* full-storage row length above which a row is processed in chunks (0 = default) */
+    int32_t long_row;   /* full-storage row length above which a row is cut into pieces that are
+                           summed separately and added in order by the fold (0 = default 128, at most 128) */
     int32_t flags;      /* 0 (skew-symmetric) or PARS3_SPLIT_SYMMETRIC */
-    int32_t reserved[3];
+    int32_t piece;      /* entries per piece of a long row (0 = default 192; 8 <= piece <= 255) */
+    int32_t reserved[2];
 } pars3_split_params;
 
 /* Read-only view of a handle's canonical split (host memory owned by the
@@ -117,11 +119,12 @@ typedef struct {
     int64_t nnz;
     int64_t half_entries;        /* entries on the half-storage tile path (read once, used twice) */
     int64_t full_entries;        /* full-storage entries on the row path (outer entries twice) */
-    int64_t long_entries;        /* full-storage entries of chunked long rows */
-    int32_t long_rows, long_chunks;
+    int64_t long_entries;        /* full-storage entries of long rows (summed in pieces) */
+    int32_t long_rows, long_pieces;
     int64_t halo_targets;        /* distinct rows that receive a cross-tile mirrored sum */
     int32_t max_tile_half;       /* largest number of half-path entries of one tile */
-    int32_t smem_bytes[3];       /* dynamic shared memory of the tile kernel per precision (0 = not packed) */
+    int32_t smem_bytes[3];       /* dynamic shared memory of pars3_spmv's tile kernel per precision (0 = not
+                                    packed, or nothing staged) */
     int64_t device_bytes;        /* device memory held by the handle after upload */
     int64_t bytes_per_spmv[3];   /* modelled DRAM bytes of one pars3_spmv per precision */
     int64_t bandwidth;           /* max i - j of the reordered lower triangle */

@@ -1,7 +1,7 @@
 // batched.cu -- Y_m = (alpha_m I + S_m) X_m for many split handles of uneven
 // sizes in ONE persistent launch: a fixed grid of blocks walks the
-// concatenated list of work units (every tile and long-row chunk of every
-// matrix) in a static round-robin order, followed by one batched fold
+// concatenated list of work units (every block of long-row pieces and every
+// tile of every matrix) in a static round-robin order, followed by one batched fold
 // launch.  Per-matrix kernel arguments live in a device table; with
 // capture != 0 the pair of launches is recorded once in a CUDA graph and
 // replayed while the arguments stay the same.
@@ -49,15 +49,15 @@ __global__ void __launch_bounds__(kBlock, 2) batched_kernel(const SpmvArgs<VT, X
         }
         __syncthreads();
         if (k == 1) {
-            if (item < a.ntiles) {
-                EpiSpmv<XT, AT, false> epi{a.alpha, a.y};
-                tile_block<VT, XT, AT>(a, item, smem, a.x, epi);
+            if (item < a.nlb) {
+                long_pieces_block<VT, XT, AT>(a, item, a.x);
             } else {
-                long_block<VT, XT, AT>(a, item - a.ntiles, smem, a.x);
+                EpiSpmv<XT, AT, false> epi{a.alpha, a.y};
+                tile_block<VT, XT, AT>(a, item - a.nlb, smem, a.x, epi);
             }
         } else {
-            if (item < a.ntiles) spmm_tile<VT, XT, AT, LPR, NV>(a, k, item, smem);
-            else spmm_long<VT, XT, AT, LPR, NV>(a, k, item - a.ntiles);
+            if (item < a.nlb) spmm_long<VT, XT, AT, LPR, NV>(a, k, item);
+            else spmm_tile<VT, XT, AT, LPR, NV>(a, k, item - a.nlb, smem);
         }
     }
 }
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kBlock, 2) batched_kernel(const SpmvArgs<VT, X
 // fold of all matrices: one thread per (receiving row, column)
 struct FoldArgs {
     int32_t nf;
-    const int32_t *frow, *fhalo, *flong, *lc0, *lc1, *lcfirst, *lcslot;
+    const int32_t *frow, *fhalo, *flong, *lp0, *lrem;
 };
 
 template <typename XT, typename AT>
@@ -92,9 +92,7 @@ __global__ void __launch_bounds__(256) batched_fold_kernel(const FoldArgs *__res
         const int hh = F.fhalo[f];
         if (hh >= 0) v += halos[m][static_cast<int64_t>(hh) * k + c];
         const int l = F.flong[f];
-        if (l >= 0)
-            for (int ch = F.lc0[l]; ch <= F.lc1[l]; ++ch)
-                v += lparts[m][static_cast<int64_t>(F.lcslot[ch] + (l - F.lcfirst[ch])) * k + c];
+        if (l >= 0) v = long_row_sum<AT>(l, F.lp0, F.lrem, lparts[m], k, c, v);
         y[r * k + c] = static_cast<XT>(v);
     }
 }
@@ -124,43 +122,10 @@ struct BatchCache {
 
 template <typename VT, typename XT, typename AT>
 static SpmvArgs<VT, XT, AT> make_args(const pars3_handle *h, int dtype, double alpha, const void *X, void *Y) {
-    const Layout &L = h->L;
-    const DevLayout &D = h->D;
-    SpmvArgs<VT, XT, AT> a;
-    a.n = h->n;
-    a.T = h->T;
-    a.W = h->W;
-    a.ntiles = h->ntiles;
-    a.nchunks = static_cast<int32_t>(L.lcbeg.size());
-    a.Mh = static_cast<int32_t>(round_up(L.max_tile_half, kAlignHalf));
-    a.hoff = D.hoff;
-    a.hcnt = D.hcnt;
-    a.hrp = D.hrp;
-    a.hcol = D.hcol;
-    a.hcperm = D.hcperm;
-    a.hval = static_cast<const VT *>(D.hval[dtype]);
-    a.hhoff = D.hhoff;
-    a.hhrow = D.hhrow;
-    a.halo = static_cast<AT *>(D.halo);
-    a.sl_off = D.sl_off;
-    a.sl_ent = D.sl_ent;
-    a.sl_meta = D.sl_meta;
-    a.fcol = D.fcol;
-    a.fval = static_cast<const VT *>(D.fval[dtype]);
-    a.lrp = D.lrp;
-    a.lcbeg = D.lcbeg;
-    a.lcend = D.lcend;
-    a.lcfirst = D.lcfirst;
-    a.lcrows = D.lcrows;
-    a.lcslot = D.lcslot;
-    a.lcol = D.lcol;
-    a.lval = static_cast<const VT *>(D.lval[dtype]);
-    a.lpart = static_cast<AT *>(D.lpart);
+    SpmvArgs<VT, XT, AT> a = make_spmv_args<VT, XT, AT>(h, dtype);
     a.x = static_cast<const XT *>(X);
     a.y = static_cast<XT *>(Y);
     a.alpha = static_cast<AT>(alpha);
-    a.err = D.err;
-    a.sym = h->symmetric;
     return a;
 }
 
@@ -189,7 +154,7 @@ static int enqueue(BatchCache &C, int count, int64_t total_units, int64_t total_
             static_cast<const SpmvArgs<VT, XT, AT> *>(C.args), static_cast<const int32_t *>(C.upre), count,
             static_cast<int>(total_units), k);
     if (total_fold > 0) {
-        const int blocks = static_cast<int>(std::min<int64_t>((total_fold + 255) / 256, 152 * 8));
+        const int blocks = static_cast<int>(std::min<int64_t>((total_fold + 255) / 256, 8LL * sm_count()));
         batched_fold_kernel<XT, AT><<<blocks, 256, 0, st>>>(
             static_cast<const FoldArgs *>(C.fa), static_cast<const AT *const *>(C.halos),
             static_cast<const AT *const *>(C.lparts), static_cast<XT *const *>(C.ys),
@@ -230,7 +195,7 @@ static int run_batched(BatchCache &C, pars3_handle *const *hs, int count, int dt
     int smem = 0;
     for (int m = 0; m < count; ++m) {
         const pars3_handle *h = hs[m];
-        upre.push_back(upre.back() + h->ntiles + static_cast<int32_t>(h->L.lcbeg.size()));
+        upre.push_back(upre.back() + h->L.nlong_blocks() + h->ntiles);
         fpre.push_back(fpre.back() + static_cast<int64_t>(h->L.fold_row.size()) * k);
         smem = std::max(smem, k == 1 ? smem_bytes_for(h, dtype) : spmm_smem_bytes(h, dtype));
     }
@@ -246,7 +211,7 @@ static int run_batched(BatchCache &C, pars3_handle *const *hs, int count, int dt
             args.push_back(make_args<VT, XT, AT>(h, dtype, alpha[m], X[m], Y[m]));
             const DevLayout &D = h->D;
             fa.push_back(FoldArgs{static_cast<int32_t>(h->L.fold_row.size()), D.fold_row, D.fold_halo, D.fold_long,
-                                  D.lc0, D.lc1, D.lcfirst, D.lcslot});
+                                  D.lp0, D.lrem});
             halos.push_back(D.halo);
             lparts.push_back(D.lpart);
             ys.push_back(Y[m]);

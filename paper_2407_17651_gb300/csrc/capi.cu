@@ -82,15 +82,10 @@ static int upload_impl(pars3_handle *h, cudaStream_t st) {
     UP(D.sl_ent, L.sl_ent);
     UP(D.sl_meta, L.sl_meta);
     UP(D.fcol, L.fcol);
-    UP(D.lrow, L.lrow);
-    UP(D.lrp, L.lrp);
-    UP(D.lc0, L.lc0);
-    UP(D.lc1, L.lc1);
-    UP(D.lcbeg, L.lcbeg);
-    UP(D.lcend, L.lcend);
-    UP(D.lcfirst, L.lcfirst);
-    UP(D.lcrows, L.lcrows);
-    UP(D.lcslot, L.lcslot);
+    UP(D.lp0, L.lp0);
+    UP(D.lrem, L.lrem);
+    UP(D.ls_ent, L.ls_ent);
+    UP(D.ls_len, L.ls_len);
     UP(D.lcol, L.lcol);
     UP(D.fold_row, L.fold_row);
     UP(D.fold_halo, L.fold_halo);

@@ -18,10 +18,10 @@
 //                 so that each row is a plain gather (no write conflicts);
 //                 sliced ELL: every row of a tile owns one lane of one of
 //                 its T/32 slices (long rows with length 0);
-//   long rows  -- rows longer than a per-tile cap on full-path entries (and
-//                 the heaviest rows of tiles above the cap) are summed in
-//                 chunks of kLongChunk entries; the partial sums of every
-//                 (chunk, row) pair are folded in chunk order.
+//   long rows  -- rows longer than long_row (and the heaviest rows of tiles
+//                 whose full-path entries exceed a cap) are cut into pieces
+//                 of `piece` entries laid out like the tile slices (one lane
+//                 per piece); the piece sums are folded in row order.
 #include <algorithm>
 #include <atomic>
 #include <climits>
@@ -163,18 +163,28 @@ void dtype_sizes(int dtype, uint32_t *vsz, uint32_t *xsz, uint32_t *asz) {
     else { *vsz = 2; *xsz = 4; *asz = 4; }
 }
 
-constexpr int64_t kLongSlots = kLongChunk + 2 * kAlignFull;  // long chunk staging incl. alignment slack
-
-static uint32_t smem_total(const pars3_handle *h, int dtype, int64_t Mh, bool has_long) {
+static uint32_t smem_total(const pars3_handle *h, int dtype, int64_t Mh) {
     uint32_t vsz, xsz, asz;
     dtype_sizes(dtype, &vsz, &xsz, &asz);
-    const uint32_t a = smem_layout(h->T, h->W, static_cast<uint32_t>(round_up(Mh, kAlignHalf)), vsz, xsz, asz).total;
-    const uint32_t b = has_long ? long_layout(h->T, static_cast<uint32_t>(kLongSlots), vsz).total : 0u;
-    return a > b ? a : b;
+    return smem_layout(h->T, h->W, static_cast<uint32_t>(round_up(Mh, kAlignHalf)), vsz, xsz, asz).total;
 }
 
 int smem_bytes_for(const pars3_handle *h, int dtype) {
-    return static_cast<int>(smem_total(h, dtype, h->L.max_tile_half, !h->L.lrow.empty()));
+    return static_cast<int>(smem_total(h, dtype, h->L.max_tile_half));
+}
+
+// Dynamic shared memory of the plain product's tile kernel.  When no tile
+// has middle entries on the half path, nothing is staged: fp64 tiles keep
+// no row sums in shared memory either (each lane stores its row), fp32 /
+// bf16 tiles only their row sums; the rest of the SM's shared memory then
+// serves as L1 for the gathers of x.
+int spmv_smem_bytes(const pars3_handle *h, int dtype) {
+    if (h->L.max_tile_half > 0) return smem_bytes_for(h, dtype);
+    if (dtype == PARS3_F64) return 0;
+    uint32_t vsz, xsz, asz;
+    dtype_sizes(dtype, &vsz, &xsz, &asz);
+    const SmemLayout s = smem_layout(h->T, h->W, 0u, vsz, xsz, asz);
+    return static_cast<int>(s.rowacc + static_cast<uint32_t>(h->T) * asz);
 }
 
 static int max_smem_all(const pars3_handle *h) {
@@ -191,7 +201,7 @@ static int64_t half_room(const pars3_handle *h) {
         if (!(h->dtypes & PARS3_DTYPE_BIT(d))) continue;
         uint32_t vsz, xsz, asz;
         dtype_sizes(d, &vsz, &xsz, &asz);
-        const int64_t base = smem_total(h, d, 0, false);
+        const int64_t base = smem_total(h, d, 0);
         const int64_t per = vsz + (vsz == asz ? 0 : asz) + 4;
         const int64_t room = static_cast<int64_t>(kSmemLimit) - base - 1024;
         best = std::min<int64_t>(best, room > 0 ? room / per : -1);
@@ -228,11 +238,27 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
             ++tcount[row_of[e] / T];
         }
     }
+    // a tile whose middle entries do not fit shared memory, or are too few
+    // to repay staging the x window (under 1/kHalfMinFrac of the tile's
+    // stored entries), takes them on the full path
     for (int32_t t = 0; t < nt; ++t) {
-        if (tcount[t] > mcap) {
-            const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+        const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+        const int64_t stored = static_cast<int64_t>(rp[r1]) - rp[r0];
+        if (tcount[t] > mcap || static_cast<int64_t>(tcount[t]) * kHalfMinFrac < stored) {
             for (int64_t e = rp[r0]; e < rp[r1]; ++e) half[e] = 0;
             tcount[t] = 0;
+        }
+    }
+    // the launch reserves the largest tile's staging area for every block,
+    // which takes that shared memory away from L1 on every SM: when the half
+    // path would hold under 1/kHalfMinShare of all stored entries it is not
+    // used at all
+    {
+        int64_t hsum = 0;
+        for (int32_t t = 0; t < nt; ++t) hsum += tcount[t];
+        if (hsum * kHalfMinShare < nnz) {
+            std::fill(half.begin(), half.end(), 0);
+            std::fill(tcount.begin(), tcount.end(), 0);
         }
     }
     L.hoff.assign(static_cast<size_t>(nt) + 1, 0);
@@ -383,52 +409,63 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
                 emit_row(i, &L.fcol[L.sl_ent[s2] + l], &fsrc[L.sl_ent[s2] + l], kSlice);
             }
     }
-    // ---- 5. long rows, concatenated and chunked
+    // ---- 5. long rows, concatenated in row order and cut into pieces
     L.lrp.assign(1, 0);
     for (int32_t i = 0; i < n; ++i)
         if (is_long[i]) {
-            const int64_t next = static_cast<int64_t>(L.lrp.back()) + flen[i];
-            if (next > INT32_MAX - kLongChunk) return PARS3_EUNSUPPORTED;   // int32 entry offsets
             L.lrow.push_back(i);
-            L.lrp.push_back(static_cast<int32_t>(next));
+            L.lrp.push_back(static_cast<int32_t>(std::min<int64_t>(static_cast<int64_t>(L.lrp.back()) + flen[i],
+                                                                   INT32_MAX)));
         }
-    const int64_t ltot = L.lrp.back();
-    L.lcol.assign(round_up(ltot, kAlignFull), 0);
-    std::vector<int32_t> lsrc(L.lcol.size(), 0);
-    for (size_t l = 0; l < L.lrow.size(); ++l) emit_row(L.lrow[l], &L.lcol[L.lrp[l]], &lsrc[L.lrp[l]], 1);
-    // chunks: consecutive long entries, at most kLongChunk entries and T rows each
     const size_t nlong = L.lrow.size();
-    L.lc0.assign(nlong, 0);
-    L.lc1.assign(nlong, 0);
-    L.lcslot.assign(1, 0);
-    {
-        size_t l = 0;
-        int64_t beg = 0;
-        while (beg < ltot) {
-            while (L.lrp[l + 1] <= beg) ++l;
-            int64_t end = std::min<int64_t>(ltot, beg + kLongChunk);
-            size_t m = l;
-            while (m + 1 < nlong && L.lrp[m + 1] < end) {
-                if (static_cast<int64_t>(m + 1 - l) + 1 > T) {   // next row would exceed T rows
-                    end = L.lrp[m + 1];
-                    break;
-                }
-                ++m;
-            }
-            const int32_t c = static_cast<int32_t>(L.lcbeg.size());
-            L.lcbeg.push_back(static_cast<int32_t>(beg));
-            L.lcend.push_back(static_cast<int32_t>(end));
-            L.lcfirst.push_back(static_cast<int32_t>(l));
-            L.lcrows.push_back(static_cast<int32_t>(m - l + 1));
-            L.lcslot.push_back(L.lcslot.back() + static_cast<int32_t>(m - l + 1));
-            for (size_t u = l; u <= m; ++u) {
-                if (L.lrp[u] >= beg) L.lc0[u] = c;
-                L.lc1[u] = c;
-            }
-            beg = end;
+    const int64_t ltot = L.lrp.back();
+    if (ltot >= INT32_MAX / 2) return PARS3_EUNSUPPORTED;   // int32 entry offsets
+    std::vector<int32_t> lflat(ltot), lsrc_flat(ltot);
+    for (size_t l = 0; l < nlong; ++l) emit_row(L.lrow[l], &lflat[L.lrp[l]], &lsrc_flat[L.lrp[l]], 1);
+    const int32_t P = h->piece > 0 ? h->piece : kPieceLen;
+    L.piece_len = P;
+    // pieces: (long row, first entry, length); full pieces in row order, then
+    // the shorter last pieces, longest first (ties by row)
+    struct Piece { int32_t l, e0, len; };
+    std::vector<Piece> pieces, rest;
+    L.lp0.assign(nlong + 1, 0);
+    L.lrem.assign(nlong, -1);
+    for (size_t l = 0; l < nlong; ++l) {
+        const int32_t len = L.lrp[l + 1] - L.lrp[l];
+        int32_t q = 0;
+        for (; q + P <= len; q += P) pieces.push_back({static_cast<int32_t>(l), L.lrp[l] + q, P});
+        L.lp0[l + 1] = static_cast<int32_t>(pieces.size());
+        if (q < len) rest.push_back({static_cast<int32_t>(l), L.lrp[l] + q, len - q});
+    }
+    std::stable_sort(rest.begin(), rest.end(), [](const Piece &a, const Piece &b) { return a.len > b.len; });
+    for (const Piece &pc : rest) {
+        L.lrem[pc.l] = static_cast<int32_t>(pieces.size());
+        pieces.push_back(pc);
+    }
+    const int64_t npieces = static_cast<int64_t>(pieces.size());
+    const int64_t nls = (npieces + kSlice - 1) / kSlice;
+    if (nls * kSlice > INT32_MAX / 2) return PARS3_EUNSUPPORTED;
+    L.ls_ent.assign(1, 0);
+    L.ls_len.assign(static_cast<size_t>(nls) * kSlice, 0);
+    for (int64_t sl = 0; sl < nls; ++sl) {
+        const int64_t width = pieces[static_cast<size_t>(sl * kSlice)].len;   // the slice's longest piece
+        const int64_t next = L.ls_ent.back() + width * kSlice;
+        if (next > INT32_MAX - kSlice) return PARS3_EUNSUPPORTED;
+        L.ls_ent.push_back(static_cast<int32_t>(next));
+    }
+    L.lcol.assign(static_cast<size_t>(L.ls_ent.back()), 0);
+    std::vector<int32_t> lsrc(L.lcol.size(), 0);
+    for (int64_t p = 0; p < npieces; ++p) {
+        const Piece &pc = pieces[static_cast<size_t>(p)];
+        const int64_t base = L.ls_ent[p / kSlice] + (p % kSlice);
+        L.ls_len[p] = static_cast<uint16_t>(pc.len);
+        for (int32_t m = 0; m < pc.len; ++m) {
+            L.lcol[base + static_cast<int64_t>(m) * kSlice] = lflat[pc.e0 + m];
+            lsrc[base + static_cast<int64_t>(m) * kSlice] = lsrc_flat[pc.e0 + m];
         }
     }
-    L.nslots = L.lcslot.back();
+    L.nslots = nls * kSlice;
+    L.ls_per_block = h->lsb > 0 ? h->lsb : kLongSlices;
     // ---- 6. fold items: each receiving row once, in row order
     {
         std::vector<int32_t> hidx(n, -1), lidx(n, -1);
@@ -489,7 +526,8 @@ int64_t model_bytes(const pars3_handle *h, int dtype) {
     b += static_cast<int64_t>(L.hcol.size()) * (sv + 2 + 2);               // half values, columns, order
     b += static_cast<int64_t>(L.fcol.size()) * (sv + 4);                   // full rows (sliced ELL)
     b += static_cast<int64_t>(L.sl_meta.size()) * 4 + static_cast<int64_t>(L.sl_ent.size()) * 4;
-    b += static_cast<int64_t>(L.lcol.size()) * (sv + 4);                   // long rows
+    b += static_cast<int64_t>(L.lcol.size()) * (sv + 4);                   // long-row pieces
+    b += L.nslots * (2 + 2 * (sv == 8 ? 8 : 4));                            // piece lengths, sums out and in
     b += static_cast<int64_t>(h->ntiles) * (h->T + 8) * 2;                 // tile row pointers
     b += 2 * static_cast<int64_t>(h->n) * sx;                              // x once, y once
     return b;
@@ -512,6 +550,8 @@ int split_recut(const pars3_handle *src, int32_t T, int32_t W, pars3_handle **ou
         h->nnz = src->nnz;
         h->dtypes = src->dtypes;
         h->long_row = src->long_row;
+        h->piece = src->piece;
+        h->lsb = src->lsb;
         h->symmetric = src->symmetric;
         h->perm = src->perm;
         h->rowptr = src->rowptr;
@@ -551,6 +591,8 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
     if (prm.dtypes & ~7) return PARS3_EINVAL;
     if (prm.flags & ~PARS3_SPLIT_SYMMETRIC) return PARS3_EINVAL;
     if ((prm.T == 0) != (prm.W == 0)) return PARS3_EINVAL;
+    if (prm.long_row < 0 || prm.piece < 0 || (prm.piece > 0 && (prm.piece < 8 || prm.piece > kPieceMax)))
+        return PARS3_EINVAL;
     pars3_handle *h = nullptr;
     try {
         h = new pars3_handle();
@@ -584,6 +626,8 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
         h->W = prm.W;
         h->ntiles = n > 0 ? (n + prm.T - 1) / prm.T : 0;
         h->long_row = prm.long_row > 0 ? prm.long_row : 0;
+        h->piece = prm.piece;
+        h->lsb = prm.reserved[0] > 0 ? std::min<int32_t>(prm.reserved[0], 1024) : 0;
         canonical_reorder(h, rowptr, col, val);
         canonical_classify(h);
         rc = build_layout(h);
@@ -633,11 +677,12 @@ extern "C" int pars3_info_get(const pars3_handle *h, pars3_info *o) {
     o->full_entries = fsum;
     o->long_entries = h->L.lrp.empty() ? 0 : h->L.lrp.back();
     o->long_rows = static_cast<int32_t>(h->L.lrow.size());
-    o->long_chunks = static_cast<int32_t>(h->L.lcbeg.size());
+    o->long_pieces = h->L.lrow.empty() ? 0 : h->L.lp0.back() + static_cast<int32_t>(
+        std::count_if(h->L.lrem.begin(), h->L.lrem.end(), [](int32_t r) { return r >= 0; }));
     o->halo_targets = static_cast<int64_t>(h->L.hhrow.size());
     o->max_tile_half = h->L.max_tile_half;
     for (int d = 0; d < kNumDtypes; ++d) {
-        o->smem_bytes[d] = (h->dtypes & PARS3_DTYPE_BIT(d)) ? smem_bytes_for(h, d) : 0;
+        o->smem_bytes[d] = (h->dtypes & PARS3_DTYPE_BIT(d)) ? spmv_smem_bytes(h, d) : 0;
         o->bytes_per_spmv[d] = model_bytes(h, d);
     }
     o->device_bytes = h->D.bytes;
@@ -702,25 +747,35 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
             for (int32_t rl = 0; rl < r1 - r0; ++rl)
                 if (!seen[rl]) return PARS3_EINVAL;   // every row owns a lane
         }
-        for (size_t l = 0; l < L.lrow.size(); ++l)
-            for (int32_t q = L.lrp[l]; q < L.lrp[l + 1]; ++q)
-                got.push_back({L.lrow[l], L.lcol[q], has64 ? L.lval64[q] : 0.0});
-        // chunks tile the long list in order; slots consecutive; row spans consistent
-        int64_t pos = 0;
-        for (size_t c = 0; c < L.lcbeg.size(); ++c) {
-            if (L.lcbeg[c] != pos || L.lcend[c] <= L.lcbeg[c] || L.lcend[c] - L.lcbeg[c] > kLongChunk) return PARS3_EINVAL;
-            pos = L.lcend[c];
-            const int32_t l0 = L.lcfirst[c];
-            if (!(L.lrp[l0] <= L.lcbeg[c] && L.lcbeg[c] < L.lrp[l0 + 1])) return PARS3_EINVAL;
-            if (L.lcslot[c + 1] - L.lcslot[c] != L.lcrows[c] || L.lcrows[c] > T) return PARS3_EINVAL;
-        }
-        if (!L.lrow.empty() && pos != L.lrp.back()) return PARS3_EINVAL;
+        // long rows: every piece of row l (its full pieces, then its last
+        // piece) lies in the long slices with its length; together they hold
+        // the row's entries
+        const int64_t nslot = static_cast<int64_t>(L.nls()) * kSlice;
+        if (static_cast<int64_t>(L.ls_len.size()) != nslot || L.nslots != nslot) return PARS3_EINVAL;
+        std::vector<uint8_t> pseen(static_cast<size_t>(nslot), 0);
         for (size_t l = 0; l < L.lrow.size(); ++l) {
-            if (L.lrp[l + 1] <= L.lrp[l]) return PARS3_EINVAL;   // every long row has an entry
-            const int32_t c0 = L.lc0[l], c1 = L.lc1[l];
-            if (!(L.lcbeg[c0] <= L.lrp[l] && L.lrp[l] < L.lcend[c0])) return PARS3_EINVAL;
-            if (!(L.lcbeg[c1] < L.lrp[l + 1] && L.lrp[l + 1] <= L.lcend[c1])) return PARS3_EINVAL;
+            std::vector<int32_t> ps;
+            for (int32_t p = L.lp0[l]; p < L.lp0[l + 1]; ++p) ps.push_back(p);
+            if (L.lrem[l] >= 0) ps.push_back(L.lrem[l]);
+            int64_t cnt = 0;
+            for (size_t u = 0; u < ps.size(); ++u) {
+                const int32_t p = ps[u];
+                if (p < 0 || p >= nslot || pseen[p]) return PARS3_EINVAL;
+                pseen[p] = 1;
+                const int32_t len = L.ls_len[p], s2 = p / kSlice, lane = p % kSlice;
+                const int32_t width = (L.ls_ent[s2 + 1] - L.ls_ent[s2]) / kSlice;
+                if (len < 1 || len > width || len > L.piece_len) return PARS3_EINVAL;
+                if (u + 1 < ps.size() && len != L.piece_len) return PARS3_EINVAL;   // only the last is short
+                for (int32_t m = 0; m < len; ++m) {
+                    const int64_t q = L.ls_ent[s2] + static_cast<int64_t>(m) * kSlice + lane;
+                    got.push_back({L.lrow[l], L.lcol[q], has64 ? L.lval64[q] : 0.0});
+                }
+                cnt += len;
+            }
+            if (cnt < 1 || cnt != L.lrp[l + 1] - L.lrp[l]) return PARS3_EINVAL;
         }
+        for (int64_t p = 0; p < nslot; ++p)
+            if (!pseen[p] && L.ls_len[p] != 0) return PARS3_EINVAL;   // padding lanes are empty
         if (got.size() != want.size()) return PARS3_EINVAL;
         auto key = [](const E &a, const E &b) { return a.r != b.r ? a.r < b.r : a.c < b.c; };
         std::sort(want.begin(), want.end(), key);

@@ -13,9 +13,14 @@ constexpr int kNumDtypes = 3;
 constexpr int kAlignHalf = 8;          // half-path tile segments start on 16-byte boundaries (u16, bf16)
 constexpr int kAlignFull = 16;         // full-path tile segments: 64 B for int32 columns, 128 B for fp64
 constexpr int kBlock = 512;            // threads of the tile kernel (one block per row tile or long chunk)
-constexpr int kLongChunk = 4096;       // entries per long-row chunk (one block each)
+constexpr int kPieceLen = 192;         // default entries per long-row piece
+constexpr int kPieceMax = 255;         // longest piece the layout allows
+constexpr int kLongSlices = 32;        // long-row slices per block
 constexpr int kLongMin = 256;          // shortest row moved to the long path to balance tiles
 constexpr int kSellMax = 128;          // longer full-path rows go to the long path
+constexpr int kHalfMinFrac = 4;        // a tile keeps its middle entries on the half path only when they
+                                       // are at least 1/kHalfMinFrac of its stored entries
+constexpr int kHalfMinShare = 16;      // ... and the half path only when it holds 1/kHalfMinShare of all
 constexpr int kSlice = 32;             // rows per sliced-ELL slice (one warp)
 constexpr int kSmemLimit = 227 * 1024; // opt-in shared memory per block on sm_100/sm_103
 
@@ -40,16 +45,24 @@ struct Layout {
     std::vector<int32_t> sl_ent;    // [nslices+1]
     std::vector<uint32_t> sl_meta;  // [nslices*32]
     std::vector<int32_t> fcol;
-    // long rows: full entries of long row l are [lrp[l], lrp[l+1]) of lcol/lval;
-    // chunk c covers entries [lcbeg[c], lcend[c]) (at most kLongChunk entries
-    // and T rows) and touches long rows lcfirst[c] .. lcfirst[c]+lcrows[c]-1,
-    // whose partial sums go to slots lcslot[c] + u; long row l spans chunks
-    // lc0[l] .. lc1[l]
+    // long rows: long row l is global row lrow[l]; its full-storage entries
+    // (in the order of a tile row: lower entries, then mirrored ones), lrp[l]
+    // .. lrp[l+1]-1 of the concatenated list (host only), are cut into pieces
+    // of piece_len entries and a shorter last piece.  Pieces are laid out
+    // like the tile slices: piece p is lane p % 32 of long slice p / 32, its
+    // slot m at ls_ent[s] + 32 m + lane of lcol/lval, length ls_len[p].  The
+    // full pieces come first, in row order (those of row l are lp0[l] ..
+    // lp0[l+1]-1), then the last pieces, longest first (ties by row); lrem[l]
+    // is row l's last piece or -1.  The sum of piece p goes to lpart[p].
     std::vector<int32_t> lrow;      // [nlong]
-    std::vector<int32_t> lrp;       // [nlong+1]
-    std::vector<int32_t> lc0, lc1;  // [nlong]
-    std::vector<int32_t> lcbeg, lcend, lcfirst, lcrows, lcslot;  // [nchunks] (+1 for lcslot)
-    std::vector<int32_t> lcol;      // padded to kAlignFull
+    std::vector<int32_t> lrp;       // [nlong+1] (host only)
+    std::vector<int32_t> lp0;       // [nlong+1]
+    std::vector<int32_t> lrem;      // [nlong]
+    std::vector<int32_t> ls_ent;    // [nls+1]
+    std::vector<uint16_t> ls_len;   // [nls*32]
+    std::vector<int32_t> lcol;      // slot-major, padded slots hold column 0 and value 0
+    int32_t piece_len = 0;
+    int32_t ls_per_block = kLongSlices;   // long slices per block
     // fold items: one per row that receives a halo sum and/or long-row partials
     std::vector<int32_t> fold_row, fold_halo, fold_long;  // halo index / long index or -1
     // values per precision (fp64 / fp32 / bf16 bits)
@@ -60,7 +73,9 @@ struct Layout {
     int32_t max_tile_full = 0;      // sliced-ELL entries (with padding) of the largest tile
     int32_t max_tile_slices = 0;
     int32_t cap_full = 0;
-    int64_t nslots = 0;
+    int64_t nslots = 0;             // long-row piece sums (32 per long slice)
+    int32_t nls() const { return ls_ent.empty() ? 0 : static_cast<int32_t>(ls_ent.size()) - 1; }
+    int32_t nlong_blocks() const { return (nls() + ls_per_block - 1) / ls_per_block; }
 };
 
 struct DevLayout {
@@ -70,14 +85,14 @@ struct DevLayout {
     int32_t *sl_off = nullptr, *sl_ent = nullptr;
     uint32_t *sl_meta = nullptr;
     int32_t *fcol = nullptr;
-    int32_t *lrow = nullptr, *lrp = nullptr, *lc0 = nullptr, *lc1 = nullptr;
-    int32_t *lcbeg = nullptr, *lcend = nullptr, *lcfirst = nullptr, *lcrows = nullptr, *lcslot = nullptr;
+    int32_t *lp0 = nullptr, *lrem = nullptr, *ls_ent = nullptr;
+    uint16_t *ls_len = nullptr;
     int32_t *lcol = nullptr;
     int32_t *fold_row = nullptr, *fold_halo = nullptr, *fold_long = nullptr;
     void *hval[kNumDtypes] = {nullptr, nullptr, nullptr};
     void *fval[kNumDtypes] = {nullptr, nullptr, nullptr};
     void *lval[kNumDtypes] = {nullptr, nullptr, nullptr};
-    // scratch: halo sums and long-row partial sums (fp64-sized, scratch_k columns)
+    // scratch: halo sums and long-row piece sums (fp64-sized, scratch_k columns)
     void *halo = nullptr;
     void *lpart = nullptr;
     int32_t scratch_k = 0;
@@ -100,6 +115,8 @@ struct pars3_handle {
     int32_t T = 0, W = 0, ntiles = 0;
     int32_t dtypes = 0;
     int32_t long_row = 0;
+    int32_t piece = 0;               // entries per long-row piece requested (0 = kPieceLen)
+    int32_t lsb = 0;                 // long slices per block requested (0 = kLongSlices)
     int32_t symmetric = 0;           // S = L + L^T instead of L - L^T (mirror sign +1)
     int64_t bw = 0;
     // canonical split (host)
@@ -133,6 +150,7 @@ int ready_on_device(const pars3_handle *h);
 void auto_cut(int64_t bw, int32_t w_min, int32_t w_cap, int32_t t_min, int32_t *T, int32_t *W);
 int build_layout(pars3_handle *h);
 int smem_bytes_for(const pars3_handle *h, int dtype);
+int spmv_smem_bytes(const pars3_handle *h, int dtype);
 
 int sm_count();
 void dtype_sizes(int dtype, uint32_t *vsz, uint32_t *xsz, uint32_t *asz);

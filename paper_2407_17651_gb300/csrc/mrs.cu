@@ -38,9 +38,9 @@ constexpr int kMaxRedBlocks = 1024;
 template <typename XT, typename AT>
 __global__ void __launch_bounds__(kRedBlock) fold_mrs_kernel(
     int nitems, const int32_t *__restrict__ frow, const int32_t *__restrict__ fhalo,
-    const int32_t *__restrict__ flong, const AT *__restrict__ halo, const int32_t *__restrict__ lc0,
-    const int32_t *__restrict__ lc1, const int32_t *__restrict__ lcfirst, const int32_t *__restrict__ lcslot,
-    const AT *__restrict__ lpart, const MrsVectors<XT> m, int ntiles, cudaGraphConditionalHandle cond,
+    const int32_t *__restrict__ flong, const AT *__restrict__ halo, const int32_t *__restrict__ lp0,
+    const int32_t *__restrict__ lrem, const AT *__restrict__ lpart, const MrsVectors<XT> m, int ntiles,
+    cudaGraphConditionalHandle cond,
     int in_graph) {
     __shared__ double red[32];
     MrsState *st = m.st;
@@ -58,8 +58,7 @@ __global__ void __launch_bounds__(kRedBlock) fold_mrs_kernel(
         const int hi = fhalo[f];
         if (hi >= 0) s += halo[hi];
         const int l = flong[f];
-        if (l >= 0)
-            for (int c = lc0[l]; c <= lc1[l]; ++c) s += lpart[lcslot[c] + (l - lcfirst[c])];
+        if (l >= 0) s = long_row_sum<AT>(l, lp0, lrem, lpart, 1, 0, s);
         const XT wx = static_cast<XT>(static_cast<AT>(y[r]) + s * scale);
         y[r] = wx;
         nrm += static_cast<double>(wx) * static_cast<double>(wx);
@@ -234,44 +233,7 @@ static int ensure_work(pars3_handle *h, MrsWork *&W) {
 
 template <typename VT, typename XT, typename AT>
 static SpmvArgs<VT, XT, AT> spmv_args(const pars3_handle *h, int dtype) {
-    const Layout &L = h->L;
-    const DevLayout &D = h->D;
-    SpmvArgs<VT, XT, AT> a;
-    a.n = h->n;
-    a.T = h->T;
-    a.W = h->W;
-    a.ntiles = h->ntiles;
-    a.nchunks = static_cast<int32_t>(L.lcbeg.size());
-    a.Mh = static_cast<int32_t>(round_up(L.max_tile_half, kAlignHalf));
-    a.hoff = D.hoff;
-    a.hcnt = D.hcnt;
-    a.hrp = D.hrp;
-    a.hcol = D.hcol;
-    a.hcperm = D.hcperm;
-    a.hval = static_cast<const VT *>(D.hval[dtype]);
-    a.hhoff = D.hhoff;
-    a.hhrow = D.hhrow;
-    a.halo = static_cast<AT *>(D.halo);
-    a.sl_off = D.sl_off;
-    a.sl_ent = D.sl_ent;
-    a.sl_meta = D.sl_meta;
-    a.fcol = D.fcol;
-    a.fval = static_cast<const VT *>(D.fval[dtype]);
-    a.lrp = D.lrp;
-    a.lcbeg = D.lcbeg;
-    a.lcend = D.lcend;
-    a.lcfirst = D.lcfirst;
-    a.lcrows = D.lcrows;
-    a.lcslot = D.lcslot;
-    a.lcol = D.lcol;
-    a.lval = static_cast<const VT *>(D.lval[dtype]);
-    a.lpart = static_cast<AT *>(D.lpart);
-    a.x = nullptr;
-    a.y = nullptr;
-    a.alpha = AT(0);
-    a.err = D.err;
-    a.sym = h->symmetric;
-    return a;
+    return make_spmv_args<VT, XT, AT>(h, dtype);
 }
 
 // largest dynamic shared memory of a launch (the fused kernel also has a
@@ -318,7 +280,7 @@ static int build_graph(pars3_handle *h, int dtype, MrsWork &W) {
     const Layout &L = h->L;
     // fusing the step into the tile kernel saves a launch per iteration in
     // fp64 (measured 2 %) but costs 8 % in fp32, where the separate fold wins
-    const bool fused = sizeof(AT) == 8 && L.fold_row.empty() && L.lcbeg.empty() &&
+    const bool fused = sizeof(AT) == 8 && L.fold_row.empty() && L.lrow.empty() &&
                        smem + static_cast<int>(kStaticSlack) <= kSmemLimit;
     cudaError_t e = cudaSuccess;
     if (stage && fused) e = set_mrs_smem<VT, XT, AT, true, true>(smem);
@@ -340,7 +302,7 @@ static int build_graph(pars3_handle *h, int dtype, MrsWork &W) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(W.capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_status(e);
-    const int grid = h->ntiles + a.nchunks;
+    const int grid = a.nlb + h->ntiles;
     const DevLayout &D = h->D;
     // kBodyUnroll iterations per pass of the while node (each launch returns
     // at once after convergence), so the node's own cost is paid less often
@@ -352,7 +314,7 @@ static int build_graph(pars3_handle *h, int dtype, MrsWork &W) {
         if (!fused)
             fold_mrs_kernel<XT, AT><<<fold_blocks(h), kRedBlock, 0, W.capture>>>(
                 static_cast<int>(L.fold_row.size()), D.fold_row, D.fold_halo, D.fold_long,
-                static_cast<const AT *>(D.halo), D.lc0, D.lc1, D.lcfirst, D.lcslot, static_cast<const AT *>(D.lpart),
+                static_cast<const AT *>(D.halo), D.lp0, D.lrem, static_cast<const AT *>(D.lpart),
                 m, h->ntiles, G.cond, 1);
     }
     cudaGraph_t captured = nullptr;
@@ -405,7 +367,7 @@ static int inner_solve(pars3_handle *h, int dtype, MrsWork &W, double alpha, dou
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaGraphLaunch(W.g[dtype].exec, st);
     if (e != cudaSuccess) return cuda_status(e);
-    const int fb = std::min(152 * 8, (n + 255) / 256);
+    const int fb = std::min(8 * sm_count(), (n + 255) / 256);
     if (dtype == PARS3_F64) {
         MrsVectors<double> m = vectors<double>(W, dtype);
         mrs_finish_kernel<double, double><<<fb, 256, 0, st>>>(n, m);

@@ -15,12 +15,9 @@ namespace pars3 {
 
 // Dynamic shared memory of the tile kernel.  A tile block holds the x
 // window, the tile's middle entries (filled by TMA bulk copies) and scratch;
-// a long-chunk block uses the same buffer for the chunk's entries.
+// a block of long-row pieces uses none.
 struct SmemLayout {
     uint32_t xs, rowacc, hval, q, hcol, cperm, hrp, cs, ce, red, mbar, total;
-};
-struct LongLayout {
-    uint32_t fval, fcol, flp, pstart, ppart, mbar, total;
 };
 
 PARS3_HD uint32_t align128(uint32_t a) { return (a + 127u) & ~127u; }
@@ -41,24 +38,6 @@ PARS3_HD SmemLayout smem_layout(uint32_t T, uint32_t W, uint32_t Mh, uint32_t vs
     s.ce = align128(s.cs + (T + W) * 2u);
     s.red = align128(s.ce + (T + W) * 2u);
     s.mbar = align128(s.red + 32u * 8u);
-    s.total = align128(s.mbar + 8u);
-    return s;
-}
-
-// F: staged entries of a long-row chunk (with alignment slack); rows of a
-// chunk: at most T; pstart: the first piece of each row of the chunk; ppart:
-// the partial sums of rows cut into several pieces.
-PARS3_HD LongLayout long_layout(uint32_t T, uint32_t F, uint32_t vsz) {
-    LongLayout s;
-    s.fval = 0;
-    s.fcol = align128(s.fval + F * vsz);
-    s.flp = align128(s.fcol + F * 4u);
-    // a chunk touches at most F rows (each has an entry in it); its pieces of
-    // at most 128 entries number at most rows + F / 128
-    const uint32_t R = T < F ? T : F;
-    s.pstart = align128(s.flp + (T + 8u) * 2u);
-    s.ppart = align128(s.pstart + (R + 8u) * 2u);   // fp64-sized partial sums
-    s.mbar = align128(s.ppart + (R + F / 128u + 8u) * 8u);
     s.total = align128(s.mbar + 8u);
     return s;
 }

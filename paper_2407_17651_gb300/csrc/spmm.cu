@@ -1,8 +1,9 @@
 // spmm.cu -- Y = (alpha I + S) X for k right-hand sides (X, Y row-major,
 // 1 <= k <= 32) on the split layout of the skew product.
 //
-// Same decomposition as the single product (one block per row tile plus one
-// per long-row chunk, then a fold); the device code is in spmm_device.cuh.
+// Same decomposition as the single product (blocks of long-row pieces, then
+// one block per row tile, then a fold); the device code is in
+// spmm_device.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,20 +16,18 @@ namespace pars3 {
 template <typename VT, typename XT, typename AT, int LPR, int NV>
 __global__ void __launch_bounds__(kBlock, 2) spmm_kernel(const SpmvArgs<VT, XT, AT> a, int k) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (static_cast<int>(blockIdx.x) < a.ntiles) spmm_tile<VT, XT, AT, LPR, NV>(a, k, blockIdx.x, smem);
-    else spmm_long<VT, XT, AT, LPR, NV>(a, k, blockIdx.x - a.ntiles);
+    if (static_cast<int>(blockIdx.x) < a.nlb) spmm_long<VT, XT, AT, LPR, NV>(a, k, blockIdx.x);
+    else spmm_tile<VT, XT, AT, LPR, NV>(a, k, blockIdx.x - a.nlb, smem);
 }
 
-// y[row, c] += halo sum + long-row partial sums (chunk order), one thread per
-// (receiving row, column)
+// y[row, c] += halo sum + long-row piece sums (in the row's order), one
+// thread per (receiving row, column)
 template <typename XT, typename AT>
 __global__ void __launch_bounds__(256) fold_spmm_kernel(int nitems, int k, const int32_t *__restrict__ frow,
                                                         const int32_t *__restrict__ fhalo,
                                                         const int32_t *__restrict__ flong,
-                                                        const AT *__restrict__ halo, const int32_t *__restrict__ lc0,
-                                                        const int32_t *__restrict__ lc1,
-                                                        const int32_t *__restrict__ lcfirst,
-                                                        const int32_t *__restrict__ lcslot,
+                                                        const AT *__restrict__ halo, const int32_t *__restrict__ lp0,
+                                                        const int32_t *__restrict__ lrem,
                                                         const AT *__restrict__ lpart, XT *__restrict__ y) {
     const int64_t total = static_cast<int64_t>(nitems) * k;
     for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
@@ -39,9 +38,7 @@ __global__ void __launch_bounds__(256) fold_spmm_kernel(int nitems, int k, const
         const int hi = fhalo[f];
         if (hi >= 0) v += halo[static_cast<int64_t>(hi) * k + c];
         const int l = flong[f];
-        if (l >= 0)
-            for (int ch = lc0[l]; ch <= lc1[l]; ++ch)
-                v += lpart[static_cast<int64_t>(lcslot[ch] + (l - lcfirst[ch])) * k + c];
+        if (l >= 0) v = long_row_sum<AT>(l, lp0, lrem, lpart, k, c, v);
         y[r * k + c] = static_cast<XT>(v);
     }
 }
@@ -60,41 +57,12 @@ static int launch_spmm_lpr(const pars3_handle *h, int dtype, double alpha, int k
                            void *halo, void *lpart, cudaStream_t st) {
     const Layout &L = h->L;
     const DevLayout &D = h->D;
-    SpmvArgs<VT, XT, AT> a;
-    a.n = h->n;
-    a.T = h->T;
-    a.W = h->W;
-    a.ntiles = h->ntiles;
-    a.nchunks = static_cast<int32_t>(L.lcbeg.size());
-    a.Mh = static_cast<int32_t>(round_up(L.max_tile_half, kAlignHalf));
-    a.hoff = D.hoff;
-    a.hcnt = D.hcnt;
-    a.hrp = D.hrp;
-    a.hcol = D.hcol;
-    a.hcperm = D.hcperm;
-    a.hval = static_cast<const VT *>(D.hval[dtype]);
-    a.hhoff = D.hhoff;
-    a.hhrow = D.hhrow;
+    SpmvArgs<VT, XT, AT> a = make_spmv_args<VT, XT, AT>(h, dtype);
     a.halo = static_cast<AT *>(halo);
-    a.sl_off = D.sl_off;
-    a.sl_ent = D.sl_ent;
-    a.sl_meta = D.sl_meta;
-    a.fcol = D.fcol;
-    a.fval = static_cast<const VT *>(D.fval[dtype]);
-    a.lrp = D.lrp;
-    a.lcbeg = D.lcbeg;
-    a.lcend = D.lcend;
-    a.lcfirst = D.lcfirst;
-    a.lcrows = D.lcrows;
-    a.lcslot = D.lcslot;
-    a.lcol = D.lcol;
-    a.lval = static_cast<const VT *>(D.lval[dtype]);
     a.lpart = static_cast<AT *>(lpart);
     a.x = static_cast<const XT *>(X);
     a.y = static_cast<XT *>(Y);
     a.alpha = static_cast<AT>(alpha);
-    a.err = D.err;
-    a.sym = h->symmetric;
     const int smem = spmm_smem_bytes(h, dtype);
     static std::atomic<uint64_t> configured{0};   // one bit per device
     const uint64_t dbit = device_bit();
@@ -104,16 +72,15 @@ static int launch_spmm_lpr(const pars3_handle *h, int dtype, double alpha, int k
         if (e != cudaSuccess) return cuda_status(e);
         configured.fetch_or(dbit);
     }
-    const int grid = h->ntiles + a.nchunks;
+    const int grid = a.nlb + h->ntiles;
     if (grid > 0) spmm_kernel<VT, XT, AT, LPR, NV><<<grid, kBlock, smem, st>>>(a, k);
     const int nf = static_cast<int>(L.fold_row.size());
     if (nf > 0) {
         const int64_t total = static_cast<int64_t>(nf) * k;
-        const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 8));
+        const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 8LL * sm_count()));
         fold_spmm_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, k, D.fold_row, D.fold_halo, D.fold_long,
-                                                         static_cast<const AT *>(halo), D.lc0, D.lc1, D.lcfirst,
-                                                         D.lcslot, static_cast<const AT *>(lpart),
-                                                         static_cast<XT *>(Y));
+                                                         static_cast<const AT *>(halo), D.lp0, D.lrem,
+                                                         static_cast<const AT *>(lpart), static_cast<XT *>(Y));
     }
     return cuda_status(cudaGetLastError());
 }

@@ -312,23 +312,30 @@ __device__ __forceinline__ void spmm_tile(const SpmvArgs<VT, XT, AT> &a, int k, 
     }
 }
 
-// Long-row chunk: one lane group per row touched, entries read in order.
+// Block b of long-row pieces (long slices [b lsb, (b+1) lsb)):
+// a lane group per piece, walking the pieces in slice order so that
+// neighbouring groups read neighbouring slots; the k-wide sum of piece p goes
+// to lpart[p k ..], and the fold adds a row's pieces in order.  A row of tens
+// of thousands of entries thus spreads over hundreds of lane groups.
 template <typename VT, typename XT, typename AT, int LPR, int NV>
-__device__ __forceinline__ void spmm_long(const SpmvArgs<VT, XT, AT> &a, int k, int cidx) {
+__device__ __forceinline__ void spmm_long(const SpmvArgs<VT, XT, AT> &a, int k, int b) {
     const int tid = threadIdx.x, P = blockDim.x;
-    const int beg = a.lcbeg[cidx], end = a.lcend[cidx];
-    const int l0 = a.lcfirst[cidx], nrc = a.lcrows[cidx];
     const int g = tid / LPR, c0 = (tid % LPR) * NV, ng = P / LPR;
     const bool on = c0 < k;
-    for (int u = g; u < nrc; u += ng) {
-        const int e0 = max(a.lrp[l0 + u], beg), e1 = min(a.lrp[l0 + u + 1], end);
+    const int s0 = b * a.lsb, s1 = min(s0 + a.lsb, a.nls);
+    const int nslot = (s1 - s0) * kSlice;
+    for (int q = g; q < nslot; q += ng) {
+        const int64_t p = static_cast<int64_t>(s0) * kSlice + q;
+        const int s = static_cast<int>(p / kSlice), l = static_cast<int>(p % kSlice);
+        const int len = __ldg(a.ls_len + p);
         AT acc[NV];
 #pragma unroll
         for (int w = 0; w < NV; ++w) acc[w] = AT(0);
-        spmm_strided_sum<VT, XT, AT, NV>(a.lval, a.lcol, e0, 1, max(e1 - e0, 0), a.x, k, c0, on, acc);
+        spmm_strided_sum<VT, XT, AT, NV>(a.lval, a.lcol, static_cast<int64_t>(__ldg(a.ls_ent + s)) + l, kSlice, len,
+                                         a.x, k, c0, on, acc);
         if (on)
 #pragma unroll
-            for (int w = 0; w < NV; ++w) a.lpart[static_cast<int64_t>(a.lcslot[cidx] + u) * k + c0 + w] = acc[w];
+            for (int w = 0; w < NV; ++w) a.lpart[p * k + c0 + w] = acc[w];
     }
 }
 

@@ -3,9 +3,9 @@
 // kernel in its Lanczos mode).
 //
 // Two launches per product: the tile kernel (one block per row tile -- the
-// block-row ownership of Sec. 3 and Fig. 2 -- plus one block per chunk of
-// the long-row list) and a small fold kernel that adds the cross-tile
-// (halo) mirrored sums and the long-row partial sums to y.  No atomics:
+// block-row ownership of Sec. 3 and Fig. 2 -- after the blocks that sum the
+// pieces of long rows) and a small fold kernel that adds the cross-tile
+// (halo) mirrored sums and the long-row piece sums to y.  No atomics:
 // every y entry has one writer per launch and every sum runs in an order
 // fixed by the layout and the block size, so results are bitwise
 // reproducible from run to run.
@@ -41,7 +41,8 @@ namespace pars3 {
 
 template <typename VT, typename XT, typename AT>
 struct SpmvArgs {
-    int32_t n, T, W, ntiles, nchunks, Mh;
+    int32_t n, T, W, ntiles, Mh;
+    int32_t nls, nlb, lsb;   // long-row slices, their blocks (launched before the tiles), slices per block
     const int32_t *hoff, *hcnt;
     const uint16_t *hrp, *hcol, *hcperm;
     const VT *hval;
@@ -51,7 +52,9 @@ struct SpmvArgs {
     const uint32_t *sl_meta;
     const int32_t *fcol;
     const VT *fval;
-    const int32_t *lrp, *lcbeg, *lcend, *lcfirst, *lcrows, *lcslot, *lcol;
+    const int32_t *ls_ent;
+    const uint16_t *ls_len;
+    const int32_t *lcol;
     const VT *lval;
     AT *lpart;
     const XT *x;
@@ -713,120 +716,69 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     epi.end_block(t, red);
 }
 
-// Long-row chunk c: entries [lcbeg[c], lcend[c]) of the long list, staged by
-// TMA from the 16-entry boundary below.  Each row of the chunk is cut into
-// pieces of at most kPiece entries, and each piece is summed by a group of
-// eight lanes (four groups per warp, pieces taken in order by the block's
-// groups): lane j of the group takes entries 32 r + 8 m + j of the piece
-// (four in flight), then three butterfly steps inside the group.  A row of
-// one piece writes its slot directly; the pieces of a longer row leave their
-// sums in shared memory and one thread adds them in piece order.  A chunk
-// inside one row of tens of thousands of entries thus keeps 32 groups busy,
-// and a short row costs three fp64 additions for its reduction instead of the
-// five of a whole-warp butterfly (the fp64 pipe is narrow on this part).
-// Every long row has at least one entry, so the row pointers of a chunk
-// increase strictly.  The order of every sum is fixed by the layout.
-// Not inlined: inlined into the tile kernel, this path changed how the
-// compiler laid out the tile path (fp64 tiles of the 128^3 + 1 % matrix,
-// which has no long rows: 46.0 -> 47.9 us per product; 46.2 us not inlined).
-constexpr int kPiece = 128;
+// Sum of one long-row piece, lane l of a long slice: slots base + 32 m
+// (m < len) of lval / lcol, in rounds of eight slots sized to the slice's
+// width w (warp-uniform: every piece but the last of each row has the same
+// length, so nearly every lane of a round holds an entry).  The next round's
+// columns are loaded while this round's values and x gathers are in flight,
+// so a round waits on one round trip (fp64: the 64-register budget holds the
+// extra columns; fp32 / bf16, compiled for three blocks per SM, load each
+// round's columns with its values).  Nothing is staged in shared memory and
+// no lanes are combined: each piece is one lane's sequential sum, and the
+// fold adds a row's pieces in order.
 template <typename VT, typename XT, typename AT>
-__device__ __noinline__ void long_block(const SpmvArgs<VT, XT, AT> &a, int c, unsigned char *smem,
-                                           const XT *__restrict__ xop) {
-    const LongLayout L = long_layout(a.T, kLongChunk + 2 * kAlignFull, sizeof(VT));
-    VT *fval = reinterpret_cast<VT *>(smem + L.fval);
-    int32_t *fcol = reinterpret_cast<int32_t *>(smem + L.fcol);
-    uint16_t *flp = reinterpret_cast<uint16_t *>(smem + L.flp);
-    uint16_t *pstart = reinterpret_cast<uint16_t *>(smem + L.pstart);
-    AT *ppart = reinterpret_cast<AT *>(smem + L.ppart);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
-    const int tid = threadIdx.x, P = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int beg = a.lcbeg[c], end = a.lcend[c];
-    const int abeg = beg & ~(kAlignFull - 1);
-    const uint32_t mp = static_cast<uint32_t>((end - abeg + kAlignFull - 1) / kAlignFull * kAlignFull);
-    const int l0 = a.lcfirst[c], nrc = a.lcrows[c];
-    if (tid == 0) {
-        mbar_init(mbar, 1);
-        fence_mbar_init();
-        mbar_arrive_expect_tx(mbar, mp * (sizeof(VT) + 4u));
-        bulk_g2s(fval, a.lval + abeg, mp * sizeof(VT), mbar);
-        bulk_g2s(fcol, a.lcol + abeg, mp * 4u, mbar);
-    }
-    for (int u = tid; u <= nrc; u += P) flp[u] = static_cast<uint16_t>(min(max(a.lrp[l0 + u], beg), end) - beg);
-    __syncthreads();
-    if (warp == 0) {   // pstart: exclusive prefix sum of the rows' piece counts
-        int carry = 0;
-        for (int b0 = 0; b0 < nrc; b0 += 32) {
-            const int u = b0 + lane;
-            const int v = u < nrc ? (flp[u + 1] - flp[u] + kPiece - 1) / kPiece : 0;
-            int incl = v;
+__device__ __forceinline__ AT piece_sum(const VT *__restrict__ val, const int32_t *__restrict__ col, int64_t base,
+                                        int len, int w, const XT *__restrict__ xg) {
+    constexpr bool kAhead = sizeof(AT) == 8;
+    if constexpr (!kAhead) return slice_row_sum_uniform<VT, XT, AT>(val, col, base, len, w, xg, AT(0));
+    int c[kUnroll];
+    slice_cols(col, base, len, c);
+    AT acc = AT(0);
+    for (int m0 = 0; m0 < w; m0 += kUnroll) {
+        const int rem = len - m0;
+        const int64_t q0 = base + static_cast<int64_t>(m0) * kSlice;
+        AT v[kUnroll], xv[kUnroll];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
+        for (int u = 0; u < kUnroll; ++u) {
+            v[u] = AT(0);
+            xv[u] = AT(0);
+            if (u < rem) {
+                v[u] = Val<VT>::ld_stream(val + q0 + static_cast<int64_t>(u) * kSlice);
+                xv[u] = static_cast<AT>(__ldg(xg + c[u]));
             }
-            if (u < nrc) pstart[u] = static_cast<uint16_t>(carry + incl - v);
-            carry += __shfl_sync(0xffffffffu, incl, 31);
         }
-        if (lane == 0) pstart[nrc] = static_cast<uint16_t>(carry);
-    }
-    mbar_wait_bounded(mbar, 0, a.err);
-    __syncthreads();
-    if (tid == 0) mbar_inval(mbar);
-    const int32_t *col_s = fcol + (beg - abeg);
-    const VT *val_s = fval + (beg - abeg);
-    AT *slot = a.lpart + a.lcslot[c];
-    const int npieces = pstart[nrc];
-    const int grp = tid >> 3, j = tid & 7, ngrp = P >> 3;
-    for (int p0 = 0; p0 < npieces; p0 += ngrp) {   // block-uniform
-        const int p = p0 + grp;
-        int u = 0, e0 = 0, e1 = 0;
-        if (p < npieces) {   // the row of piece p: the largest u with pstart[u] <= p
-            int ua = 0, ub = nrc - 1;
-            while (ua < ub) {
-                const int mid = (ua + ub + 1) >> 1;
-                if (pstart[mid] <= p) ua = mid;
-                else ub = mid - 1;
-            }
-            u = ua;
-            e0 = flp[u] + (p - pstart[u]) * kPiece;
-            e1 = min(e0 + kPiece, static_cast<int>(flp[u + 1]));
-        }
-        const int rounds = __reduce_max_sync(0xffffffffu, static_cast<unsigned>((e1 - e0 + 31) >> 5));
-        AT acc = AT(0);
-        for (int r = 0; r < rounds; ++r) {
-            AT v[4], xv[4];
+        const int64_t q1 = q0 + static_cast<int64_t>(kUnroll) * kSlice;
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int e = e0 + 32 * r + 8 * m + j;
-                v[m] = AT(0);
-                xv[m] = AT(0);
-                if (e < e1) {
-                    v[m] = sval<VT>(val_s, e);
-                    xv[m] = static_cast<AT>(__ldg(xop + col_s[e]));
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                if (e0 + 32 * r + 8 * m + j < e1) acc += v[m] * xv[m];
-        }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        if (p < npieces && j == 0) {
-            if (pstart[u + 1] - pstart[u] == 1) slot[u] = acc;
-            else ppart[p] = acc;
+        for (int u = 0; u < kUnroll; ++u) c[u] = (u < rem - kUnroll) ? __ldcs(col + q1 + static_cast<int64_t>(u) * kSlice) : 0;
+        switch (min(w - m0, kUnroll)) {
+        case 1: acc = slot_sums<1, AT>(v, xv, rem, acc); break;
+        case 2: acc = slot_sums<2, AT>(v, xv, rem, acc); break;
+        case 3: acc = slot_sums<3, AT>(v, xv, rem, acc); break;
+        case 4: acc = slot_sums<4, AT>(v, xv, rem, acc); break;
+        case 5: acc = slot_sums<5, AT>(v, xv, rem, acc); break;
+        case 6: acc = slot_sums<6, AT>(v, xv, rem, acc); break;
+        case 7: acc = slot_sums<7, AT>(v, xv, rem, acc); break;
+        default: acc = slot_sums<8, AT>(v, xv, rem, acc); break;
         }
     }
-    __syncthreads();
-    for (int u = tid; u < nrc; u += P) {   // rows of several pieces, in piece order
-        const int q0 = pstart[u], q1 = pstart[u + 1];
-        if (q1 - q0 > 1) {
-            AT t = ppart[q0];
-            for (int q = q0 + 1; q < q1; ++q) t += ppart[q];
-            slot[u] = t;
-        }
+    return acc;
+}
+
+// Block b of long-row pieces: long slices [b lsb, (b+1) lsb),
+// one per warp in turn; the sum of piece p goes to lpart[p].  Power-law rows
+// (R-MAT rows reach 65k entries) thus spread over many lanes of many blocks,
+// while a lane's sum stays a plain sequential one.  Not inlined: the tile
+// path keeps its own register allocation.
+template <typename VT, typename XT, typename AT>
+__device__ __noinline__ void long_pieces_block(const SpmvArgs<VT, XT, AT> &a, int b, const XT *__restrict__ xop) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int s1 = min((b + 1) * a.lsb, a.nls);
+    for (int s = b * a.lsb + warp; s < s1; s += nw) {
+        const int e0 = __ldg(a.ls_ent + s);
+        const int w = (__ldg(a.ls_ent + s + 1) - e0) / kSlice;
+        const int64_t p = static_cast<int64_t>(s) * kSlice + lane;
+        const int len = __ldg(a.ls_len + p);
+        a.lpart[p] = piece_sum<VT, XT, AT>(a.lval, a.lcol, static_cast<int64_t>(e0) + lane, len, w, xop);
     }
 }
 
@@ -838,11 +790,11 @@ constexpr int tile_min_blocks() { return sizeof(AT) == 8 ? 2 : 3; }
 template <typename VT, typename XT, typename AT>
 __global__ void __launch_bounds__(kBlock, tile_min_blocks<AT>()) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (static_cast<int>(blockIdx.x) < a.ntiles) {
-        EpiSpmv<XT, AT> epi{a.alpha, a.y};
-        tile_block<VT, XT, AT>(a, blockIdx.x, smem, a.x, epi);
+    if (static_cast<int>(blockIdx.x) < a.nlb) {
+        long_pieces_block<VT, XT, AT>(a, blockIdx.x, a.x);
     } else {
-        long_block<VT, XT, AT>(a, blockIdx.x - a.ntiles, smem, a.x);
+        EpiSpmv<XT, AT> epi{a.alpha, a.y};
+        tile_block<VT, XT, AT>(a, blockIdx.x - a.nlb, smem, a.x, epi);
     }
 }
 
@@ -872,8 +824,8 @@ __global__ void __launch_bounds__(kBlock, 2) tile_kernel_mrs(const SpmvArgs<VT, 
     }
     const XT *xop = nullptr;
     EpiMrs<XT, AT, S> epi = make_mrs_epi<XT, AT, S>(m.st, m.w, m.p, m.xsol, m.fold_bits, m.part, &xop);
-    if (static_cast<int>(blockIdx.x) < a.ntiles) tile_block<VT, XT, AT>(a, blockIdx.x, smem, xop, epi);
-    else long_block<VT, XT, AT>(a, blockIdx.x - a.ntiles, smem, xop);
+    if (static_cast<int>(blockIdx.x) < a.nlb) long_pieces_block<VT, XT, AT>(a, blockIdx.x, xop);
+    else tile_block<VT, XT, AT>(a, blockIdx.x - a.nlb, smem, xop, epi);
     if constexpr (FUSED) {
         __shared__ double red[32];
         double tot = 0.0;
@@ -882,15 +834,24 @@ __global__ void __launch_bounds__(kBlock, 2) tile_kernel_mrs(const SpmvArgs<VT, 
     }
 }
 
+// Piece sums of long row l in the row's entry order: its full pieces, then
+// its shorter last piece.
+template <typename AT>
+__device__ __forceinline__ AT long_row_sum(int l, const int32_t *__restrict__ lp0, const int32_t *__restrict__ lrem,
+                                           const AT *__restrict__ lpart, int64_t k, int c, AT v) {
+    for (int p = lp0[l]; p < lp0[l + 1]; ++p) v += lpart[static_cast<int64_t>(p) * k + c];
+    const int r = lrem[l];
+    if (r >= 0) v += lpart[static_cast<int64_t>(r) * k + c];
+    return v;
+}
+
 // One thread per receiving row: y[row] += halo sum, then the row's long-row
-// partial sums in chunk order.
+// piece sums in order.
 template <typename XT, typename AT>
 __global__ void __launch_bounds__(256) fold_kernel(int nitems, const int32_t *__restrict__ frow,
                                                    const int32_t *__restrict__ fhalo,
                                                    const int32_t *__restrict__ flong, const AT *__restrict__ halo,
-                                                   const int32_t *__restrict__ lc0, const int32_t *__restrict__ lc1,
-                                                   const int32_t *__restrict__ lcfirst,
-                                                   const int32_t *__restrict__ lcslot,
+                                                   const int32_t *__restrict__ lp0, const int32_t *__restrict__ lrem,
                                                    const AT *__restrict__ lpart, XT *__restrict__ y) {
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nitems; f += gridDim.x * blockDim.x) {
         const int r = frow[f];
@@ -898,10 +859,51 @@ __global__ void __launch_bounds__(256) fold_kernel(int nitems, const int32_t *__
         const int hi = fhalo[f];
         if (hi >= 0) v += halo[hi];
         const int l = flong[f];
-        if (l >= 0)
-            for (int c = lc0[l]; c <= lc1[l]; ++c) v += lpart[lcslot[c] + (l - lcfirst[c])];
+        if (l >= 0) v = long_row_sum<AT>(l, lp0, lrem, lpart, 1, 0, v);
         y[r] = static_cast<XT>(v);
     }
+}
+
+// Kernel arguments of handle h for precision dtype (values of that
+// precision; x, y, alpha and the scratch are set by the caller).
+template <typename VT, typename XT, typename AT>
+SpmvArgs<VT, XT, AT> make_spmv_args(const pars3_handle *h, int dtype) {
+    const Layout &L = h->L;
+    const DevLayout &D = h->D;
+    SpmvArgs<VT, XT, AT> a;
+    a.n = h->n;
+    a.T = h->T;
+    a.W = h->W;
+    a.ntiles = h->ntiles;
+    a.Mh = static_cast<int32_t>(round_up(L.max_tile_half, kAlignHalf));
+    a.nls = L.nls();
+    a.nlb = L.nlong_blocks();
+    a.lsb = L.ls_per_block;
+    a.hoff = D.hoff;
+    a.hcnt = D.hcnt;
+    a.hrp = D.hrp;
+    a.hcol = D.hcol;
+    a.hcperm = D.hcperm;
+    a.hval = static_cast<const VT *>(D.hval[dtype]);
+    a.hhoff = D.hhoff;
+    a.hhrow = D.hhrow;
+    a.halo = static_cast<AT *>(D.halo);
+    a.sl_off = D.sl_off;
+    a.sl_ent = D.sl_ent;
+    a.sl_meta = D.sl_meta;
+    a.fcol = D.fcol;
+    a.fval = static_cast<const VT *>(D.fval[dtype]);
+    a.ls_ent = D.ls_ent;
+    a.ls_len = D.ls_len;
+    a.lcol = D.lcol;
+    a.lval = static_cast<const VT *>(D.lval[dtype]);
+    a.lpart = static_cast<AT *>(D.lpart);
+    a.x = nullptr;
+    a.y = nullptr;
+    a.alpha = AT(0);
+    a.err = D.err;
+    a.sym = h->symmetric;
+    return a;
 }
 
 template <typename T>

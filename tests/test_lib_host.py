@@ -118,24 +118,33 @@ def test_layout_routes_long_rows_and_full_tiles():
     perm, _, _ = P.pars3_reorder(A.n, A.rowptr, A.col)
     h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=256, W=256, long_row=64)
     info = P.pars3_info_get(h)
-    assert info["long_rows"] > 0 and info["long_chunks"] >= 1
+    assert info["long_rows"] > 0 and info["long_pieces"] >= 1
     assert info["half_entries"] + (info["full_entries"] + info["long_entries"]) // 2 == A.nnz
     assert P.pars3_layout_check(h) == 0
 
 
-@pytest.mark.parametrize("T,long_row", [(32, 1), (256, 2), (4096, 2), (1024, 128)])
-def test_long_row_chunks_cover_every_long_entry(T, long_row):
-    """Chunks of the long-row list: at most 4096 entries and T rows each, every
-    long row with at least one entry, the long rows' entries reconstructing
-    the split (pars3_layout_check), for chunks of one row up to thousands."""
+@pytest.mark.parametrize("T,long_row,piece", [(32, 1, 0), (256, 2, 8), (4096, 2, 0), (1024, 128, 255), (512, 3, 9)])
+def test_long_row_pieces_cover_every_long_entry(T, long_row, piece):
+    """Pieces of the long rows: every long row with at least one entry, all
+    of its pieces but the last of the full length, each piece once in the
+    long slices, the long rows' entries reconstructing the split
+    (pars3_layout_check)."""
     A = W.grid((120, 110), "normal", 17)
     perm, _, _ = P.pars3_reorder(A.n, A.rowptr, A.col)
-    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=32, long_row=long_row)
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=32, long_row=long_row, piece=piece)
     info = P.pars3_info_get(h)
     assert info["half_entries"] + (info["full_entries"] + info["long_entries"]) // 2 == A.nnz
     if long_row < 4:
-        assert info["long_rows"] > A.n // 2 and info["long_chunks"] >= info["long_entries"] // 4096
+        assert info["long_rows"] > A.n // 2 and info["long_pieces"] >= info["long_rows"]
     assert P.pars3_layout_check(h) == 0
+
+
+def test_piece_length_range():
+    A = W.grid((30, 20), "uniform", 6)
+    for bad in (-1, 1, 7, 256):
+        with pytest.raises(P.Pars3Error) as e:
+            P.pars3_split(A.n, A.rowptr, A.col, A.val, None, T=32, W=32, piece=bad)
+        assert e.value.code == P.EINVAL
 
 
 def test_overfull_tile_leaves_the_half_path():

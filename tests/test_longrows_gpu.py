@@ -1,12 +1,14 @@
 """GPU parity of the long-row path on the shapes that stress it.
 
-Long rows are cut into pieces of at most 128 entries, each summed by a group
-of eight lanes; the pieces of one row are added in piece order.  Two shapes:
-- one row longer than several 4096-entry chunks (a hub vertex joined to every
-  vertex of a 2D grid), so that whole chunks lie inside one row;
-- chunks holding about a thousand short rows (every row with more than two
-  full-storage entries sent to the long list, tiles of 4096 rows), so that
-  the prefix of piece counts spans many warp-scan steps.
+Long rows are cut into pieces of `piece` entries (default 192) and a shorter
+last piece; each piece is one lane's sequential sum, laid out like the tile
+slices, and the fold adds a row's pieces in order.  Shapes:
+- one row of 14,400 entries (a hub vertex joined to every vertex of a 2D
+  grid): hundreds of pieces of one row, spread over many blocks;
+- thousands of short long rows (every row with more than two full-storage
+  entries sent to the long list): one piece per row, slices of 32 rows'
+  last pieces sorted by length;
+- piece lengths from 8 to 255 on the hub row and on an R-MAT graph.
 Tolerances as in test_spmv_gpu: |y - y_ref| <= tau * (|alpha||x_i| +
 sum_j |s_ij||x_j|), tau = 1e-12 (fp64) and 2e-6 (fp32).  Two calls on the
 same input must agree bit for bit, and the SpMM path must match column by
@@ -71,14 +73,14 @@ def check_against_oracle(A, h, perm, dtype, alpha, x):
 
 
 @pytest.mark.parametrize("dtype", [P.F64, P.F32])
-def test_row_spanning_several_chunks(dtype):
+def test_row_of_hundreds_of_pieces(dtype):
     A = hub_plus_grid(120, 5)
     perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
     h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=1024, W=32,
                       dtypes=P.dtype_bit(P.F64) | P.dtype_bit(P.F32))
     P.pars3_upload(h)
     info = P.pars3_info_get(h)
-    assert info["long_rows"] >= 1 and info["long_chunks"] >= 4   # 14,400 entries in one row
+    assert info["long_rows"] >= 1 and info["long_pieces"] >= 14400 // 192   # 14,400 entries in one row
     assert P.pars3_layout_check(h) == 0
     for alpha, seed in ((0.5, 1), (0.0, 2)):
         x = W.vector("uniform", A.n, seed)
@@ -89,16 +91,16 @@ def test_row_spanning_several_chunks(dtype):
 
 
 @pytest.mark.parametrize("dtype", [P.F64, P.F32])
-def test_chunks_of_many_short_rows(dtype):
+def test_many_short_long_rows(dtype):
     A = W.grid((150, 150), "normal", 7)
     perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
     h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=4096, W=32, long_row=2,
                       dtypes=P.dtype_bit(P.F64) | P.dtype_bit(P.F32))
     P.pars3_upload(h)
     info = P.pars3_info_get(h)
-    # most rows hold four entries: chunks of 4096 entries touch about a thousand rows
+    # most rows hold four entries: one piece per long row
     assert info["long_rows"] > 15000
-    assert info["long_rows"] / info["long_chunks"] > 500
+    assert info["long_pieces"] == info["long_rows"]
     assert P.pars3_layout_check(h) == 0
     x = W.vector("uniform", A.n, 3)
     y1 = check_against_oracle(A, h, perm, dtype, 0.25, x)
@@ -107,12 +109,12 @@ def test_chunks_of_many_short_rows(dtype):
     h.close()
 
 
-def test_spmm_on_a_row_spanning_several_chunks():
+def test_spmm_on_a_row_of_many_pieces():
     A = hub_plus_grid(100, 9)
     perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
     h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=512, W=32, dtypes=P.dtype_bit(P.F32))
     P.pars3_upload(h)
-    assert P.pars3_info_get(h)["long_chunks"] >= 2
+    assert P.pars3_info_get(h)["long_pieces"] >= 2
     k = 4
     X = W.vector("uniform", (A.n, k), 4)
     Y = product(h, P.F32, 0.5, X[perm], k=k)
@@ -122,3 +124,31 @@ def test_spmm_on_a_row_spanning_several_chunks():
         bound = F.abs_bound(0.5, X[:, c])[perm]
         assert np.all(np.abs(Y[:, c] - ref) <= TAU[P.F32] * bound + 1e-30), c
     h.close()
+
+
+@pytest.mark.parametrize("piece", [8, 37, 255])
+@pytest.mark.parametrize("dtype", [P.F64, P.F32])
+def test_piece_lengths(piece, dtype):
+    """Pieces from 8 to 255 entries: the hub row and an R-MAT graph (power-law
+    rows, several rows of many pieces, remainders of every length)."""
+    for A in (hub_plus_grid(60, 3), W.rmat(13, 60000, seed=10)):
+        perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
+        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=512, W=32, long_row=32, piece=piece,
+                          dtypes=P.dtype_bit(P.F64) | P.dtype_bit(P.F32))
+        P.pars3_upload(h)
+        info = P.pars3_info_get(h)
+        assert info["long_rows"] >= 1 and info["long_pieces"] >= info["long_entries"] // piece
+        assert P.pars3_layout_check(h) == 0
+        x = W.vector("uniform", A.n, piece)
+        y1 = check_against_oracle(A, h, perm, dtype, 0.5, x)
+        y2 = product(h, dtype, 0.5, x[perm])
+        assert np.array_equal(y1, y2)
+        k = 4
+        X = W.vector("uniform", (A.n, k), piece + 1)
+        Y = product(h, dtype, 0.5, X[perm], k=k)
+        F = O.Full(A)
+        for c in range(k):
+            ref = F.apply(0.5, X[:, c])[perm]
+            bound = F.abs_bound(0.5, X[:, c])[perm]
+            assert np.all(np.abs(Y[:, c] - ref) <= TAU[dtype] * bound + 1e-30), c
+        h.close()
