@@ -92,7 +92,8 @@ typedef struct {
                            summed separately and added in order by the fold (0 = default 128, at most 128) */
     int32_t flags;      /* 0 (skew-symmetric) or PARS3_SPLIT_SYMMETRIC */
     int32_t piece;      /* entries per piece of a long row (0 = default 192; 8 <= piece <= 255) */
-    int32_t reserved[2];
+    int32_t long_slices;/* 32-piece slices of long rows per thread block (0 = default 32; at most 1024) */
+    int32_t reserved[1];
 } pars3_split_params;
 
 /* Read-only view of a handle's canonical split (host memory owned by the

@@ -80,6 +80,7 @@ static int upload_impl(pars3_handle *h, cudaStream_t st) {
     UP(D.hhrow, L.hhrow);
     UP(D.sl_off, L.sl_off);
     UP(D.sl_ent, L.sl_ent);
+    UP(D.sl_e, L.sl_e);
     UP(D.sl_meta, L.sl_meta);
     UP(D.fcol, L.fcol);
     UP(D.lp0, L.lp0);

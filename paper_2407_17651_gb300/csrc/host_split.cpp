@@ -364,6 +364,7 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
     };
     L.sl_off.assign(static_cast<size_t>(nt) + 1, 0);
     L.sl_ent.assign(1, 0);
+    L.sl_e.clear();
     std::vector<std::vector<int32_t>> tile_rows(1);
     {
         std::vector<int32_t> rows;
@@ -392,6 +393,9 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
                 tile_ent += static_cast<int64_t>(kSlice) * width;
             }
             L.sl_off[t + 1] = static_cast<int32_t>(L.sl_ent.size() - 1);
+            int32_t se = L.sl_off[t + 1];
+            while (se > L.sl_off[t] && L.sl_ent[se] == L.sl_ent[se - 1]) --se;
+            L.sl_e.push_back(se);
             L.max_tile_full = static_cast<int32_t>(std::max<int64_t>(L.max_tile_full, tile_ent));
             L.max_tile_slices = std::max(L.max_tile_slices, L.sl_off[t + 1] - L.sl_off[t]);
         }
@@ -593,6 +597,7 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
     if ((prm.T == 0) != (prm.W == 0)) return PARS3_EINVAL;
     if (prm.long_row < 0 || prm.piece < 0 || (prm.piece > 0 && (prm.piece < 8 || prm.piece > kPieceMax)))
         return PARS3_EINVAL;
+    if (prm.long_slices < 0 || prm.long_slices > 1024) return PARS3_EINVAL;
     pars3_handle *h = nullptr;
     try {
         h = new pars3_handle();
@@ -627,7 +632,7 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
         h->ntiles = n > 0 ? (n + prm.T - 1) / prm.T : 0;
         h->long_row = prm.long_row > 0 ? prm.long_row : 0;
         h->piece = prm.piece;
-        h->lsb = prm.reserved[0] > 0 ? std::min<int32_t>(prm.reserved[0], 1024) : 0;
+        h->lsb = prm.long_slices;
         canonical_reorder(h, rowptr, col, val);
         canonical_classify(h);
         rc = build_layout(h);
@@ -746,6 +751,10 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
             }
             for (int32_t rl = 0; rl < r1 - r0; ++rl)
                 if (!seen[rl]) return PARS3_EINVAL;   // every row owns a lane
+            // slices from sl_e[t] on, and only those, have width 0
+            if (L.sl_e[t] < L.sl_off[t] || L.sl_e[t] > L.sl_off[t + 1]) return PARS3_EINVAL;
+            for (int32_t s2 = L.sl_off[t]; s2 < L.sl_off[t + 1]; ++s2)
+                if ((L.sl_ent[s2 + 1] == L.sl_ent[s2]) != (s2 >= L.sl_e[t])) return PARS3_EINVAL;
         }
         // long rows: every piece of row l (its full pieces, then its last
         // piece) lies in the long slices with its length; together they hold

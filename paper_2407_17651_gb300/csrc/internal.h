@@ -45,6 +45,8 @@ struct Layout {
     std::vector<int32_t> sl_ent;    // [nslices+1]
     std::vector<uint32_t> sl_meta;  // [nslices*32]
     std::vector<int32_t> fcol;
+    std::vector<int32_t> sl_e;      // [ntiles] first slice of tile t whose rows are all empty (width 0);
+                                    // slices sl_e[t] .. sl_off[t+1]-1 hold the rows without full entries
     // long rows: long row l is global row lrow[l]; its full-storage entries
     // (in the order of a tile row: lower entries, then mirrored ones), lrp[l]
     // .. lrp[l+1]-1 of the concatenated list (host only), are cut into pieces
@@ -82,7 +84,7 @@ struct DevLayout {
     int32_t *hoff = nullptr, *hcnt = nullptr;
     uint16_t *hrp = nullptr, *hcol = nullptr, *hcperm = nullptr;
     int32_t *hhoff = nullptr, *hhrow = nullptr;
-    int32_t *sl_off = nullptr, *sl_ent = nullptr;
+    int32_t *sl_off = nullptr, *sl_ent = nullptr, *sl_e = nullptr;
     uint32_t *sl_meta = nullptr;
     int32_t *fcol = nullptr;
     int32_t *lp0 = nullptr, *lrem = nullptr, *ls_ent = nullptr;

@@ -48,7 +48,7 @@ struct SpmvArgs {
     const VT *hval;
     const int32_t *hhoff, *hhrow;
     AT *halo;
-    const int32_t *sl_off, *sl_ent;
+    const int32_t *sl_off, *sl_ent, *sl_e;
     const uint32_t *sl_meta;
     const int32_t *fcol;
     const VT *fval;
@@ -612,23 +612,38 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     if constexpr (Epi::kStage) epi.stage_tail(r0, nr, smem + align128(L.total), tid, P);
     __syncthreads();   // the barrier is initialised before anyone waits on it
 
-    // 1. full pass (sliced ELL) while the copy runs
+    const int se = a.sl_e[t];
+    // rows without full-path entries (the slices se .. s1-1, width 0: on a
+    // power-law graph most rows of a tile): their start value, by all
+    // threads at once with coalesced metadata loads, instead of a warp per
+    // slice
+    for (int q = tid; q < (s1 - se) * kSlice; q += P) {
+        const uint32_t meta = __ldg(a.sl_meta + static_cast<int64_t>(se) * kSlice + q);
+        const int rl = static_cast<int>(meta & 0xffffu);
+        if (rl != 0xffff) {
+            const AT v0 = epi.start(xop, r0 + rl);
+            if (direct) epi.finish(r0 + rl, v0);
+            else rowacc[rl] = v0;
+        }
+    }
+    // 1. full pass (sliced ELL) while the copy runs, over the slices that
+    // hold entries (s0 .. se-1)
     if constexpr (sizeof(AT) == 8 && Epi::kPipelined) {
-        full_pass_pipelined<VT, XT, AT, Epi>(a.sl_ent, a.sl_meta, a.fval, a.fcol, s0 + warp, s1, nwarps, r0, xop,
+        full_pass_pipelined<VT, XT, AT, Epi>(a.sl_ent, a.sl_meta, a.fval, a.fcol, s0 + warp, se, nwarps, r0, xop,
                                              epi, rowacc, direct);
     } else {
         // the next slice's metadata is fetched while the current one runs
         int s = s0 + warp;
         uint32_t meta_n = 0u;
         int ent_n = 0;
-        if (s < s1) {
+        if (s < se) {
             meta_n = __ldg(a.sl_meta + static_cast<int64_t>(s) * kSlice + lane);
             ent_n = __ldg(a.sl_ent + s);
         }
-        for (; s < s1; s += nwarps) {
+        for (; s < se; s += nwarps) {
             const uint32_t meta = meta_n;
             const int ent = ent_n;
-            if (s + nwarps < s1) {
+            if (s + nwarps < se) {
                 meta_n = __ldg(a.sl_meta + static_cast<int64_t>(s + nwarps) * kSlice + lane);
                 ent_n = __ldg(a.sl_ent + s + nwarps);
             }
@@ -890,6 +905,7 @@ SpmvArgs<VT, XT, AT> make_spmv_args(const pars3_handle *h, int dtype) {
     a.halo = static_cast<AT *>(D.halo);
     a.sl_off = D.sl_off;
     a.sl_ent = D.sl_ent;
+    a.sl_e = D.sl_e;
     a.sl_meta = D.sl_meta;
     a.fcol = D.fcol;
     a.fval = static_cast<const VT *>(D.fval[dtype]);

@@ -36,7 +36,8 @@ class Pars3Error(RuntimeError):
 
 class pars3_split_params(C.Structure):
     _fields_ = [("T", C.c_int32), ("W", C.c_int32), ("dtypes", C.c_int32), ("long_row", C.c_int32),
-                ("flags", C.c_int32), ("piece", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("flags", C.c_int32), ("piece", C.c_int32), ("long_slices", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class pars3_canonical(C.Structure):
@@ -222,13 +223,13 @@ class Handle:
 
 
 def pars3_split(n: int, rowptr, col, val, perm=None, T: int = 0, W: int = 0, dtypes: int = 0,
-                long_row: int = 0, symmetric: bool = False, piece: int = 0) -> Handle:
+                long_row: int = 0, symmetric: bool = False, piece: int = 0, long_slices: int = 0) -> Handle:
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     ci = np.ascontiguousarray(col, dtype=np.int32)
     v = np.ascontiguousarray(val, dtype=np.float64)
     pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
     prm = pars3_split_params(T=T, W=W, dtypes=dtypes, long_row=long_row,
-                             flags=SPLIT_SYMMETRIC if symmetric else 0, piece=piece)
+                             flags=SPLIT_SYMMETRIC if symmetric else 0, piece=piece, long_slices=long_slices)
     out = C.c_void_p()
     _chk(lib().pars3_split(int(n), _p(rp), _p(ci), _p(v), None if pm is None else _p(pm), C.byref(prm),
                            C.byref(out)), "pars3_split")

@@ -139,12 +139,19 @@ def test_long_row_pieces_cover_every_long_entry(T, long_row, piece):
     assert P.pars3_layout_check(h) == 0
 
 
-def test_piece_length_range():
+def test_piece_length_and_long_slices_range():
     A = W.grid((30, 20), "uniform", 6)
     for bad in (-1, 1, 7, 256):
         with pytest.raises(P.Pars3Error) as e:
             P.pars3_split(A.n, A.rowptr, A.col, A.val, None, T=32, W=32, piece=bad)
         assert e.value.code == P.EINVAL
+    for bad in (-1, 1025):
+        with pytest.raises(P.Pars3Error) as e:
+            P.pars3_split(A.n, A.rowptr, A.col, A.val, None, T=32, W=32, long_slices=bad)
+        assert e.value.code == P.EINVAL
+    for good in (1, 16, 1024):
+        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, None, T=32, W=32, long_row=2, long_slices=good)
+        assert P.pars3_layout_check(h) == 0
 
 
 def test_overfull_tile_leaves_the_half_path():

@@ -33,8 +33,22 @@ def _handle(A, **kw):
     return h, perm
 
 
+def grid_with_hub(a: int, every: int, seed: int):
+    """a x a 5-point grid plus a hub vertex joined to every `every`-th grid
+    vertex: a banded part with cross-tile middle entries (halo sums) and one
+    long row (piece sums), the two kinds of scratch."""
+    u, v = W.grid_edges((a, a))
+    n = a * a + 1
+    hub = n - 1
+    spokes = np.arange(0, a * a, every, dtype=np.int64)
+    u = np.concatenate([np.asarray(u, np.int64), np.full(spokes.size, hub, np.int64)])
+    v = np.concatenate([np.asarray(v, np.int64), spokes])
+    keys = np.unique(np.maximum(u, v) * n + np.minimum(u, v))
+    return W.from_keys(n, keys, "normal", seed, name=f"grid{a}_hub")
+
+
 @pytest.mark.parametrize("name,gen,kw", [
-    ("rmat_long_rows_and_halo", lambda: W.rmat(13, 60000, seed=10), {"T": 256, "W": 256, "long_row": 64}),
+    ("grid_hub_long_rows_and_halo", lambda: grid_with_hub(100, 7, 10), {"T": 256, "W": 128, "long_row": 64}),
     ("band_halo", lambda: W.banded_skew(20000, 100, 0.3, 3), {"T": 256, "W": 128}),
 ])
 def test_noalloc_matches_oracle_on_two_calls(name, gen, kw):
@@ -42,6 +56,8 @@ def test_noalloc_matches_oracle_on_two_calls(name, gen, kw):
     h, perm = _handle(A, **kw)
     info = P.pars3_info_get(h)
     assert info["halo_targets"] > 0
+    if name.startswith("grid_hub"):
+        assert info["long_rows"] > 0 and info["long_pieces"] > 1
     F = O.Full(A)
     for dtype in (P.F64, P.F32):
         vt = torch.float64 if dtype == P.F64 else torch.float32
