@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 skew SpMV (and the MRS solver) -- one JSON line.
 
-Workload (default): the 3D 7-point grid 128^3 with 1% random long-range
-edges (n = 2,097,152, 6,304,727 stored lower entries), values N(0,1),
-alpha = 0.5, x ~ U(-1,1); one reorder + split, then a step = 200 repeated
-y = (alpha I + S) x through pars3_spmv, inputs resident in HBM.  Metric:
-effective skew-SpMV GB/s = algorithmic bytes (half storage:
-nnz*(value+4) + (n+1)*4 + 2*n*vector bytes) per product / time.
+Workload (default): the largest configuration, an R-MAT graph of scale 22
+(n = 4,194,304, 20,000,000 stored lower entries, power-law degrees), values
+U(-1,1), alpha = 0, x ~ N(0,1); one reorder + autotuned split, then a step
+= 200 repeated y = (alpha I + S) x through pars3_spmv, inputs resident in
+HBM.  Metric: effective skew-SpMV GB/s = algorithmic bytes (half storage:
+nnz*(value+4) + (n+1)*4 + 2*n*vector bytes) per product / time.  The other
+workloads (the 128^3 + 1% grid, the band-friendly and finite-element-like
+matrices, the batched set) and the MRS comparison on the 128^3 + 1% matrix
+are reported in the same line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -199,19 +202,21 @@ def extra_section(args, peak):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     both = P.dtype_bit(P.F64) | P.dtype_bit(P.F32)
 
-    def single(name, A, alpha, x, desc, symmetric=False):
-        """Cut points autotuned separately for each precision."""
+    def single(name, A, alpha, x, desc, symmetric=False, precisions=("f64", "f32")):
+        """Split parameters autotuned separately for each precision."""
         t0 = time.perf_counter()
         perm, bw0, bw1 = P.pars3_reorder(A.n, A.rowptr, A.col)
         t_rcm = time.perf_counter() - t0
         row = {"workload": desc, "n": A.n, "nnz_stored": A.nnz, "alpha": alpha, "rcm_bandwidth": bw1,
                "rcm_s": t_rcm}
         for dt, nm, vt, sv, sx in ((P.F64, "f64", torch.float64, 8, 8), (P.F32, "f32", torch.float32, 4, 4)):
+            if nm not in precisions:
+                continue
             t0 = time.perf_counter()
-            tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=dt, k=1, dtypes=P.dtype_bit(dt))
+            tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=dt, k=1, dtypes=P.dtype_bit(dt),
+                                    symmetric=symmetric)
             t_tune = time.perf_counter() - t0
-            h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=tune["T"], W=tune["W"], dtypes=P.dtype_bit(dt),
-                              symmetric=symmetric)
+            h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, symmetric=symmetric, **P.split_kwargs(tune))
             P.pars3_upload(h)
             info = P.pars3_info_get(h)
             xp = torch.from_numpy(x[perm]).to("cuda", vt)
@@ -224,7 +229,7 @@ def extra_section(args, peak):
                        "layout_GBps": lb / us / 1e3, "GFLOPs": (4 * A.nnz + (2 * A.n if alpha else 0)) / us / 1e3,
                        "T": info["T"], "W": info["W"], "half_entries": info["half_entries"],
                        "full_entries": info["full_entries"], "long_entries": info["long_entries"],
-                       "autotune_s": t_tune}
+                       "split_params": P.split_kwargs(tune), "autotune_s": t_tune}
             h.close()
         out[name] = row
 
@@ -245,13 +250,18 @@ def extra_section(args, peak):
     out["fem_like"]["section_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     A, alpha, x = W.config1()
+    single("cfg1", A, alpha, x, "grid3d 128^3 + 1% random long-range edges, N(0,1), alpha=0.5")
+    out["cfg1"]["section_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
     single("cfg1_symmetric", A, alpha, x, "the 128^3 + 1% matrix as the symmetric S = L + L^T "
            "(PARS3_SPLIT_SYMMETRIC), alpha=0.5", symmetric=True)
     out["cfg1_symmetric"]["section_s"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    A, alpha, x = W.config2()
-    single("cfg2", A, alpha, x, "R-MAT scale 22, 20M stored, U(-1,1), alpha=0, cut points autotuned")
-    out["cfg2"]["section_s"] = time.perf_counter() - t0
+    if args.workload != "cfg2" or args.dtype != "f32":
+        t0 = time.perf_counter()
+        A, alpha, x = W.config2()
+        single("cfg2", A, alpha, x, "R-MAT scale 22, 20M stored, U(-1,1), alpha=0, split parameters autotuned",
+               precisions=("f32",) if args.workload == "cfg2" else ("f64", "f32"))
+        out["cfg2"]["section_s"] = time.perf_counter() - t0
     del A, x
 
     # batched uneven workload
@@ -262,9 +272,9 @@ def extra_section(args, peak):
         A = W.config4_matrix(m, shp)
         perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
         tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=P.F32, k=4, dtypes=both)
-        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=tune["T"], W=tune["W"], dtypes=both)
+        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, **P.split_kwargs(tune))
         P.pars3_upload(h)
-        hs.append(h); perms.append(perm); ns.append(A.n); nnzs.append(A.nnz); cuts.append((tune["T"], tune["W"]))
+        hs.append(h); perms.append(perm); ns.append(A.n); nnzs.append(A.nnz); cuts.append((tune["T"], tune["W"], tune["lane_bytes"]))
     t_prep = time.perf_counter() - t0
     rows = {}
     st = torch.cuda.current_stream()
@@ -299,7 +309,7 @@ def extra_section(args, peak):
     out["cfg4"] = {"workload": "64 uneven grids (n log-uniform in [1e4, 5e5], 2D/3D), N(0,1), alpha=1, "
                                "one persistent launch + fold per call, replayed from a CUDA graph",
                    "sum_n": sum(ns), "sum_nnz_stored": sum(nnzs), "prep_s": t_prep,
-                   "cut_points": sorted(set(cuts)), "results": rows,
+                   "cut_points_T_W_lane_bytes": sorted(set(cuts)), "results": rows,
                    "section_s": time.perf_counter() - t0}
     return out
 
@@ -397,7 +407,10 @@ def all_cores_baseline(F, alpha, x, unit_bytes: int, budget_s: float):
                       f"replicas ({el:.1f} s)"}
 
 
-def mrs_section(A, perm, T, Wc, alphas, budget_iters: int):
+MRS_CUT = (2048, 32)   # the cut the autotuner picks for the 128^3 + 1% matrix in fp64
+
+
+def mrs_section(alphas, budget_iters: int):
     """Configuration 3: (alpha I + S) x = b on the configuration-1 matrix,
     time to a true relative residual of 1e-10: plain fp64 MRS against an
     fp32 / bf16-value inner MRS inside fp64 refinement (wall time of one
@@ -406,6 +419,9 @@ def mrs_section(A, perm, T, Wc, alphas, budget_iters: int):
     import torch
     import workloads as W
     from paper_2407_17651_gb300 import pars3 as P
+    A, _, _ = W.config1()
+    perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
+    T, Wc = MRS_CUT
     h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=Wc,
                       dtypes=P.dtype_bit(P.F64) | P.dtype_bit(P.F32) | P.dtype_bit(P.BF16))
     P.pars3_upload(h)
@@ -438,15 +454,33 @@ def mrs_section(A, perm, T, Wc, alphas, budget_iters: int):
     return out
 
 
-def traffic_from_profile(kernel_hash: str, launch_units: float):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
+def mrs_summary(mrs):
+    """Seconds to a true relative residual of 1e-10 per alpha and precision,
+    and the mixed-precision speedups, compactly (kept at the end of the line)."""
+    if not mrs:
+        return None
+    out = {}
+    for a, row in mrs.items():
+        out[a] = {"fp64_s": round(row["fp64"]["time_s"], 5), "fp32_ir_s": round(row["fp32-ir"]["time_s"], 5),
+                  "bf16_ir_s": round(row["bf16-ir"]["time_s"], 5),
+                  "speedup_fp32_ir": row["fp32-ir"].get("speedup_vs_fp64"),
+                  "speedup_bf16_ir": row["bf16-ir"].get("speedup_vs_fp64"),
+                  "max_true_relres": max(row[k]["true_relres"] for k in ("fp64", "fp32-ir", "bf16-ir")),
+                  "all_converged": all(row[k]["converged"] for k in ("fp64", "fp32-ir", "bf16-ir"))}
+    return out
+
+
+def traffic_from_profile(key: str, kernel_hash: str, split_kw: dict):
+    """DRAM bytes per launch from the committed ncu summary of `key`, if it
+    was taken on the current kernel source with the same split parameters."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    ent = d.get("tile_kernel_f64_cfg1")
+    ent = d.get(key)
     if not ent or ent.get("source_hash") != kernel_hash:
+        return None
+    if ent.get("split_params") not in (None, split_kw):
         return None
     return float(ent["dram_bytes_per_launch"])
 
@@ -454,7 +488,8 @@ def traffic_from_profile(kernel_hash: str, launch_units: float):
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("spmv_kernels.cuh", "spmv.cu", "devcommon.cuh", "smem_layout.h", "host_split.cpp", "internal.h"):
+    for f in ("spmv_kernels.cuh", "spmv.cu", "devcommon.cuh", "smem_layout.h", "host_split.cpp", "internal.h",
+              "autotune.cu"):
         h.update(open(os.path.join(ROOT, "paper_2407_17651_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -465,7 +500,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg1")
+    ap.add_argument("--workload", default="cfg2")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--k", type=int, default=1, help="right-hand sides (k > 1 times pars3_spmm on an n x k block)")
     ap.add_argument("--T", type=int, default=-1, help="tile rows (default: pars3_autotune)")
@@ -502,15 +537,15 @@ def main():
     t_rcm = time.perf_counter() - t0
     t_tune = None
     if args.T >= 0:
-        T, Wc = args.T, args.W
-    else:   # cut points from the autotuner (untimed preprocessing)
+        split_kw = dict(T=args.T, W=args.W, dtypes=P.dtype_bit(dt))
+    else:   # split parameters from the autotuner (untimed preprocessing)
         t0 = time.perf_counter()
         tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=dt, k=max(1, args.k),
                                 dtypes=P.dtype_bit(dt))
         t_tune = time.perf_counter() - t0
-        T, Wc = tune["T"], tune["W"]
+        split_kw = P.split_kwargs(tune)
     t0 = time.perf_counter()
-    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=Wc, dtypes=P.dtype_bit(dt))
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, **split_kw)
     t_split = time.perf_counter() - t0
     t0 = time.perf_counter()
     P.pars3_upload(h)
@@ -585,7 +620,18 @@ def main():
     avg_spmv_s = tot_s_local / (REPEATS * args.steps)   # average product (launch) duration, timed region
     achieved = ub / avg_spmv_s / 1e9
     khash = kernel_source_hash()
-    traffic = traffic_from_profile(khash, 1.0) if (dt == P.F64 and args.workload == "cfg1" and k == 1) else None
+    traffic = traffic_from_profile(f"tile_kernel_{args.dtype}_{args.workload}", khash, split_kw) if k == 1 else None
+    # the fp64 products do one FMA per stored entry and direction: measure the
+    # device's fp64 FMA rate in the same run (a kernel of independent chains)
+    fp64 = None
+    if dt == P.F64:
+        rate = P.pars3_fp64_fma_rate()
+        fmas = (2 * A.nnz + (A.n if alpha else 0)) * k
+        fp64 = {"fma_per_launch": fmas, "achieved_fma_per_s": fmas / avg_spmv_s, "peak_fma_per_s": rate,
+                "frac": fmas / avg_spmv_s / rate if rate > 0 else None,
+                "floor_us": 1e6 * fmas / rate if rate > 0 else None,
+                "how": "2 FMA per stored entry (row sum and mirrored sum) plus alpha x; peak from "
+                       "pars3_fp64_fma_rate (independent FMA chains on every SM, CUDA events)"}
 
     # end to end through the host-buffer entry point (original numbering)
     e2e = None
@@ -605,8 +651,8 @@ def main():
 
     cpu = cpu_baseline(A, alpha, x, args.cpu_budget) if (rank == 0 and ws == 1) else None
     mrs = None
-    if args.mrs and args.workload == "cfg1" and k == 1:
-        mrs = mrs_section(A, perm, info["T"], info["W"], [float(a) for a in args.mrs.split(",")], args.mrs_iters)
+    if args.mrs and k == 1 and rank == 0:
+        mrs = mrs_section([float(a) for a in args.mrs.split(",")], args.mrs_iters)
     launches_per_spmv = 1 + (1 if info["halo_targets"] + info["long_rows"] > 0 else 0)
     extra = extra_section(args, peak) if (args.extra and rank == 0) else None
     if rank == 0:
@@ -635,7 +681,9 @@ def main():
                          # the DRAM bytes the profile counted, over the same average duration: how
                          # close the kernel's actual traffic runs to the copy ceiling
                          "traffic_GBps": traffic / avg_spmv_s / 1e9 if traffic else None,
-                         "traffic_frac": traffic / avg_spmv_s / 1e9 / peak if traffic else None},
+                         "traffic_frac": traffic / avg_spmv_s / 1e9 / peak if traffic else None,
+                         "hbm_floor_us": 1e6 * ub / (peak * 1e9),
+                         "fp64_pipe": fp64},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_spmv * REPEATS * args.steps,
@@ -649,6 +697,8 @@ def main():
                                             "how": "one extra untimed step with an event between every two "
                                                    "products"}},
             "kernel_source_hash": khash,
+            "split_params": split_kw,
+            "mrs_summary": mrs_summary(mrs),
         }
         print(json.dumps(line), flush=True)
     h.close()

@@ -76,6 +76,8 @@ extern "C" {
                                    paper's method also covers, abstract and Sec. 5) instead of the
                                    skew-symmetric S = L - L^T */
 
+#define PARS3_VARIANT_LOOKAHEAD 1 /* pars3_split_params.variant, see there */
+
 typedef struct pars3_handle pars3_handle;
 
 /* Split parameters (Sec. 3.1.2, Fig. 8: the middle/outer boundary is a
@@ -93,7 +95,11 @@ typedef struct {
     int32_t flags;      /* 0 (skew-symmetric) or PARS3_SPLIT_SYMMETRIC */
     int32_t piece;      /* entries per piece of a long row (0 = default 192; 8 <= piece <= 255) */
     int32_t long_slices;/* 32-piece slices of long rows per thread block (0 = default 32; at most 1024) */
-    int32_t reserved[1];
+    int32_t lane_bytes; /* pars3_spmm: bytes of X a lane holds per row, 4/8 (one element), 16 or 32
+                           (0 = rule: 32 when k >= 16 allows it, else 16 when k allows it, else one element) */
+    int32_t variant;    /* tile kernel: 0 = default; PARS3_VARIANT_LOOKAHEAD = fp32 / bf16 tiles load the next
+                           slice's columns ahead at two blocks per SM (fp64 tiles always do) */
+    int32_t reserved[3];
 } pars3_split_params;
 
 /* Read-only view of a handle's canonical split (host memory owned by the
@@ -284,13 +290,26 @@ int pars3_spmv_noalloc(const pars3_handle *h, int32_t dtype, double alpha, const
 int pars3_check(const pars3_handle *h, void *stream);
 
 /* pars3_autotune -- times pars3_spmm (k right-hand sides) on the current
- * device for candidate cut points (T, W) and returns the fastest in *best
- * (other fields copied from *base).  The matrix arguments are those of
- * pars3_split.  Leaves no device state behind.  Errors: as pars3_split and
- * pars3_upload. */
+ * device and returns the fastest split parameters in *best (fields not
+ * searched are copied from *base): the cut points (T, W) (coordinate search
+ * over powers of two), then, for matrices with long rows, the long-row
+ * threshold, piece length and long slices per block, then the tile kernel
+ * variant (fp32 / bf16, k = 1) or the lane width of the multi-vector
+ * product (k > 1).  The matrix arguments are those of pars3_split.  Leaves
+ * no device state behind.  Errors: as pars3_split and pars3_upload. */
 int pars3_autotune(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
                    const int32_t *perm, const pars3_split_params *base, int32_t dtype, int32_t k,
                    pars3_split_params *best, double *best_us);
+
+/* pars3_fp64_fma_rate -- measurement helper (the paper has no counterpart):
+ * the current device's fp64 fused multiply-add rate in FMAs per second, from
+ * a kernel of independent FMA chains on every SM (best of three timed runs
+ * after a warm-up, CUDA events on stream; synchronizes the stream).  The
+ * fp64 products read one value and do one FMA per stored entry, so on a part
+ * with a narrow fp64 unit this rate bounds them beside HBM bandwidth.
+ * Allocates and frees 8 bytes of device memory.  Errors: EINVAL (null
+ * pointer), ECUDA, ENOMEM. */
+int pars3_fp64_fma_rate(double *fma_per_s, void *stream);
 
 /* Release a handle (host and device memory).  NULL is ignored. */
 void pars3_free(pars3_handle *h);

@@ -1,21 +1,28 @@
-// autotune.cu -- pars3_autotune: choose the cut points (T, W) of the 3-way
-// split (Sec. 3.1.2: the tile a thread block owns and the middle bandwidth)
-// by timing pars3_spmm on the current device.
+// autotune.cu -- pars3_autotune: choose the split parameters by timing
+// pars3_spmm on the current device.  First the cut points (T, W) of the
+// 3-way split (Sec. 3.1.2: the tile a thread block owns and the middle
+// bandwidth), then the layout choices that are this implementation's own.
 //
-// The search is coordinate-wise over powers of two, so that a matrix is
-// split at most about ten times:
+// The search is coordinate-wise, so that a matrix is split at most about
+// fifteen times:
 //   1. W = 32, T in {512, 1024, 2048, 4096}            -> T1
 //   2. T = T1, W in {64, ..., min(T1, w_max)}          -> W2
-//   3. W = W2, T in {T1 / 2, 2 T1} not yet timed       -> best
+//   3. W = W2, T in {T1 / 2, 2 T1} not yet timed       -> (T, W)
+//   4. matrices with rows of more than 32 full-storage entries: the long-row
+//      threshold, piece length and long slices per block, from a short list
+//      of measured good settings (power-law rows want shorter tile rows and
+//      longer pieces);
+//   5. k = 1 with fp32 / bf16 values: the look-ahead tile kernel variant;
+//      k > 1: the other lane widths of the multi-vector product.
 // w_max is the reordered bandwidth rounded up to a power of two, capped like
 // the default rule (1024 with F64 packed, else 2048): a middle band wider
 // than the matrix's band holds no more entries.  A candidate replaces the
 // incumbent only when it is at least 2 % faster, so near-ties keep the
-// smaller band and the earlier tile size.  Candidates the layout cannot
-// hold (shared memory) are skipped.  The matrix is reordered and sorted
-// once; each candidate re-runs only the cut-dependent stages of the split,
-// is uploaded, timed (3 warm-up products, then the median of 3 groups of 8
-// products measured with CUDA events) and freed.
+// earlier (simpler) choice.  Candidates the layout cannot hold (shared
+// memory) are skipped.  The matrix is reordered and sorted once; each
+// candidate re-runs only the cut-dependent stages of the split, is uploaded,
+// timed (3 warm-up products, then the median of 3 groups of 8 products
+// measured with CUDA events) and freed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,10 +43,10 @@ struct Timer {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
 
     // microseconds per product, or +inf when the candidate cannot be laid out
-    int time(int32_t T, int32_t W, double *us) {
+    int time(const pars3_split_params &p, double *us) {
         *us = INFINITY;
         pars3_handle *h = nullptr;
-        int rc = split_recut(tmpl, T, W, &h);
+        int rc = split_recut(tmpl, p, &h);
         if (rc == PARS3_EUNSUPPORTED) return PARS3_OK;
         if (rc != PARS3_OK) return rc;
         rc = pars3_upload(h, st);
@@ -72,6 +79,18 @@ struct Timer {
     }
 };
 
+// longest row of the full-storage (both triangles) pattern
+int64_t max_full_row(const pars3_handle *h) {
+    std::vector<int32_t> deg(static_cast<size_t>(h->n), 0);
+    for (int32_t i = 0; i < h->n; ++i) {
+        deg[i] += h->rowptr[i + 1] - h->rowptr[i];
+        for (int32_t e = h->rowptr[i]; e < h->rowptr[i + 1]; ++e) ++deg[h->col[e]];
+    }
+    int64_t m = 0;
+    for (int32_t d : deg) m = std::max<int64_t>(m, d);
+    return m;
+}
+
 int32_t pow2_ceil(int64_t v) {
     int32_t p = 32;
     while (p < v && p < (1 << 15)) p <<= 1;
@@ -93,6 +112,9 @@ extern "C" int pars3_autotune(int32_t n, const int32_t *rowptr, const int32_t *c
     pars3_split_params b0{};
     if (base) b0 = *base;
     if (b0.dtypes == 0) b0.dtypes = PARS3_DTYPE_BIT(PARS3_F64);
+    if (check_layout_params(b0) != PARS3_OK) return PARS3_EINVAL;
+    // the long-row stage only searches when the caller left those settings at their defaults
+    const bool base_layout_default = b0.long_row == 0 && b0.piece == 0 && b0.long_slices == 0;
     b0.dtypes |= PARS3_DTYPE_BIT(dtype);
     *best = b0;
     if (best_us) *best_us = 0.0;
@@ -124,30 +146,71 @@ extern "C" int pars3_autotune(int32_t n, const int32_t *rowptr, const int32_t *c
     if (e == cudaSuccess) e = cudaEventCreate(&tm.e1);
     rc = cuda_status(e);
 
-    std::vector<std::pair<int32_t, int32_t>> tried;
-    int32_t bT = 0, bW = 0;
+    std::vector<pars3_split_params> tried;
+    pars3_split_params bp = b0;
+    bp.T = 0;
     double bus = INFINITY;
-    auto consider = [&](int32_t T, int32_t W) {
-        if (rc != PARS3_OK || W > T || T > 32768) return;
-        for (auto &c : tried)
-            if (c.first == T && c.second == W) return;
-        tried.emplace_back(T, W);
+    auto same = [](const pars3_split_params &x, const pars3_split_params &y) {
+        return x.T == y.T && x.W == y.W && x.long_row == y.long_row && x.piece == y.piece &&
+               x.long_slices == y.long_slices && x.lane_bytes == y.lane_bytes && x.variant == y.variant;
+    };
+    auto consider = [&](const pars3_split_params &c) {
+        if (rc != PARS3_OK || c.W > c.T || c.T > 32768) return;
+        for (auto &t : tried)
+            if (same(t, c)) return;
+        tried.push_back(c);
         double us;
-        rc = tm.time(T, W, &us);
+        rc = tm.time(c, &us);
         if (rc == PARS3_OK && us < 0.98 * bus) {
             bus = us;
-            bT = T;
-            bW = W;
+            bp = c;
         }
     };
-    for (int32_t T : {512, 1024, 2048, 4096}) consider(T, 32);
-    const int32_t T1 = bT;
+    auto cut = [&](int32_t T, int32_t W) {
+        pars3_split_params c = bp.T > 0 ? bp : b0;
+        c.T = T;
+        c.W = W;
+        consider(c);
+    };
+    for (int32_t T : {512, 1024, 2048, 4096}) cut(T, 32);
+    const int32_t T1 = bp.T;
     if (T1 > 0)
-        for (int32_t W = 64; W <= std::min(T1, wmax); W <<= 1) consider(T1, W);
+        for (int32_t W = 64; W <= std::min(T1, wmax); W <<= 1) cut(T1, W);
     if (T1 > 0) {
-        const int32_t W2 = bW;
-        consider(std::max(T1 / 2, W2), W2);
-        consider(T1 * 2, W2);
+        const int32_t W2 = bp.W;
+        cut(std::max(T1 / 2, W2), W2);
+        cut(T1 * 2, W2);
+    }
+    // 4. long rows: (threshold, piece, slices per block) against the incumbent's
+    // defaults (128, 192, 32)
+    if (bp.T > 0 && base_layout_default && max_full_row(tmpl) > 32) {
+        const int32_t T4 = bp.T;
+        struct L3 { int32_t long_row, piece, slices; };
+        for (const L3 &l : {L3{32, 255, 16}, L3{128, 255, 16}, L3{32, 192, 32}, L3{64, 128, 32}}) {
+            pars3_split_params c = bp;
+            c.long_row = l.long_row;
+            c.piece = l.piece;
+            c.long_slices = l.slices;
+            consider(c);
+        }
+        // shorter tiles with the chosen long-row settings
+        pars3_split_params c = bp;
+        c.T = std::max(T4 / 2, bp.W);
+        consider(c);
+    }
+    // 5. kernel variant (k = 1) or lane width (k > 1)
+    if (bp.T > 0 && k == 1 && dtype != PARS3_F64 && b0.variant == 0) {
+        pars3_split_params c = bp;
+        c.variant = PARS3_VARIANT_LOOKAHEAD;
+        consider(c);
+    }
+    if (bp.T > 0 && k > 1 && b0.lane_bytes == 0) {
+        const int32_t elem = dtype == PARS3_F64 ? 8 : 4;
+        for (int32_t lb : {32, 16, elem}) {
+            pars3_split_params c = bp;
+            c.lane_bytes = lb;
+            consider(c);
+        }
     }
 
     if (tm.e0) cudaEventDestroy(tm.e0);
@@ -157,9 +220,8 @@ extern "C" int pars3_autotune(int32_t n, const int32_t *rowptr, const int32_t *c
     if (tm.st) cudaStreamDestroy(tm.st);
     pars3_free(tmpl);
     if (rc != PARS3_OK) return rc;
-    if (bT == 0) return PARS3_EUNSUPPORTED;
-    best->T = bT;
-    best->W = bW;
+    if (bp.T == 0) return PARS3_EUNSUPPORTED;
+    *best = bp;
     if (best_us) *best_us = bus;
     return PARS3_OK;
 }

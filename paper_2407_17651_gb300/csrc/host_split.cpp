@@ -541,21 +541,40 @@ int64_t model_bytes(const pars3_handle *h, int dtype) {
 
 namespace pars3 {
 
+// Layout parameters of a split (everything but the cut points and the
+// packed precisions): PARS3_OK or PARS3_EINVAL.
+int check_layout_params(const pars3_split_params &p) {
+    if (p.long_row < 0 || p.piece < 0 || (p.piece > 0 && (p.piece < 8 || p.piece > kPieceMax))) return PARS3_EINVAL;
+    if (p.long_slices < 0 || p.long_slices > 1024) return PARS3_EINVAL;
+    if (!(p.lane_bytes == 0 || p.lane_bytes == 4 || p.lane_bytes == 8 || p.lane_bytes == 16 || p.lane_bytes == 32))
+        return PARS3_EINVAL;
+    if (p.variant != 0 && p.variant != PARS3_VARIANT_LOOKAHEAD) return PARS3_EINVAL;
+    return PARS3_OK;
+}
+
+static void set_layout_params(pars3_handle *h, const pars3_split_params &p) {
+    h->long_row = p.long_row > 0 ? p.long_row : 0;
+    h->piece = p.piece;
+    h->lsb = p.long_slices;
+    h->lane_bytes = p.lane_bytes;
+    h->variant = p.variant;
+}
+
 // A handle with the same reordered matrix as src (perm, band CSR, packed
-// precisions, long-row threshold) and the cut points (T, W): only the
-// cut-dependent stages run.  Used by the autotuner.
-int split_recut(const pars3_handle *src, int32_t T, int32_t W, pars3_handle **out) {
+// precisions, mirror sign) and the cut points and layout parameters of p:
+// only the cut-dependent stages run.  Used by the autotuner.
+int split_recut(const pars3_handle *src, const pars3_split_params &p, pars3_handle **out) {
     *out = nullptr;
+    const int32_t T = p.T, W = p.W;
     if (!is_pow2(T) || !is_pow2(W) || W < 32 || W > T || T > 32768) return PARS3_EINVAL;
+    if (check_layout_params(p) != PARS3_OK) return PARS3_EINVAL;
     pars3_handle *h = nullptr;
     try {
         h = new pars3_handle();
         h->n = src->n;
         h->nnz = src->nnz;
         h->dtypes = src->dtypes;
-        h->long_row = src->long_row;
-        h->piece = src->piece;
-        h->lsb = src->lsb;
+        set_layout_params(h, p);
         h->symmetric = src->symmetric;
         h->perm = src->perm;
         h->rowptr = src->rowptr;
@@ -595,9 +614,7 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
     if (prm.dtypes & ~7) return PARS3_EINVAL;
     if (prm.flags & ~PARS3_SPLIT_SYMMETRIC) return PARS3_EINVAL;
     if ((prm.T == 0) != (prm.W == 0)) return PARS3_EINVAL;
-    if (prm.long_row < 0 || prm.piece < 0 || (prm.piece > 0 && (prm.piece < 8 || prm.piece > kPieceMax)))
-        return PARS3_EINVAL;
-    if (prm.long_slices < 0 || prm.long_slices > 1024) return PARS3_EINVAL;
+    if (check_layout_params(prm) != PARS3_OK) return PARS3_EINVAL;
     pars3_handle *h = nullptr;
     try {
         h = new pars3_handle();
@@ -630,9 +647,7 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
         h->T = prm.T;
         h->W = prm.W;
         h->ntiles = n > 0 ? (n + prm.T - 1) / prm.T : 0;
-        h->long_row = prm.long_row > 0 ? prm.long_row : 0;
-        h->piece = prm.piece;
-        h->lsb = prm.long_slices;
+        set_layout_params(h, prm);
         canonical_reorder(h, rowptr, col, val);
         canonical_classify(h);
         rc = build_layout(h);

@@ -119,6 +119,8 @@ struct pars3_handle {
     int32_t long_row = 0;
     int32_t piece = 0;               // entries per long-row piece requested (0 = kPieceLen)
     int32_t lsb = 0;                 // long slices per block requested (0 = kLongSlices)
+    int32_t lane_bytes = 0;          // SpMM bytes of X per lane (0 = rule)
+    int32_t variant = 0;             // tile kernel variant (PARS3_VARIANT_*)
     int32_t symmetric = 0;           // S = L + L^T instead of L - L^T (mirror sign +1)
     int64_t bw = 0;
     // canonical split (host)
@@ -143,7 +145,8 @@ int validate_lower(int32_t n, const int32_t *rowptr, const int32_t *col);
 int64_t bandwidth(int32_t n, const int32_t *rowptr, const int32_t *col, const int32_t *pinv);
 
 // host_split.cpp
-int split_recut(const pars3_handle *src, int32_t T, int32_t W, pars3_handle **out);
+int split_recut(const pars3_handle *src, const pars3_split_params &p, pars3_handle **out);
+int check_layout_params(const pars3_split_params &p);
 // bit of the calling thread's current CUDA device (kernel attributes are set
 // once per device and kernel)
 uint64_t device_bit();

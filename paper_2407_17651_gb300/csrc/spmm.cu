@@ -111,7 +111,7 @@ static int launch_spmm_typed(const pars3_handle *h, int dtype, double alpha, int
                              void *halo, void *lpart, cudaStream_t st) {
     const bool aligned = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15u) == 0;
     constexpr int V = 16 / static_cast<int>(sizeof(XT));
-    const int nv = aligned ? spmm_nv<XT>(k) : 1;
+    const int nv = spmm_lane_elems<XT>(k, h->lane_bytes, aligned);
     if (nv == 2 * V) return launch_spmm_nv<VT, XT, AT, 2 * V>(h, dtype, alpha, k, X, Y, halo, lpart, st);
     if (nv == V) return launch_spmm_nv<VT, XT, AT, V>(h, dtype, alpha, k, X, Y, halo, lpart, st);
     return launch_spmm_nv<VT, XT, AT, 1>(h, dtype, alpha, k, X, Y, halo, lpart, st);

@@ -116,6 +116,19 @@ PARS3_HD int spmm_nv(int k) {
     return (k % v == 0) ? v : 1;
 }
 
+// elements per lane for a requested lane width (bytes; 0 = the rule above):
+// one element, a 16-byte vector or two of them, as far as k and the
+// alignment of X and Y allow
+template <typename XT>
+PARS3_HD int spmm_lane_elems(int k, int lane_bytes, bool aligned) {
+    if (!aligned) return 1;
+    const int v = 16 / static_cast<int>(sizeof(XT));
+    if (lane_bytes == 32 && k % (2 * v) == 0) return 2 * v;
+    if (lane_bytes == 16 && k % v == 0) return v;
+    if (lane_bytes > 0 && lane_bytes <= 8) return 1;
+    return spmm_nv<XT>(k);
+}
+
 // lanes per row (a power of two) for k columns held NV to a lane
 PARS3_HD int spmm_lpr(int k, int nv) {
     const int lanes = (k + nv - 1) / nv;

@@ -43,13 +43,29 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     static std::atomic<uint64_t> configured{0};   // one bit per device
     const uint64_t dbit = device_bit();
     if (!(configured.load() & dbit)) {
-        cudaError_t e = cudaFuncSetAttribute(tile_kernel<VT, XT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemLimit);
+        cudaError_t e = cudaFuncSetAttribute(tile_kernel<VT, XT, AT, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+        if constexpr (sizeof(AT) == 4) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(tile_kernel<VT, XT, AT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemLimit);
+        }
         if (e != cudaSuccess) return cuda_status(e);
         configured.fetch_or(dbit);
     }
     const int grid = a.nlb + h->ntiles;
-    if (grid > 0) tile_kernel<VT, XT, AT><<<grid, kBlock, smem, st>>>(a);
+    // fp32 / bf16 look-ahead variant: direct stores, nothing staged unless
+    // the tile has middle entries
+    const bool la = sizeof(AT) == 4 && h->variant == PARS3_VARIANT_LOOKAHEAD;
+    const int smem_la = L.max_tile_half > 0 ? smem : 0;
+    if (grid > 0) {
+        if constexpr (sizeof(AT) == 4) {
+            if (la) tile_kernel<VT, XT, AT, true><<<grid, kBlock, smem_la, st>>>(a);
+            else tile_kernel<VT, XT, AT, false><<<grid, kBlock, smem, st>>>(a);
+        } else {
+            tile_kernel<VT, XT, AT, false><<<grid, kBlock, smem, st>>>(a);
+        }
+    }
     const int nf = static_cast<int>(L.fold_row.size());
     if (nf > 0) {
         const int blocks = static_cast<int>(std::min<int64_t>((nf + 255) / 256, 8LL * sm_count()));

@@ -550,7 +550,10 @@ __device__ __forceinline__ void prefetch_slices(const SpmvArgs<VT, XT, AT> &a, i
     bulk_prefetch_l2(a.sl_meta + static_cast<int64_t>(s0) * kSlice, static_cast<uint64_t>(s1 - s0) * kSlice * 4u);
 }
 
-template <typename VT, typename XT, typename AT, class Epi>
+// LA: fp32 / bf16 tiles use the fp64 tiles' look-ahead full pass and
+// direct stores (the kernel variant compiled for two blocks per SM, whose
+// registers hold them)
+template <typename VT, typename XT, typename AT, class Epi, bool LA = false>
 __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t, unsigned char *smem,
                                            const XT *__restrict__ xop, Epi &epi) {
     const SmemLayout L = smem_layout(a.T, a.W, a.Mh, sizeof(VT), sizeof(XT), sizeof(AT));
@@ -585,7 +588,7 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     // stores its row's sum as soon as it has it, and the block needs neither
     // the row sums in shared memory nor a barrier.  fp64 only: with fp32 /
     // bf16 the three-blocks-per-SM register budget would spill.
-    const bool direct = sizeof(AT) == 8 && !staged && Epi::kDirect;
+    const bool direct = (sizeof(AT) == 8 || LA) && !staged && Epi::kDirect;
     epi.bind(r0, a.T, smem + align128(L.total));
     if (staged && tid == 0) {
         mbar_init(mbar, 1);
@@ -628,7 +631,7 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     }
     // 1. full pass (sliced ELL) while the copy runs, over the slices that
     // hold entries (s0 .. se-1)
-    if constexpr (sizeof(AT) == 8 && Epi::kPipelined) {
+    if constexpr ((sizeof(AT) == 8 || LA) && Epi::kPipelined) {
         full_pass_pipelined<VT, XT, AT, Epi>(a.sl_ent, a.sl_meta, a.fval, a.fcol, s0 + warp, se, nwarps, r0, xop,
                                              epi, rowacc, direct);
     } else {
@@ -802,14 +805,14 @@ __device__ __noinline__ void long_pieces_block(const SpmvArgs<VT, XT, AT> &a, in
 template <typename AT>
 constexpr int tile_min_blocks() { return sizeof(AT) == 8 ? 2 : 3; }
 
-template <typename VT, typename XT, typename AT>
-__global__ void __launch_bounds__(kBlock, tile_min_blocks<AT>()) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
+template <typename VT, typename XT, typename AT, bool LA = false>
+__global__ void __launch_bounds__(kBlock, LA ? 2 : tile_min_blocks<AT>()) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (static_cast<int>(blockIdx.x) < a.nlb) {
         long_pieces_block<VT, XT, AT>(a, blockIdx.x, a.x);
     } else {
         EpiSpmv<XT, AT> epi{a.alpha, a.y};
-        tile_block<VT, XT, AT>(a, blockIdx.x - a.nlb, smem, a.x, epi);
+        tile_block<VT, XT, AT, EpiSpmv<XT, AT>, LA>(a, blockIdx.x - a.nlb, smem, a.x, epi);
     }
 }
 

@@ -19,6 +19,7 @@ F64, F32, BF16 = 0, 1, 2
 RCM_GUARD = 1
 RCM_PERIPHERAL = 2
 SPLIT_SYMMETRIC = 1
+VARIANT_LOOKAHEAD = 1
 
 OK, EINVAL, ENOTSKEW, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, EUNSUPPORTED, ESTATE, ENONFINITE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9
@@ -37,7 +38,7 @@ class Pars3Error(RuntimeError):
 class pars3_split_params(C.Structure):
     _fields_ = [("T", C.c_int32), ("W", C.c_int32), ("dtypes", C.c_int32), ("long_row", C.c_int32),
                 ("flags", C.c_int32), ("piece", C.c_int32), ("long_slices", C.c_int32),
-                ("reserved", C.c_int32 * 1)]
+                ("lane_bytes", C.c_int32), ("variant", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class pars3_canonical(C.Structure):
@@ -114,6 +115,7 @@ def lib() -> C.CDLL:
         "pars3_spmv_host": ([P, i32, f64, P, P, P], C.c_int),
         "pars3_check": ([P, P], C.c_int),
         "pars3_autotune": ([i32, P, P, P, P, P, i32, i32, P, P], C.c_int),
+        "pars3_fp64_fma_rate": ([P, P], C.c_int),
         "pars3_free": ([P], None),
     }
     for name, (args, res) in sig.items():
@@ -129,7 +131,7 @@ def exported_symbols():
     return ["pars3_strerror", "pars3_version", "pars3_reorder", "pars3_split", "pars3_split_export",
             "pars3_info_get", "pars3_layout_check", "pars3_upload", "pars3_spmv", "pars3_spmm",
             "pars3_spmm_batched", "pars3_mrs", "pars3_permute", "pars3_unpermute", "pars3_spmv_host",
-            "pars3_check", "pars3_autotune", "pars3_free", "pars3_spmv_noalloc"]
+            "pars3_check", "pars3_autotune", "pars3_free", "pars3_spmv_noalloc", "pars3_fp64_fma_rate"]
 
 
 def _chk(rc: int, where: str):
@@ -223,13 +225,15 @@ class Handle:
 
 
 def pars3_split(n: int, rowptr, col, val, perm=None, T: int = 0, W: int = 0, dtypes: int = 0,
-                long_row: int = 0, symmetric: bool = False, piece: int = 0, long_slices: int = 0) -> Handle:
+                long_row: int = 0, symmetric: bool = False, piece: int = 0, long_slices: int = 0,
+                lane_bytes: int = 0, variant: int = 0) -> Handle:
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     ci = np.ascontiguousarray(col, dtype=np.int32)
     v = np.ascontiguousarray(val, dtype=np.float64)
     pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
     prm = pars3_split_params(T=T, W=W, dtypes=dtypes, long_row=long_row,
-                             flags=SPLIT_SYMMETRIC if symmetric else 0, piece=piece, long_slices=long_slices)
+                             flags=SPLIT_SYMMETRIC if symmetric else 0, piece=piece, long_slices=long_slices,
+                             lane_bytes=lane_bytes, variant=variant)
     out = C.c_void_p()
     _chk(lib().pars3_split(int(n), _p(rp), _p(ci), _p(v), None if pm is None else _p(pm), C.byref(prm),
                            C.byref(out)), "pars3_split")
@@ -350,20 +354,39 @@ def pars3_mrs(h: Handle, alpha: float, b, x, rtol: float = 1e-10, max_iter: int 
     return r.as_dict()
 
 
+SPLIT_KEYS = ("T", "W", "dtypes", "long_row", "piece", "long_slices", "lane_bytes", "variant")
+
+
 def pars3_autotune(n: int, rowptr, col, val, perm=None, dtype: int = F64, k: int = 1, dtypes: int = 0,
-                   T: int = 0, W: int = 0, long_row: int = 0):
-    """Cut points (T, W) chosen by timing pars3_spmm with k right-hand sides
-    on the current device; returns dict(T, W, dtypes, long_row, us)."""
+                   T: int = 0, W: int = 0, long_row: int = 0, symmetric: bool = False):
+    """Split parameters chosen by timing pars3_spmm with k right-hand sides on
+    the current device; returns a dict of SPLIT_KEYS plus the time "us".
+    Pass it on with split_kwargs(result) to pars3_split."""
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     ci = np.ascontiguousarray(col, dtype=np.int32)
     v = np.ascontiguousarray(val, dtype=np.float64)
     pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
-    base = pars3_split_params(T=T, W=W, dtypes=dtypes, long_row=long_row)
+    base = pars3_split_params(T=T, W=W, dtypes=dtypes, long_row=long_row,
+                              flags=SPLIT_SYMMETRIC if symmetric else 0)
     best = pars3_split_params()
     us = C.c_double()
     _chk(lib().pars3_autotune(int(n), _p(rp), _p(ci), _p(v), None if pm is None else _p(pm), C.byref(base),
                               int(dtype), int(k), C.byref(best), C.byref(us)), "pars3_autotune")
-    return dict(T=best.T, W=best.W, dtypes=best.dtypes, long_row=best.long_row, us=us.value)
+    out = {key: getattr(best, key) for key in SPLIT_KEYS}
+    out["us"] = us.value
+    return out
+
+
+def split_kwargs(tuned: dict) -> dict:
+    """The pars3_split keyword arguments of an autotune result."""
+    return {key: tuned[key] for key in SPLIT_KEYS}
+
+
+def pars3_fp64_fma_rate(stream=None) -> float:
+    """fp64 FMAs per second of the current device (measurement helper)."""
+    r = C.c_double()
+    _chk(lib().pars3_fp64_fma_rate(C.byref(r), _stream(stream)), "pars3_fp64_fma_rate")
+    return r.value
 
 
 def pars3_free(h: Handle):

@@ -25,6 +25,49 @@ def pow2(v):
     return v > 0 and (v & (v - 1)) == 0
 
 
+def assert_valid_layout_params(r):
+    assert r["long_row"] in (0, 32, 64, 128) and r["piece"] in (0, 128, 192, 255), r
+    assert r["long_slices"] in (0, 16, 32) and r["lane_bytes"] in (0, 4, 8, 16, 32), r
+    assert r["variant"] in (0, P.VARIANT_LOOKAHEAD), r
+
+
+@pytest.mark.parametrize("dtype,k", [(P.F64, 1), (P.F32, 1), (P.F32, 8), (P.F64, 4)],
+                         ids=["f64k1", "f32k1", "f32k8", "f64k4"])
+def test_power_law_choice_valid_bit_exact_and_correct(dtype, k):
+    """On an R-MAT graph the search also covers the long-row settings and the
+    kernel variant or lane width; the split at the returned parameters is
+    bit-exact against the oracle and its product (and multi-vector product)
+    matches the oracle."""
+    A = W.rmat(14, 120000, seed=33)
+    perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
+    r = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=dtype, k=k)
+    assert_valid_layout_params(r)
+    kw = P.split_kwargs(r)
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, **kw)
+    ex = P.pars3_split_export(h)
+    so = O.split(A, perm, r["T"], r["W"])
+    for key in KEYS:
+        assert np.array_equal(ex[key], so[key]), key
+    assert P.pars3_layout_check(h) == 0
+    P.pars3_upload(h)
+    F = O.Full(A)
+    vt = torch.float64 if dtype == P.F64 else torch.float32
+    tau = 1e-12 if dtype == P.F64 else 2e-6
+    X = W.vector("uniform", (A.n, k), 7)
+    Xd = torch.from_numpy(np.ascontiguousarray(X[perm] if k > 1 else X[perm, 0])).to("cuda", vt)
+    Yd = torch.full_like(Xd, float("nan"))
+    if k == 1:
+        P.pars3_spmv(h, dtype, 0.5, Xd, Yd)
+    else:
+        P.pars3_spmm(h, dtype, 0.5, Xd, Yd)
+    torch.cuda.synchronize()
+    Y = Yd.double().cpu().numpy().reshape(A.n, k)
+    for c in range(k):
+        ref = F.apply(0.5, X[:, c])[perm]
+        bound = F.abs_bound(0.5, X[:, c])[perm]
+        assert np.all(np.abs(Y[:, c] - ref) <= tau * bound + 1e-30), c
+
+
 @pytest.mark.parametrize("dtype,k", [(P.F64, 1), (P.F32, 4), (P.BF16, 16)], ids=["f64k1", "f32k4", "bf16k16"])
 def test_choice_valid_bit_exact_and_correct(dtype, k):
     A = W.grid_plus_random((24, 24, 24), 0.01, "normal", 5)
@@ -33,7 +76,8 @@ def test_choice_valid_bit_exact_and_correct(dtype, k):
     T, Wc = r["T"], r["W"]
     assert pow2(T) and pow2(Wc) and 32 <= Wc <= T <= 8192, r
     assert r["us"] > 0 and r["dtypes"] & P.dtype_bit(dtype)
-    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=Wc, dtypes=r["dtypes"])
+    assert_valid_layout_params(r)
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, **P.split_kwargs(r))
     ex = P.pars3_split_export(h)
     so = O.split(A, perm, T, Wc)
     for key in KEYS:

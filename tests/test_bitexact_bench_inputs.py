@@ -46,8 +46,8 @@ def _assert_rcm_equal(A, flags, guard, peripheral):
     return perm
 
 
-def _assert_split_equal(A, perm, T, Wc):
-    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=Wc)
+def _assert_split_equal(A, perm, T, Wc, **layout):
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=T, W=Wc, **layout)
     ex = P.pars3_split_export(h)
     so = O.split(A, perm, T, Wc)
     for k in KEYS:
@@ -99,7 +99,8 @@ def test_split_bit_exact_at_autotuned_cuts(name, dtype, k):
     A = _bench_matrix(name)
     perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
     t = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=dtype, k=k, dtypes=P.dtype_bit(dtype))
-    _assert_split_equal(A, perm, t["T"], t["W"])
+    kw = P.split_kwargs(t)
+    _assert_split_equal(A, perm, kw.pop("T"), kw.pop("W"), **kw)
 
 
 @pytest.mark.gpu
@@ -114,4 +115,5 @@ def test_split_bit_exact_at_autotuned_cuts_batched():
         A = W.config4_matrix(m, shp)
         perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
         t = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=P.F32, k=4, dtypes=both)
-        _assert_split_equal(A, perm, t["T"], t["W"])
+        kw = P.split_kwargs(t)
+        _assert_split_equal(A, perm, kw.pop("T"), kw.pop("W"), **kw)

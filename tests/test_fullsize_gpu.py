@@ -76,7 +76,7 @@ def test_cfg1_autotuned_cut_and_k32(cfg1):
     A, alpha, x, perm, F = cfg1
     for dtype, k in ((P.F64, 1), (P.F32, 32)):
         t = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=dtype, k=k, dtypes=ALL)
-        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=t["T"], W=t["W"], dtypes=ALL)
+        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, **P.split_kwargs(t))
         P.pars3_upload(h)
         X = x if k == 1 else W.vector("uniform", (A.n, k), 91)
         compare(A, perm, h, dtype, alpha, X, F)
@@ -88,10 +88,10 @@ def test_cfg2_autotuned(cfg1):
     F = O.Full(A)
     for dtype in (P.F64, P.F32):
         t = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=dtype, k=1, dtypes=ALL)
-        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=t["T"], W=t["W"], dtypes=ALL)
+        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, **P.split_kwargs(t))
         P.pars3_upload(h)
         info = P.pars3_info_get(h)
-        assert info["long_rows"] > 0   # the power-law rows take the chunked path
+        assert info["long_rows"] > 0   # the power-law rows are summed in pieces
         compare(A, perm, h, dtype, alpha, x, F)
         h.close()
 
@@ -105,7 +105,7 @@ def test_cfg4_batched_autotuned(dtype, k):
         perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
         t = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=P.F32, k=4,
                              dtypes=P.dtype_bit(P.F64) | P.dtype_bit(P.F32))
-        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=t["T"], W=t["W"], dtypes=t["dtypes"])
+        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, **P.split_kwargs(t))
         P.pars3_upload(h)
         mats.append(A)
         perms.append(perm)

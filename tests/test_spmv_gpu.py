@@ -165,3 +165,12 @@ def test_rejects_misaligned_vectors():
     with pytest.raises(P.Pars3Error) as e:
         P.pars3_spmv(h, P.F64, 1.0, buf[1:], y)
     assert e.value.code == P.EINVAL
+
+
+def test_fp64_fma_rate_probe():
+    """The fp64 FMA rate helper returns a plausible rate for a GB300-class
+    part (between 0.05 and 10 T FMA/s) and the same order twice."""
+    r1 = P.pars3_fp64_fma_rate()
+    r2 = P.pars3_fp64_fma_rate()
+    assert 5e10 < r1 < 1e13 and 5e10 < r2 < 1e13
+    assert 0.5 < r1 / r2 < 2.0
