@@ -19,6 +19,11 @@ namespace pars3 {
 
 int spmm_smem_bytes(const pars3_handle *h, int dtype);
 
+// upper bound of the batched kernel's static shared memory (its argument
+// copy and item index; ptxas reports 384 bytes), kept out of the dynamic
+// shared memory it may request
+constexpr int kBatchedStaticSmem = 1024;
+
 // work unit u belongs to matrix m with upre[m] <= u < upre[m+1]
 __device__ __forceinline__ int unit_matrix(const int32_t *upre, int count, int u) {
     int lo = 0, hi = count;
@@ -65,7 +70,7 @@ __global__ void __launch_bounds__(kBlock, 2) batched_kernel(const SpmvArgs<VT, X
 // fold of all matrices: one thread per (receiving row, column)
 struct FoldArgs {
     int32_t nf;
-    const int32_t *frow, *fhalo, *flong, *lp0, *lrem;
+    FoldLists F;
 };
 
 template <typename XT, typename AT>
@@ -86,13 +91,12 @@ __global__ void __launch_bounds__(256) batched_fold_kernel(const FoldArgs *__res
         const int64_t local = q - fpre[m];
         const int f = static_cast<int>(local / k), c = static_cast<int>(local - static_cast<int64_t>(f) * k);
         const FoldArgs F = fa[m];
-        const int64_t r = F.frow[f];
+        const int64_t r = F.F.row[f];
         XT *y = ys[m];
         AT v = static_cast<AT>(y[r * k + c]);
-        const int hh = F.fhalo[f];
+        const int hh = F.F.halo[f];
         if (hh >= 0) v += halos[m][static_cast<int64_t>(hh) * k + c];
-        const int l = F.flong[f];
-        if (l >= 0) v = long_row_sum<AT>(l, F.lp0, F.lrem, lparts[m], k, c, v);
+        v = long_row_sum<AT>(F.F.p0[f], F.F.np[f], F.F.rem[f], lparts[m], k, c, v);
         y[r * k + c] = static_cast<XT>(v);
     }
 }
@@ -144,7 +148,7 @@ static int enqueue(BatchCache &C, int count, int64_t total_units, int64_t total_
     if (!(configured.load() & dbit)) {
         cudaError_t e = cudaFuncSetAttribute(batched_kernel<VT, XT, AT, LPR, NV>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemLimit - static_cast<int>(sizeof(SpmvArgs<VT, XT, AT>)) - 64);
+                                             kSmemLimit - kBatchedStaticSmem);
         if (e != cudaSuccess) return cuda_status(e);
         configured.fetch_or(dbit);
     }
@@ -199,7 +203,7 @@ static int run_batched(BatchCache &C, pars3_handle *const *hs, int count, int dt
         fpre.push_back(fpre.back() + static_cast<int64_t>(h->L.fold_row.size()) * k);
         smem = std::max(smem, k == 1 ? smem_bytes_for(h, dtype) : spmm_smem_bytes(h, dtype));
     }
-    if (smem + static_cast<int>(sizeof(SpmvArgs<VT, XT, AT>)) + 64 > kSmemLimit) return PARS3_EUNSUPPORTED;
+    if (smem + kBatchedStaticSmem > kSmemLimit) return PARS3_EUNSUPPORTED;
     if (!same) {
         C.release();
         std::vector<SpmvArgs<VT, XT, AT>> args;
@@ -210,8 +214,7 @@ static int run_batched(BatchCache &C, pars3_handle *const *hs, int count, int dt
             const pars3_handle *h = hs[m];
             args.push_back(make_args<VT, XT, AT>(h, dtype, alpha[m], X[m], Y[m]));
             const DevLayout &D = h->D;
-            fa.push_back(FoldArgs{static_cast<int32_t>(h->L.fold_row.size()), D.fold_row, D.fold_halo, D.fold_long,
-                                  D.lp0, D.lrem});
+            fa.push_back(FoldArgs{static_cast<int32_t>(h->L.fold_row.size()), fold_lists(D)});
             halos.push_back(D.halo);
             lparts.push_back(D.lpart);
             ys.push_back(Y[m]);

@@ -76,6 +76,10 @@ static int upload_impl(pars3_handle *h, cudaStream_t st) {
     UP(D.hrp, L.hrp);
     UP(D.hcol, L.hcol);
     UP(D.hcperm, L.hcperm);
+    UP(D.hrowc, L.hrowc);
+    UP(D.hcsoff, L.hcsoff);
+    UP(D.hcsn, L.hcsn);
+    UP(D.hcs, L.hcs);
     UP(D.hhoff, L.hhoff);
     UP(D.hhrow, L.hhrow);
     UP(D.sl_off, L.sl_off);
@@ -83,14 +87,14 @@ static int upload_impl(pars3_handle *h, cudaStream_t st) {
     UP(D.sl_e, L.sl_e);
     UP(D.sl_meta, L.sl_meta);
     UP(D.fcol, L.fcol);
-    UP(D.lp0, L.lp0);
-    UP(D.lrem, L.lrem);
     UP(D.ls_ent, L.ls_ent);
     UP(D.ls_len, L.ls_len);
     UP(D.lcol, L.lcol);
     UP(D.fold_row, L.fold_row);
     UP(D.fold_halo, L.fold_halo);
-    UP(D.fold_long, L.fold_long);
+    UP(D.fold_p0, L.fold_p0);
+    UP(D.fold_np, L.fold_np);
+    UP(D.fold_rem, L.fold_rem);
     UP(D.perm, h->perm);
     if (h->dtypes & PARS3_DTYPE_BIT(PARS3_F64)) {
         double *a, *b, *c;

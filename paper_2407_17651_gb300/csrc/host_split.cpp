@@ -163,14 +163,15 @@ void dtype_sizes(int dtype, uint32_t *vsz, uint32_t *xsz, uint32_t *asz) {
     else { *vsz = 2; *xsz = 4; *asz = 4; }
 }
 
-static uint32_t smem_total(const pars3_handle *h, int dtype, int64_t Mh) {
+static uint32_t smem_total(const pars3_handle *h, int dtype, int64_t Mh, int64_t CS) {
     uint32_t vsz, xsz, asz;
     dtype_sizes(dtype, &vsz, &xsz, &asz);
-    return smem_layout(h->T, h->W, static_cast<uint32_t>(round_up(Mh, kAlignHalf)), vsz, xsz, asz).total;
+    return smem_layout(h->T, h->W, static_cast<uint32_t>(round_up(Mh, kAlignHalf)), static_cast<uint32_t>(CS), vsz,
+                       xsz, asz).total;
 }
 
 int smem_bytes_for(const pars3_handle *h, int dtype) {
-    return static_cast<int>(smem_total(h, dtype, h->L.max_tile_half));
+    return static_cast<int>(smem_total(h, dtype, h->L.max_tile_half, h->L.max_tile_cs));
 }
 
 // Dynamic shared memory of the plain product's tile kernel.  When no tile
@@ -183,7 +184,7 @@ int spmv_smem_bytes(const pars3_handle *h, int dtype) {
     if (dtype == PARS3_F64) return 0;
     uint32_t vsz, xsz, asz;
     dtype_sizes(dtype, &vsz, &xsz, &asz);
-    const SmemLayout s = smem_layout(h->T, h->W, 0u, vsz, xsz, asz);
+    const SmemLayout s = smem_layout(h->T, h->W, 0u, 0u, vsz, xsz, asz);
     return static_cast<int>(s.rowacc + static_cast<uint32_t>(h->T) * asz);
 }
 
@@ -201,8 +202,8 @@ static int64_t half_room(const pars3_handle *h) {
         if (!(h->dtypes & PARS3_DTYPE_BIT(d))) continue;
         uint32_t vsz, xsz, asz;
         dtype_sizes(d, &vsz, &xsz, &asz);
-        const int64_t base = smem_total(h, d, 0);
-        const int64_t per = vsz + (vsz == asz ? 0 : asz) + 4;
+        const int64_t base = smem_total(h, d, 0, 8);
+        const int64_t per = vsz + 6 + 4;   // value, column, (column, row) order, row, at most a segment word
         const int64_t room = static_cast<int64_t>(kSmemLimit) - base - 1024;
         best = std::min<int64_t>(best, room > 0 ? room / per : -1);
     }
@@ -271,6 +272,7 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
     const int64_t hn = L.hoff[nt];
     L.hcol.assign(hn, 0);
     L.hcperm.assign(hn, 0);
+    L.hrowc.assign(hn, 0);
     L.hrp.assign(static_cast<size_t>(nt) * (T + 8), 0);
     std::vector<int32_t> hsrc(hn, 0);   // entry + 1 (0 = padding)
     std::vector<int32_t> hpos(nnz, -1);
@@ -290,22 +292,37 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
         }
         for (int32_t i = r1; i <= r0 + T + 7; ++i) lrp[i - r0] = static_cast<uint16_t>(q);
     }
+    // (column, row) order of each tile's middle entries, the window position
+    // of each one's row, and the column segments: one word per distinct
+    // column (window position | first (column, row) index << 16), in column
+    // order, then an end word (0xffff | count << 16); the tile's halo columns
+    // (positions below W) are its first segments, in the order of its halo
+    // targets
     L.hhoff.assign(static_cast<size_t>(nt) + 1, 0);
+    L.hcsoff.assign(static_cast<size_t>(nt) + 1, 0);
+    L.hcs.clear();
+    L.hcsn.clear();
+    L.max_tile_cs = 0;
     for (int32_t t = 0; t < nt; ++t) {
-        const int32_t r0 = t * T;
+        const int32_t r0 = t * T, wb = r0 - W;
         int32_t q = 0, last = -1;
         for (int32_t s = h->tile_ptr[t]; s < h->tile_ptr[t + 1]; ++s) {
             const int32_t e = h->tile_list[s];
             if (!half[e]) continue;
             L.hcperm[L.hoff[t] + q] = static_cast<uint16_t>(hpos[e] - L.hoff[t]);
-            ++q;
+            L.hrowc[L.hoff[t] + q] = static_cast<uint16_t>(row_of[e] - wb);
             const int32_t j = ci[e];
-            if (j < r0 && j != last) {
-                L.hhrow.push_back(j);
-                last = j;
-            }
+            if (j != last) L.hcs.push_back(static_cast<uint32_t>(j - wb) | (static_cast<uint32_t>(q) << 16));
+            if (j < r0 && j != last) L.hhrow.push_back(j);
+            last = j;
+            ++q;
         }
         L.hhoff[t + 1] = static_cast<int32_t>(L.hhrow.size());
+        L.hcs.push_back(0xffffu | (static_cast<uint32_t>(q) << 16));
+        L.hcsn.push_back(static_cast<int32_t>(L.hcs.size()) - L.hcsoff[t] - 1);   // segments (not the end word)
+        while (L.hcs.size() % 4) L.hcs.push_back(0xffffu | (static_cast<uint32_t>(q) << 16));
+        L.hcsoff[t + 1] = static_cast<int32_t>(L.hcs.size());
+        L.max_tile_cs = std::max(L.max_tile_cs, L.hcsoff[t + 1] - L.hcsoff[t]);
     }
     // ---- 2. full-path length of every row: its non-half lower entries and the
     // non-half entries of its column (mirrored)
@@ -477,9 +494,12 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
         for (size_t l = 0; l < L.lrow.size(); ++l) lidx[L.lrow[l]] = static_cast<int32_t>(l);
         for (int32_t i = 0; i < n; ++i)
             if (hidx[i] >= 0 || lidx[i] >= 0) {
+                const int32_t l = lidx[i];
                 L.fold_row.push_back(i);
                 L.fold_halo.push_back(hidx[i]);
-                L.fold_long.push_back(lidx[i]);
+                L.fold_p0.push_back(l >= 0 ? L.lp0[l] : 0);
+                L.fold_np.push_back(l >= 0 ? L.lp0[l + 1] - L.lp0[l] : 0);
+                L.fold_rem.push_back(l >= 0 ? L.lrem[l] : -1);
             }
     }
     // ---- 7. values per precision
@@ -749,6 +769,33 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
                 if (q > 0 && L.hcol[L.hoff[t] + e] < L.hcol[L.hoff[t] + L.hcperm[L.hoff[t] + q - 1]])
                     return PARS3_EINVAL;
             }
+            // the row of each (column, row) entry, and the column segments:
+            // one per distinct column in order, covering the list, halo
+            // columns first (one per halo target)
+            {
+                std::vector<int32_t> row_of_q(L.hcnt[t]);
+                for (int32_t i = r0; i < r1; ++i)
+                    for (int32_t q = lrp[i - r0]; q < lrp[i - r0 + 1]; ++q) row_of_q[q] = i;
+                for (int32_t q = 0; q < L.hcnt[t]; ++q)
+                    if (wb + L.hrowc[L.hoff[t] + q] != row_of_q[L.hcperm[L.hoff[t] + q]]) return PARS3_EINVAL;
+                const uint32_t *cs = &L.hcs[L.hcsoff[t]];
+                const int32_t ncs = L.hcsoff[t + 1] - L.hcsoff[t];
+                int32_t s = 0, k = 0, nhalo = 0;
+                for (; s < ncs && (cs[s] & 0xffffu) != 0xffffu; ++s) {
+                    const int32_t pos = static_cast<int32_t>(cs[s] & 0xffffu);
+                    if (static_cast<int32_t>(cs[s] >> 16) != k) return PARS3_EINVAL;
+                    if (s > 0 && pos <= static_cast<int32_t>(cs[s - 1] & 0xffffu)) return PARS3_EINVAL;
+                    while (k < L.hcnt[t] && L.hcol[L.hoff[t] + L.hcperm[L.hoff[t] + k]] == pos) ++k;
+                    if (k == static_cast<int32_t>(cs[s] >> 16)) return PARS3_EINVAL;   // empty segment
+                    if (pos < W) {
+                        if (L.hhoff[t] + nhalo >= L.hhoff[t + 1] || L.hhrow[L.hhoff[t] + nhalo] != wb + pos)
+                            return PARS3_EINVAL;
+                        ++nhalo;
+                    }
+                }
+                if (k != L.hcnt[t] || s >= ncs || static_cast<int32_t>(cs[s] >> 16) != L.hcnt[t]) return PARS3_EINVAL;
+                if (nhalo != L.hhoff[t + 1] - L.hhoff[t]) return PARS3_EINVAL;
+            }
             std::vector<uint8_t> seen(r1 - r0, 0);
             for (int32_t s2 = L.sl_off[t]; s2 < L.sl_off[t + 1]; ++s2) {
                 const int32_t width = (L.sl_ent[s2 + 1] - L.sl_ent[s2]) / kSlice;
@@ -813,7 +860,15 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
         for (size_t f = 0; f < L.fold_row.size(); ++f) {
             if (f > 0 && L.fold_row[f] <= L.fold_row[f - 1]) return PARS3_EINVAL;
             nh += L.fold_halo[f] >= 0;
-            nl += L.fold_long[f] >= 0;
+            const bool has_long = L.fold_np[f] > 0 || L.fold_rem[f] >= 0;
+            nl += has_long;
+            if (has_long) {   // the row's pieces, as the long-row tables give them
+                const auto it = std::lower_bound(L.lrow.begin(), L.lrow.end(), L.fold_row[f]);
+                if (it == L.lrow.end() || *it != L.fold_row[f]) return PARS3_EINVAL;
+                const size_t l = static_cast<size_t>(it - L.lrow.begin());
+                if (L.fold_p0[f] != L.lp0[l] || L.fold_np[f] != L.lp0[l + 1] - L.lp0[l] || L.fold_rem[f] != L.lrem[l])
+                    return PARS3_EINVAL;
+            }
         }
         if (nh != L.hhrow.size() || nl != L.lrow.size()) return PARS3_EINVAL;
     } catch (const std::bad_alloc &) {

@@ -34,6 +34,10 @@ struct Layout {
     std::vector<uint16_t> hrp;      // [ntiles*(T+8)] tile-local row pointers
     std::vector<uint16_t> hcol;     // window position p = j - (tT - W)
     std::vector<uint16_t> hcperm;   // tile-local entry index, (col, row) order
+    std::vector<uint16_t> hrowc;    // window position of the row of the k-th (col, row) entry
+    std::vector<int32_t> hcsoff;    // [ntiles+1] column segments of tile t: hcs[hcsoff[t] ..]
+    std::vector<int32_t> hcsn;      // [ntiles] number of column segments of tile t
+    std::vector<uint32_t> hcs;      // window position | (first (col, row) index << 16), end word last
     std::vector<int32_t> hhoff;     // [ntiles+1] halo targets of tile t
     std::vector<int32_t> hhrow;     // global row of each halo target (sorted per tile)
     // full path, sliced ELL: the short rows of tile t, sorted by length
@@ -65,13 +69,16 @@ struct Layout {
     std::vector<int32_t> lcol;      // slot-major, padded slots hold column 0 and value 0
     int32_t piece_len = 0;
     int32_t ls_per_block = kLongSlices;   // long slices per block
-    // fold items: one per row that receives a halo sum and/or long-row partials
-    std::vector<int32_t> fold_row, fold_halo, fold_long;  // halo index / long index or -1
+    // fold items: one per row that receives a halo sum and/or long-row piece
+    // sums: its halo index (or -1), its full pieces fold_p0 .. fold_p0 +
+    // fold_np - 1 and its last piece fold_rem (or -1)
+    std::vector<int32_t> fold_row, fold_halo, fold_p0, fold_np, fold_rem;
     // values per precision (fp64 / fp32 / bf16 bits)
     std::vector<double> hval64, fval64, lval64;
     std::vector<float> hval32, fval32, lval32;
     std::vector<uint16_t> hval16, fval16, lval16;
     int32_t max_tile_half = 0;
+    int32_t max_tile_cs = 0;        // column segment words of the largest tile (multiple of 4)
     int32_t max_tile_full = 0;      // sliced-ELL entries (with padding) of the largest tile
     int32_t max_tile_slices = 0;
     int32_t cap_full = 0;
@@ -82,15 +89,18 @@ struct Layout {
 
 struct DevLayout {
     int32_t *hoff = nullptr, *hcnt = nullptr;
-    uint16_t *hrp = nullptr, *hcol = nullptr, *hcperm = nullptr;
+    uint16_t *hrp = nullptr, *hcol = nullptr, *hcperm = nullptr, *hrowc = nullptr;
+    int32_t *hcsoff = nullptr, *hcsn = nullptr;
+    uint32_t *hcs = nullptr;
     int32_t *hhoff = nullptr, *hhrow = nullptr;
     int32_t *sl_off = nullptr, *sl_ent = nullptr, *sl_e = nullptr;
     uint32_t *sl_meta = nullptr;
     int32_t *fcol = nullptr;
-    int32_t *lp0 = nullptr, *lrem = nullptr, *ls_ent = nullptr;
+    int32_t *ls_ent = nullptr;
     uint16_t *ls_len = nullptr;
     int32_t *lcol = nullptr;
-    int32_t *fold_row = nullptr, *fold_halo = nullptr, *fold_long = nullptr;
+    int32_t *fold_row = nullptr, *fold_halo = nullptr, *fold_p0 = nullptr, *fold_np = nullptr,
+            *fold_rem = nullptr;
     void *hval[kNumDtypes] = {nullptr, nullptr, nullptr};
     void *fval[kNumDtypes] = {nullptr, nullptr, nullptr};
     void *lval[kNumDtypes] = {nullptr, nullptr, nullptr};

@@ -37,11 +37,8 @@ constexpr int kMaxRedBlocks = 1024;
 // block) beta_j from all partial norms and the Givens step.
 template <typename XT, typename AT>
 __global__ void __launch_bounds__(kRedBlock) fold_mrs_kernel(
-    int nitems, const int32_t *__restrict__ frow, const int32_t *__restrict__ fhalo,
-    const int32_t *__restrict__ flong, const AT *__restrict__ halo, const int32_t *__restrict__ lp0,
-    const int32_t *__restrict__ lrem, const AT *__restrict__ lpart, const MrsVectors<XT> m, int ntiles,
-    cudaGraphConditionalHandle cond,
-    int in_graph) {
+    int nitems, const FoldLists F, const AT *__restrict__ halo, const AT *__restrict__ lpart,
+    const MrsVectors<XT> m, int ntiles, cudaGraphConditionalHandle cond, int in_graph) {
     __shared__ double red[32];
     MrsState *st = m.st;
     if (st->done) {   // an unrolled loop body past convergence (or a solve that starts converged)
@@ -53,12 +50,10 @@ __global__ void __launch_bounds__(kRedBlock) fold_mrs_kernel(
     const AT scale = static_cast<AT>(st->e_scale);   // 1 / beta_{j-1}
     double nrm = 0.0;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nitems; f += gridDim.x * blockDim.x) {
-        const int r = frow[f];
+        const int r = __ldg(F.row + f), hi = __ldg(F.halo + f);
         AT s = AT(0);
-        const int hi = fhalo[f];
         if (hi >= 0) s += halo[hi];
-        const int l = flong[f];
-        if (l >= 0) s = long_row_sum<AT>(l, lp0, lrem, lpart, 1, 0, s);
+        s = long_row_sum<AT>(__ldg(F.p0 + f), __ldg(F.np + f), __ldg(F.rem + f), lpart, 1, 0, s);
         const XT wx = static_cast<XT>(static_cast<AT>(y[r]) + s * scale);
         y[r] = wx;
         nrm += static_cast<double>(wx) * static_cast<double>(wx);
@@ -272,7 +267,8 @@ static int build_graph(pars3_handle *h, int dtype, MrsWork &W) {
     uint32_t vsz, xsz, asz;
     dtype_sizes(dtype, &vsz, &xsz, &asz);
     const uint32_t tile_total =
-        smem_layout(h->T, h->W, static_cast<uint32_t>(round_up(h->L.max_tile_half, kAlignHalf)), vsz, xsz, asz).total;
+        smem_layout(h->T, h->W, static_cast<uint32_t>(round_up(h->L.max_tile_half, kAlignHalf)),
+                    static_cast<uint32_t>(h->L.max_tile_cs), vsz, xsz, asz).total;
     const uint32_t staged_bytes = align128(tile_total) + 3u * EpiMrs<XT, AT, true>::slice_bytes(h->T);
     constexpr uint32_t kStaticSlack = 1024;   // static shared memory of the fused kernel
     const bool stage = staged_bytes + kStaticSlack <= static_cast<uint32_t>(kSmemLimit);
@@ -313,8 +309,8 @@ static int build_graph(pars3_handle *h, int dtype, MrsWork &W) {
         else tile_kernel_mrs<VT, XT, AT, false, false><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
         if (!fused)
             fold_mrs_kernel<XT, AT><<<fold_blocks(h), kRedBlock, 0, W.capture>>>(
-                static_cast<int>(L.fold_row.size()), D.fold_row, D.fold_halo, D.fold_long,
-                static_cast<const AT *>(D.halo), D.lp0, D.lrem, static_cast<const AT *>(D.lpart),
+                static_cast<int>(L.fold_row.size()), fold_lists(D), static_cast<const AT *>(D.halo),
+                static_cast<const AT *>(D.lpart),
                 m, h->ntiles, G.cond, 1);
     }
     cudaGraph_t captured = nullptr;

@@ -17,26 +17,28 @@ namespace pars3 {
 // window, the tile's middle entries (filled by TMA bulk copies) and scratch;
 // a block of long-row pieces uses none.
 struct SmemLayout {
-    uint32_t xs, rowacc, hval, q, hcol, cperm, hrp, cs, ce, red, mbar, total;
+    uint32_t xs, rowacc, colacc, hval, hcol, cperm, hrowc, hrp, hcs, red, mbar, total;
 };
 
 PARS3_HD uint32_t align128(uint32_t a) { return (a + 127u) & ~127u; }
 
 // T: tile rows, W: window, Mh: half-path entries of the largest tile (padded
-// to 8), vsz/xsz/asz: bytes of the value, vector and accumulator types.
-// Every region starts on a 128-byte boundary (TMA bulk copies need 16).
-PARS3_HD SmemLayout smem_layout(uint32_t T, uint32_t W, uint32_t Mh, uint32_t vsz, uint32_t xsz, uint32_t asz) {
+// to 8), CS: column segment words of the largest tile (a multiple of 4),
+// vsz/xsz/asz: bytes of the value, vector and accumulator types.  Every
+// region starts on a 128-byte boundary (TMA bulk copies need 16).
+PARS3_HD SmemLayout smem_layout(uint32_t T, uint32_t W, uint32_t Mh, uint32_t CS, uint32_t vsz, uint32_t xsz,
+                                uint32_t asz) {
     SmemLayout s;
     s.xs = 0;
     s.rowacc = align128(s.xs + (T + W) * xsz);
-    s.hval = align128(s.rowacc + T * asz);
-    s.q = (vsz == asz) ? s.hval : align128(s.hval + Mh * vsz);
-    s.hcol = align128((vsz == asz) ? s.hval + Mh * vsz : s.q + Mh * asz);
+    s.colacc = align128(s.rowacc + T * asz);
+    s.hval = align128(s.colacc + T * asz);
+    s.hcol = align128(s.hval + Mh * vsz);
     s.cperm = align128(s.hcol + Mh * 2u);
-    s.hrp = align128(s.cperm + Mh * 2u);
-    s.cs = align128(s.hrp + (T + 8u) * 2u);
-    s.ce = align128(s.cs + (T + W) * 2u);
-    s.red = align128(s.ce + (T + W) * 2u);
+    s.hrowc = align128(s.cperm + Mh * 2u);
+    s.hrp = align128(s.hrowc + Mh * 2u);
+    s.hcs = align128(s.hrp + (T + 8u) * 2u);
+    s.red = align128(s.hcs + CS * 4u);
     s.mbar = align128(s.red + 32u * 8u);
     s.total = align128(s.mbar + 8u);
     return s;

@@ -23,22 +23,18 @@ __global__ void __launch_bounds__(kBlock, 2) spmm_kernel(const SpmvArgs<VT, XT, 
 // y[row, c] += halo sum + long-row piece sums (in the row's order), one
 // thread per (receiving row, column)
 template <typename XT, typename AT>
-__global__ void __launch_bounds__(256) fold_spmm_kernel(int nitems, int k, const int32_t *__restrict__ frow,
-                                                        const int32_t *__restrict__ fhalo,
-                                                        const int32_t *__restrict__ flong,
-                                                        const AT *__restrict__ halo, const int32_t *__restrict__ lp0,
-                                                        const int32_t *__restrict__ lrem,
-                                                        const AT *__restrict__ lpart, XT *__restrict__ y) {
+__global__ void __launch_bounds__(256) fold_spmm_kernel(int nitems, int k, const FoldLists F,
+                                                        const AT *__restrict__ halo, const AT *__restrict__ lpart,
+                                                        XT *__restrict__ y) {
     const int64_t total = static_cast<int64_t>(nitems) * k;
     for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
          q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int f = static_cast<int>(q / k), c = static_cast<int>(q - static_cast<int64_t>(f) * k);
-        const int64_t r = frow[f];
+        const int64_t r = __ldg(F.row + f);
+        const int hi = __ldg(F.halo + f);
         AT v = static_cast<AT>(y[r * k + c]);
-        const int hi = fhalo[f];
         if (hi >= 0) v += halo[static_cast<int64_t>(hi) * k + c];
-        const int l = flong[f];
-        if (l >= 0) v = long_row_sum<AT>(l, lp0, lrem, lpart, k, c, v);
+        v = long_row_sum<AT>(__ldg(F.p0 + f), __ldg(F.np + f), __ldg(F.rem + f), lpart, k, c, v);
         y[r * k + c] = static_cast<XT>(v);
     }
 }
@@ -78,8 +74,7 @@ static int launch_spmm_lpr(const pars3_handle *h, int dtype, double alpha, int k
     if (nf > 0) {
         const int64_t total = static_cast<int64_t>(nf) * k;
         const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 8LL * sm_count()));
-        fold_spmm_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, k, D.fold_row, D.fold_halo, D.fold_long,
-                                                         static_cast<const AT *>(halo), D.lp0, D.lrem,
+        fold_spmm_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, k, fold_lists(D), static_cast<const AT *>(halo),
                                                          static_cast<const AT *>(lpart), static_cast<XT *>(Y));
     }
     return cuda_status(cudaGetLastError());

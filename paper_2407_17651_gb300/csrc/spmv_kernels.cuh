@@ -44,7 +44,10 @@ struct SpmvArgs {
     int32_t n, T, W, ntiles, Mh;
     int32_t nls, nlb, lsb;   // long-row slices, their blocks (launched before the tiles), slices per block
     const int32_t *hoff, *hcnt;
-    const uint16_t *hrp, *hcol, *hcperm;
+    const uint16_t *hrp, *hcol, *hcperm, *hrowc;
+    const int32_t *hcsoff, *hcsn;
+    const uint32_t *hcs;
+    int32_t CS;         // column segment words of the largest tile
     const VT *hval;
     const int32_t *hhoff, *hhrow;
     AT *halo;
@@ -252,35 +255,35 @@ __device__ __forceinline__ void full_pass_pipelined(const int32_t *__restrict__ 
     }
 }
 
-// Half-storage row of the middle part: returns sum_j l_rj x_j and stores the
-// mirrored products q[e] = l_rj x_r (q may alias the value array: entry e is
-// read before it is overwritten, by the same thread).
+// Half-storage row of the middle part: sum_j l_rj x_j over its staged
+// entries e0 .. e1-1, x_j from the staged window (one thread, or the whole
+// warp for long rows).
 template <typename VT, typename XT, typename AT>
-__device__ __forceinline__ AT half_row_thread(int e0, int e1, const VT *hval, const uint16_t *hcol, AT *q,
-                                              const XT *xs, AT xr) {
+__device__ __forceinline__ AT half_row_thread(int e0, int e1, const VT *hval, const uint16_t *hcol, const XT *xs) {
     AT acc = AT(0);
-    for (int e = e0; e < e1; ++e) {
-        const AT v = sval<VT>(hval, e);
-        const AT xj = static_cast<AT>(xs[hcol[e]]);
-        q[e] = v * xr;
-        acc += v * xj;
-    }
+    for (int e = e0; e < e1; ++e) acc += sval<VT>(hval, e) * static_cast<AT>(xs[hcol[e]]);
     return acc;
 }
 
 template <typename VT, typename XT, typename AT>
-__device__ __forceinline__ AT half_row_warp(int e0, int e1, const VT *hval, const uint16_t *hcol, AT *q,
-                                            const XT *xs, AT xr) {
+__device__ __forceinline__ AT half_row_warp(int e0, int e1, const VT *hval, const uint16_t *hcol, const XT *xs) {
     const int lane = threadIdx.x & 31;
     AT acc = AT(0);
-    for (int e = e0 + lane; e < e1; e += 32) {
-        const AT v = sval<VT>(hval, e);
-        const AT xj = static_cast<AT>(xs[hcol[e]]);
-        q[e] = v * xr;
-        acc += v * xj;
-    }
+    for (int e = e0 + lane; e < e1; e += 32) acc += sval<VT>(hval, e) * static_cast<AT>(xs[hcol[e]]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Mirrored sum of one column: sum_i l_ij x_i over the column's entries, in
+// (column, row) order k0 .. k1-1: the staged value of entry cperm[k] and
+// x_i at the window position hrowc[k] of its row -- one FMA per entry, the
+// value read a second time from shared memory instead of a stored product.
+template <typename VT, typename XT, typename AT>
+__device__ __forceinline__ AT half_col_sum(int k0, int k1, const VT *hval, const uint16_t *cperm,
+                                           const uint16_t *hrowc, const XT *xs) {
+    AT acc = AT(0);
+    for (int k = k0; k < k1; ++k) acc += sval<VT>(hval, cperm[k]) * static_cast<AT>(xs[hrowc[k]]);
     return acc;
 }
 
@@ -556,16 +559,16 @@ __device__ __forceinline__ void prefetch_slices(const SpmvArgs<VT, XT, AT> &a, i
 template <typename VT, typename XT, typename AT, class Epi, bool LA = false>
 __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t, unsigned char *smem,
                                            const XT *__restrict__ xop, Epi &epi) {
-    const SmemLayout L = smem_layout(a.T, a.W, a.Mh, sizeof(VT), sizeof(XT), sizeof(AT));
+    const SmemLayout L = smem_layout(a.T, a.W, a.Mh, a.CS, sizeof(VT), sizeof(XT), sizeof(AT));
     XT *xs = reinterpret_cast<XT *>(smem + L.xs);
     AT *rowacc = reinterpret_cast<AT *>(smem + L.rowacc);
+    AT *colacc = reinterpret_cast<AT *>(smem + L.colacc);
     VT *hval = reinterpret_cast<VT *>(smem + L.hval);
-    AT *q = reinterpret_cast<AT *>(smem + L.q);
     uint16_t *hcol = reinterpret_cast<uint16_t *>(smem + L.hcol);
     uint16_t *cperm = reinterpret_cast<uint16_t *>(smem + L.cperm);
+    uint16_t *hrowc = reinterpret_cast<uint16_t *>(smem + L.hrowc);
     uint16_t *hrp = reinterpret_cast<uint16_t *>(smem + L.hrp);
-    uint16_t *cs = reinterpret_cast<uint16_t *>(smem + L.cs);
-    uint16_t *ce = reinterpret_cast<uint16_t *>(smem + L.ce);
+    uint32_t *hcs = reinterpret_cast<uint32_t *>(smem + L.hcs);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
     const int tid = threadIdx.x, P = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = P >> 5;
@@ -575,6 +578,8 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
     const int hb = a.hoff[t], hm = a.hcnt[t];
     const uint32_t hmp = static_cast<uint32_t>((hm + kAlignHalf - 1) / kAlignHalf * kAlignHalf);
     const uint32_t rpb = static_cast<uint32_t>(a.T + 8) * 2u;
+    const int cs0 = a.hcsoff[t];
+    const uint32_t csb = static_cast<uint32_t>(a.hcsoff[t + 1] - cs0) * 4u;
 
     // 0. with fp32 / bf16 values the copy engine prefetches the tile's
     // sliced-ELL rows into L2 (the warps' loads then wait on L2, not on HBM);
@@ -594,7 +599,7 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
         mbar_init(mbar, 1);
         fence_mbar_init();
         uint32_t tx = epi.stage_bytes(r0, nr);
-        if (stage_half) tx += nbulk + rpb + hmp * (sizeof(VT) + 4u);
+        if (stage_half) tx += nbulk + rpb + hmp * (sizeof(VT) + 6u) + csb;
         mbar_arrive_expect_tx(mbar, tx);
         if (stage_half) {
             if (nbulk > 0) bulk_g2s(xs + (wlo - wb), xop + wlo, nbulk, mbar);
@@ -602,15 +607,14 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
             bulk_g2s(hval, a.hval + hb, hmp * sizeof(VT), mbar);
             bulk_g2s(hcol, a.hcol + hb, hmp * 2u, mbar);
             bulk_g2s(cperm, a.hcperm + hb, hmp * 2u, mbar);
+            bulk_g2s(hrowc, a.hrowc + hb, hmp * 2u, mbar);
+            bulk_g2s(hcs, a.hcs + cs0, csb, mbar);
         }
         if constexpr (Epi::kStage) epi.stage_issue(r0, nr, smem + align128(L.total), mbar);
     }
     if (stage_half) {
         for (int g = wlo + static_cast<int>(nbulk / sizeof(XT)) + tid; g < r1; g += P) xs[g - wb] = xop[g];
-        for (int p = tid; p < nr + a.W; p += P) {
-            cs[p] = 0;
-            ce[p] = 0;
-        }
+        for (int r = tid; r < nr; r += P) colacc[r] = AT(0);
     }
     if constexpr (Epi::kStage) epi.stage_tail(r0, nr, smem + align128(L.total), tid, P);
     __syncthreads();   // the barrier is initialised before anyone waits on it
@@ -684,53 +688,41 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
         epi.end_block(t, red);
         return;
     }
-    AT *qq = sizeof(VT) == sizeof(AT) ? reinterpret_cast<AT *>(hval) : q;
-
-    // 2. half pass: middle row sums and mirrored products.  A warp owns 32
-    // consecutive rows; middle rows longer than kShortRow are summed by the
-    // whole warp, one after the other.
+    // 2. middle entries, each read from HBM once and used twice (Eqs. 2-6)
+    // with one FMA per use: row sums (a warp owns 32 consecutive rows; rows
+    // longer than kShortRow are summed by the whole warp, one after the
+    // other), then, with no barrier in between, mirrored sums per column
+    // (one thread per distinct column, its entries in row order).  Columns
+    // inside the tile complete their row below; columns before the tile (the
+    // conflicting region of Fig. 2) are the first segments and go to the
+    // halo list that the fold adds to the previous tile.
     for (int rb = (tid & ~31); rb < nr; rb += P) {
         const int r = rb + lane;
         const bool valid = r < nr;
-        const AT xr = valid ? static_cast<AT>(xs[r + a.W]) : AT(0);
         const int h0 = valid ? hrp[r] : 0, h1 = valid ? hrp[r + 1] : 0;
         const bool hlong = (h1 - h0) > kShortRow;
         AT hs = AT(0);
-        if (valid && !hlong) hs = half_row_thread<VT, XT, AT>(h0, h1, hval, hcol, qq, xs, xr);
+        if (valid && !hlong) hs = half_row_thread<VT, XT, AT>(h0, h1, hval, hcol, xs);
         unsigned m = __ballot_sync(0xffffffffu, hlong);
         while (m) {
             const int b = __ffs(m) - 1;
             m &= m - 1;
             const int f0 = __shfl_sync(0xffffffffu, h0, b), f1 = __shfl_sync(0xffffffffu, h1, b);
-            const AT xb = __shfl_sync(0xffffffffu, xr, b);
-            const AT s2 = half_row_warp<VT, XT, AT>(f0, f1, hval, hcol, qq, xs, xb);
+            const AT s2 = half_row_warp<VT, XT, AT>(f0, f1, hval, hcol, xs);
             if (lane == b) hs = s2;
         }
         if (valid && h1 > h0) rowacc[r] += hs;
     }
-    __syncthreads();
-
-    // 3. mirrored sums per column: segment boundaries of the (column, row) list
-    for (int k = tid; k < hm; k += P) {
-        const int key = hcol[cperm[k]];
-        if (k == 0 || hcol[cperm[k - 1]] != key) cs[key] = static_cast<uint16_t>(k);
-        if (k == hm - 1 || hcol[cperm[k + 1]] != key) ce[key] = static_cast<uint16_t>(k + 1);
+    const int g0 = a.hhoff[t], nhalo = a.hhoff[t + 1] - g0;
+    for (int sgm = tid; sgm < a.hcsn[t]; sgm += P) {
+        const uint32_t w0 = hcs[sgm], w1 = hcs[sgm + 1];
+        const AT c = half_col_sum<VT, XT, AT>(static_cast<int>(w0 >> 16), static_cast<int>(w1 >> 16), hval, cperm,
+                                              hrowc, xs);
+        if (sgm < nhalo) a.halo[g0 + sgm] = a.sym ? c : -c;
+        else colacc[static_cast<int>(w0 & 0xffffu) - a.W] = c;
     }
     __syncthreads();
-    for (int r = tid; r < nr; r += P) {
-        const int p = r + a.W;
-        const int k0 = cs[p], k1 = ce[p];
-        AT c = AT(0);
-        for (int k = k0; k < k1; ++k) c += qq[cperm[k]];
-        epi.finish(r0 + r, k1 > k0 ? (a.sym ? rowacc[r] + c : rowacc[r] - c) : rowacc[r]);
-    }
-    const int g0 = a.hhoff[t], g1 = a.hhoff[t + 1];
-    for (int h = g0 + tid; h < g1; h += P) {
-        const int p = a.hhrow[h] - wb;
-        AT c = AT(0);
-        for (int k = cs[p]; k < ce[p]; ++k) c += qq[cperm[k]];
-        a.halo[h] = a.sym ? c : -c;
-    }
+    for (int r = tid; r < nr; r += P) epi.finish(r0 + r, a.sym ? rowacc[r] + colacc[r] : rowacc[r] - colacc[r]);
     epi.end_block(t, red);
 }
 
@@ -852,34 +844,47 @@ __global__ void __launch_bounds__(kBlock, 2) tile_kernel_mrs(const SpmvArgs<VT, 
     }
 }
 
-// Piece sums of long row l in the row's entry order: its full pieces, then
-// its shorter last piece.
+// Piece sums of a long row in the row's entry order: its np full pieces
+// from p0, then its shorter last piece rem (if any).  Loads are issued four
+// at a time ahead of the additions, which stay in order.
 template <typename AT>
-__device__ __forceinline__ AT long_row_sum(int l, const int32_t *__restrict__ lp0, const int32_t *__restrict__ lrem,
-                                           const AT *__restrict__ lpart, int64_t k, int c, AT v) {
-    for (int p = lp0[l]; p < lp0[l + 1]; ++p) v += lpart[static_cast<int64_t>(p) * k + c];
-    const int r = lrem[l];
-    if (r >= 0) v += lpart[static_cast<int64_t>(r) * k + c];
+__device__ __forceinline__ AT long_row_sum(int p0, int np, int rem, const AT *__restrict__ lpart, int64_t k, int c,
+                                           AT v) {
+    int q = 0;
+    for (; q + 4 <= np; q += 4) {
+        AT t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = lpart[static_cast<int64_t>(p0 + q + u) * k + c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v += t[u];
+    }
+    for (; q < np; ++q) v += lpart[static_cast<int64_t>(p0 + q) * k + c];
+    if (rem >= 0) v += lpart[static_cast<int64_t>(rem) * k + c];
     return v;
 }
+
+// The fold lists of a handle (device pointers).
+struct FoldLists {
+    const int32_t *row, *halo, *p0, *np, *rem;
+};
 
 // One thread per receiving row: y[row] += halo sum, then the row's long-row
 // piece sums in order.
 template <typename XT, typename AT>
-__global__ void __launch_bounds__(256) fold_kernel(int nitems, const int32_t *__restrict__ frow,
-                                                   const int32_t *__restrict__ fhalo,
-                                                   const int32_t *__restrict__ flong, const AT *__restrict__ halo,
-                                                   const int32_t *__restrict__ lp0, const int32_t *__restrict__ lrem,
+__global__ void __launch_bounds__(256) fold_kernel(int nitems, const FoldLists F, const AT *__restrict__ halo,
                                                    const AT *__restrict__ lpart, XT *__restrict__ y) {
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nitems; f += gridDim.x * blockDim.x) {
-        const int r = frow[f];
+        const int r = __ldg(F.row + f), hi = __ldg(F.halo + f);
+        const int p0 = __ldg(F.p0 + f), np = __ldg(F.np + f), rem = __ldg(F.rem + f);
         AT v = static_cast<AT>(y[r]);
-        const int hi = fhalo[f];
         if (hi >= 0) v += halo[hi];
-        const int l = flong[f];
-        if (l >= 0) v = long_row_sum<AT>(l, lp0, lrem, lpart, 1, 0, v);
+        v = long_row_sum<AT>(p0, np, rem, lpart, 1, 0, v);
         y[r] = static_cast<XT>(v);
     }
+}
+
+inline FoldLists fold_lists(const DevLayout &D) {
+    return FoldLists{D.fold_row, D.fold_halo, D.fold_p0, D.fold_np, D.fold_rem};
 }
 
 // Kernel arguments of handle h for precision dtype (values of that
@@ -902,6 +907,11 @@ SpmvArgs<VT, XT, AT> make_spmv_args(const pars3_handle *h, int dtype) {
     a.hrp = D.hrp;
     a.hcol = D.hcol;
     a.hcperm = D.hcperm;
+    a.hrowc = D.hrowc;
+    a.hcsoff = D.hcsoff;
+    a.hcsn = D.hcsn;
+    a.hcs = D.hcs;
+    a.CS = L.max_tile_cs;
     a.hval = static_cast<const VT *>(D.hval[dtype]);
     a.hhoff = D.hhoff;
     a.hhrow = D.hhrow;
