@@ -202,7 +202,7 @@ static int64_t half_room(const pars3_handle *h) {
         if (!(h->dtypes & PARS3_DTYPE_BIT(d))) continue;
         uint32_t vsz, xsz, asz;
         dtype_sizes(d, &vsz, &xsz, &asz);
-        const int64_t base = smem_total(h, d, 0, 8);
+        const int64_t base = smem_total(h, d, 8, 8) - 8 * (vsz + 6);   // the fixed part of a half-path layout
         const int64_t per = vsz + 6 + 4;   // value, column, (column, row) order, row, at most a segment word
         const int64_t room = static_cast<int64_t>(kSmemLimit) - base - 1024;
         best = std::min<int64_t>(best, room > 0 ? room / per : -1);

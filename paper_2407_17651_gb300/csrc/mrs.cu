@@ -271,7 +271,11 @@ static int build_graph(pars3_handle *h, int dtype, MrsWork &W) {
                     static_cast<uint32_t>(h->L.max_tile_cs), vsz, xsz, asz).total;
     const uint32_t staged_bytes = align128(tile_total) + 3u * EpiMrs<XT, AT, true>::slice_bytes(h->T);
     constexpr uint32_t kStaticSlack = 1024;   // static shared memory of the fused kernel
-    const bool stage = staged_bytes + kStaticSlack <= static_cast<uint32_t>(kSmemLimit);
+    // fp64 tiles without middle entries finish each row in the full pass
+    // itself (no staging, no row sums in shared memory, the most L1 for the
+    // gathers of the operand): measured 118 -> see DESIGN; others stage
+    const bool direct_fp64 = sizeof(AT) == 8 && h->L.max_tile_half == 0;
+    const bool stage = !direct_fp64 && staged_bytes + kStaticSlack <= static_cast<uint32_t>(kSmemLimit);
     const int smem = stage ? std::max(smem_bytes_for(h, dtype), static_cast<int>(staged_bytes)) : smem_bytes_for(h, dtype);
     const Layout &L = h->L;
     // fusing the step into the tile kernel saves a launch per iteration in

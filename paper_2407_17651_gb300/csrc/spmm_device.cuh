@@ -256,8 +256,17 @@ __device__ __forceinline__ void spmm_tile(const SpmvArgs<VT, XT, AT> &a, int k, 
             ce[p] = 0;
         }
         __syncthreads();   // the barrier is initialised before anyone waits on it
-        mbar_wait_bounded(mbar, 0, a.err);
-        __syncthreads();
+        const bool gave_up = !mbar_wait_bounded(mbar, 0, a.err);
+        if (__syncthreads_or(gave_up)) {
+            // a staged copy did not arrive in time (the error word says so):
+            // the tile's rows and halo sums are marked invalid
+            for (int64_t q = tid; q < static_cast<int64_t>(nr) * k; q += P)
+                a.y[static_cast<int64_t>(r0) * k + q] = static_cast<XT>(CUDART_NAN);
+            for (int64_t q = static_cast<int64_t>(a.hhoff[t]) * k + tid; q < static_cast<int64_t>(a.hhoff[t + 1]) * k;
+                 q += P)
+                a.halo[q] = static_cast<AT>(CUDART_NAN);
+            return;
+        }
         if (tid == 0) mbar_inval(mbar);
         for (int r = tid; r < nr; r += P)
             for (int e = hrp[r]; e < hrp[r + 1]; ++e) hrow[e] = static_cast<uint16_t>(r);

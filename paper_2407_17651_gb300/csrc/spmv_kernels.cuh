@@ -32,6 +32,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include "devcommon.cuh"
 #include "internal.h"
@@ -302,6 +303,7 @@ struct EpiSpmv {
         return alpha * static_cast<AT>(__ldg(x + r));
     }
     __device__ __forceinline__ void finish(int r, AT v) { y[r] = static_cast<XT>(v); }
+    __device__ __forceinline__ void invalid(int r) { y[r] = static_cast<XT>(CUDART_NAN); }
     __device__ __forceinline__ void end_block(int, double *) {}
     __device__ __forceinline__ void bind(int, int, unsigned char *) {}
     __device__ __forceinline__ uint32_t stage_bytes(int, int) const { return 0u; }
@@ -410,6 +412,21 @@ __device__ __forceinline__ void mrs_step(MrsState *st, double tot, cudaGraphCond
     if (in_graph) cudaGraphSetConditional(cond, done ? 0u : 1u);
 }
 
+// Epilogue parameters of one MRS iteration, written to shared memory by the
+// first thread of each block: the epilogue reads them there when a row
+// finishes, so none of them occupies registers during the full pass (which
+// therefore keeps the fp64 look-ahead of the plain product).
+template <typename XT, typename AT>
+struct MrsEpiParams {
+    XT *y;
+    const XT *wpp, *pold;
+    XT *pnew, *xsol;
+    const uint32_t *fold_bits;
+    double *part;
+    AT scale, coef, c_w, c_p, tau;   // c_w = 1 / (beta_{j-2} rho_{j-1}), c_p = R[j-3,j-1] / rho_{j-1}
+    int lag;
+};
+
 template <typename XT, typename AT, bool S>
 struct EpiMrs {
     // With S, the tile's slices of w_{j-2}, p_{j-3} and x are bulk-copied
@@ -418,74 +435,78 @@ struct EpiMrs {
     // end; without S (tiles too large for the extra shared memory) they are
     // read from global memory.
     static constexpr bool kStage = S;
-    // the registers of the look-ahead pass would spill next to the
-    // epilogue's state
-    static constexpr bool kPipelined = false;
-    static constexpr bool kDirect = false;    // finish() needs the block's staged vectors and norm
-    XT *y;
-    const XT *wpp, *pold;
-    XT *pnew, *xsol;
-    const uint32_t *fold_bits;
-    double *part;
-    AT scale, coef, inv_b2, r3, inv_rho, tau;
-    bool lag;
+    static constexpr bool kPipelined = true;
+    // unstaged, a lane can finish its row as soon as it has the sum (the
+    // vectors come from global memory); staged, only after the copies land
+    static constexpr bool kDirect = !S;
+    const MrsEpiParams<XT, AT> *p;            // shared memory
+    unsigned char *area;                      // staged slices
     double nrm;
-    int r0;
-    const XT *s_wpp, *s_pold, *s_x;   // staged slices (tile-local index)
+    int r0, T;
     static PARS3_HD uint32_t slice_bytes(int T) {
         return (static_cast<uint32_t>(T) * sizeof(XT) + 127u) & ~127u;
+    }
+    __device__ __forceinline__ const XT *s_wpp() const {
+        return S ? reinterpret_cast<const XT *>(area) : p->wpp + r0;
+    }
+    __device__ __forceinline__ const XT *s_pold() const {
+        return S ? reinterpret_cast<const XT *>(area + slice_bytes(T)) : p->pold + r0;
+    }
+    __device__ __forceinline__ const XT *s_x() const {
+        return S ? reinterpret_cast<const XT *>(area + 2u * slice_bytes(T)) : p->xsol + r0;
     }
     // bytes the bulk copies move (16-byte multiple of each slice)
     __device__ __forceinline__ uint32_t stage_bytes(int, int nr) const {
         const uint32_t b = (static_cast<uint32_t>(nr) * sizeof(XT)) & ~15u;
-        return (lag ? 3u : 1u) * b;
+        return (p->lag ? 3u : 1u) * b;
     }
-    __device__ __forceinline__ void bind(int rr0, int T, unsigned char *area) {
+    __device__ __forceinline__ void bind(int rr0, int TT, unsigned char *ar) {
         r0 = rr0;
-        if (S) {
-            s_wpp = reinterpret_cast<const XT *>(area);
-            s_pold = reinterpret_cast<const XT *>(area + slice_bytes(T));
-            s_x = reinterpret_cast<const XT *>(area + 2u * slice_bytes(T));
-        } else {   // unstaged: the slices are the global vectors themselves
-            s_wpp = wpp + rr0;
-            s_pold = pold + rr0;
-            s_x = xsol + rr0;
-        }
+        T = TT;
+        area = ar;
     }
-    __device__ __forceinline__ void stage_issue(int rr0, int nr, unsigned char *area, uint64_t *mbar) {
+    __device__ __forceinline__ void stage_issue(int rr0, int nr, unsigned char *, uint64_t *mbar) {
         const uint32_t b = (static_cast<uint32_t>(nr) * sizeof(XT)) & ~15u;
         if (b == 0) return;
-        bulk_g2s(const_cast<XT *>(s_wpp), wpp + rr0, b, mbar);
-        if (lag) {
-            bulk_g2s(const_cast<XT *>(s_pold), pold + rr0, b, mbar);
-            bulk_g2s(const_cast<XT *>(s_x), xsol + rr0, b, mbar);
+        bulk_g2s(const_cast<XT *>(s_wpp()), p->wpp + rr0, b, mbar);
+        if (p->lag) {
+            bulk_g2s(const_cast<XT *>(s_pold()), p->pold + rr0, b, mbar);
+            bulk_g2s(const_cast<XT *>(s_x()), p->xsol + rr0, b, mbar);
         }
     }
     // rows past the last 16-byte boundary of the slice: plain loads
     __device__ __forceinline__ void stage_tail(int rr0, int nr, unsigned char *, int tid, int P) {
         const int first = static_cast<int>(((static_cast<uint32_t>(nr) * sizeof(XT)) & ~15u) / sizeof(XT));
         for (int q = first + tid; q < nr; q += P) {
-            const_cast<XT *>(s_wpp)[q] = wpp[rr0 + q];
-            if (lag) {
-                const_cast<XT *>(s_pold)[q] = pold[rr0 + q];
-                const_cast<XT *>(s_x)[q] = xsol[rr0 + q];
+            const_cast<XT *>(s_wpp())[q] = p->wpp[rr0 + q];
+            if (p->lag) {
+                const_cast<XT *>(s_pold())[q] = p->pold[rr0 + q];
+                const_cast<XT *>(s_x())[q] = p->xsol[rr0 + q];
             }
         }
     }
     __device__ __forceinline__ AT start(const XT *__restrict__, int) const { return AT(0); }
     __device__ __forceinline__ void finish(int r, AT raw) {
         const int q = r - r0;
-        AT w = raw * scale;
-        const AT wp = static_cast<AT>(s_wpp[q]);
-        if (coef != AT(0)) w += coef * wp;
+        AT w = raw * p->scale;
+        const AT wp = static_cast<AT>(s_wpp()[q]);
+        if (p->coef != AT(0)) w += p->coef * wp;
         const XT wx = static_cast<XT>(w);
-        y[r] = wx;
-        if (!((__ldg(fold_bits + (r >> 5)) >> (r & 31)) & 1u)) nrm += static_cast<double>(wx) * static_cast<double>(wx);
-        if (lag) {
-            const AT pv = (wp * inv_b2 - r3 * static_cast<AT>(s_pold[q])) * inv_rho;
-            pnew[r] = static_cast<XT>(pv);
-            xsol[r] = static_cast<XT>(static_cast<AT>(s_x[q]) + tau * pv);
+        p->y[r] = wx;
+        if (!((__ldg(p->fold_bits + (r >> 5)) >> (r & 31)) & 1u))
+            nrm += static_cast<double>(wx) * static_cast<double>(wx);
+        if (p->lag) {
+            // p_{j-1} = (w_{j-2} / beta_{j-2} - R[j-3,j-1] p_{j-3}) / rho_{j-1}, with both
+            // quotients folded into the two coefficients once per iteration
+            const AT pv = wp * p->c_w - p->c_p * static_cast<AT>(s_pold()[q]);
+            p->pnew[r] = static_cast<XT>(pv);
+            p->xsol[r] = static_cast<XT>(static_cast<AT>(s_x()[q]) + p->tau * pv);
         }
+    }
+    // an output that could not be computed (the norm then is NaN as well)
+    __device__ __forceinline__ void invalid(int r) {
+        p->y[r] = static_cast<XT>(CUDART_NAN);
+        nrm = CUDART_NAN;
     }
     // fixed-order block sum of the thread norms into part[t]
     __device__ __forceinline__ void end_block(int t, double *red) {
@@ -499,33 +520,30 @@ struct EpiMrs {
         if (threadIdx.x == 0) {
             double s = 0.0;
             for (int w = 0; w < nw; ++w) s += red[w];
-            part[t] = s;
+            p->part[t] = s;
         }
     }
 };
 
-template <typename XT, typename AT, bool S>
-__device__ __forceinline__ EpiMrs<XT, AT, S> make_mrs_epi(const MrsState *st, XT *const *wr, XT *const *pr, XT *xsol,
-                                                       const uint32_t *fold_bits, double *part, const XT **xop) {
-    EpiMrs<XT, AT, S> e;
+// The parameters of iteration j = st->j + 1 (one thread); *xop is the
+// operand w_{j-1}.
+template <typename XT, typename AT>
+__device__ __forceinline__ void fill_mrs_params(MrsEpiParams<XT, AT> *e, const MrsState *st, XT *const *wr,
+                                                XT *const *pr, XT *xsol, const uint32_t *fold_bits, double *part) {
     const int j = st->j + 1;
-    *xop = wr[(j + 2) % 3];
-    e.y = wr[j % 3];
-    e.wpp = wr[(j + 1) % 3];
-    e.pold = pr[j % 3];
-    e.pnew = pr[(j + 2) % 3];
-    e.xsol = xsol;
-    e.fold_bits = fold_bits;
-    e.part = part;
-    e.scale = static_cast<AT>(st->e_scale);
-    e.coef = static_cast<AT>(st->e_coef);
-    e.lag = j >= 2;
-    e.inv_b2 = static_cast<AT>(st->e_inv_b2);
-    e.r3 = static_cast<AT>(st->e_r3);
-    e.inv_rho = static_cast<AT>(st->e_inv_rho);
-    e.tau = static_cast<AT>(st->e_tau);
-    e.nrm = 0.0;
-    return e;
+    e->y = wr[j % 3];
+    e->wpp = wr[(j + 1) % 3];
+    e->pold = pr[j % 3];
+    e->pnew = pr[(j + 2) % 3];
+    e->xsol = xsol;
+    e->fold_bits = fold_bits;
+    e->part = part;
+    e->scale = static_cast<AT>(st->e_scale);
+    e->coef = static_cast<AT>(st->e_coef);
+    e->lag = j >= 2;
+    e->c_w = static_cast<AT>(st->e_inv_b2 * st->e_inv_rho);
+    e->c_p = static_cast<AT>(st->e_r3 * st->e_inv_rho);
+    e->tau = static_cast<AT>(st->e_tau);
 }
 
 // L2 prefetch of slices [s0, s1): their values, columns and metadata.  A
@@ -677,9 +695,20 @@ __device__ __forceinline__ void tile_block(const SpmvArgs<VT, XT, AT> &a, int t,
             }
         }
     }
-    if (direct) return;   // every row is complete and stored; nothing staged, nothing to reduce
-    if (staged) mbar_wait_bounded(mbar, 0, a.err);
-    __syncthreads();
+    if (direct) {   // every row is complete and stored; nothing staged
+        __shared__ double red_direct[32];
+        epi.end_block(t, red_direct);
+        return;
+    }
+    const bool gave_up = staged && !mbar_wait_bounded(mbar, 0, a.err);
+    if (__syncthreads_or(gave_up)) {
+        // a staged copy did not arrive in time (the error word says so): the
+        // tile's rows and halo sums are marked invalid instead of computed
+        // from incomplete data
+        for (int r = tid; r < nr; r += P) epi.invalid(r0 + r);
+        for (int hh = a.hhoff[t] + tid; hh < a.hhoff[t + 1]; hh += P) a.halo[hh] = static_cast<AT>(CUDART_NAN);
+        return;
+    }
     if (staged && tid == 0) mbar_inval(mbar);
 
     double *red = reinterpret_cast<double *>(smem + L.red);
@@ -821,6 +850,14 @@ struct MrsVectors {
     double *part;
 };
 
+// The last block of a fused iteration sums the blocks' partial norms and
+// runs the scalar step (not inlined, so the tile path keeps its registers).
+static __device__ __noinline__ void mrs_fused_tail(MrsState *st, double *part, int ntiles, cudaGraphConditionalHandle cond) {
+    __shared__ double red[32];
+    double tot = 0.0;
+    if (last_block_sum(&st->ticket, part, ntiles, red, &tot) && threadIdx.x == 0) mrs_step(st, tot, cond, 1);
+}
+
 // With FUSED (no halo targets and no long rows, so nothing is left for a
 // fold), the last tile block to finish also reduces the partial norms and
 // runs the scalar step, and the loop body is this one launch.
@@ -832,16 +869,16 @@ __global__ void __launch_bounds__(kBlock, 2) tile_kernel_mrs(const SpmvArgs<VT, 
         if (FUSED && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
         return;
     }
-    const XT *xop = nullptr;
-    EpiMrs<XT, AT, S> epi = make_mrs_epi<XT, AT, S>(m.st, m.w, m.p, m.xsol, m.fold_bits, m.part, &xop);
+    __shared__ MrsEpiParams<XT, AT> ep;
+    if (threadIdx.x == 0) fill_mrs_params<XT, AT>(&ep, m.st, m.w, m.p, m.xsol, m.fold_bits, m.part);
+    __syncthreads();
+    const XT *xop = m.w[(m.st->j + 3) % 3];   // w_{j-1} for iteration j = st->j + 1
+    EpiMrs<XT, AT, S> epi;
+    epi.p = &ep;
+    epi.nrm = 0.0;
     if (static_cast<int>(blockIdx.x) < a.nlb) long_pieces_block<VT, XT, AT>(a, blockIdx.x, xop);
     else tile_block<VT, XT, AT>(a, blockIdx.x - a.nlb, smem, xop, epi);
-    if constexpr (FUSED) {
-        __shared__ double red[32];
-        double tot = 0.0;
-        if (last_block_sum(&m.st->ticket, m.part, a.ntiles, red, &tot) && threadIdx.x == 0)
-            mrs_step(m.st, tot, cond, 1);
-    }
+    if constexpr (FUSED) mrs_fused_tail(m.st, m.part, a.ntiles, cond);
 }
 
 // Piece sums of a long row in the row's entry order: its np full pieces
