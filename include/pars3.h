@@ -212,12 +212,14 @@ int pars3_upload(pars3_handle *h, void *stream);
 
 /* pars3_spmv -- y = (alpha I + P S P^T) x for x, y of n entries in the
  * handle's numbering: fp64 vectors for PARS3_F64, fp32 for PARS3_F32 and
- * PARS3_BF16.  Two kernels: the tile kernel (one block per row tile: TMA
- * staging of the x window [tT-W, tT+T), the half-storage middle entries with
- * their in-tile mirrored sums in shared memory, the full-storage outer rows,
- * chunked long rows) and the fold kernel (cross-tile halo sums and long-row
- * partial sums, fixed order).  x and y must not overlap.  Errors: EINVAL,
- * ESTATE (not uploaded), EUNSUPPORTED (precision not packed), ECUDA. */
+ * PARS3_BF16.  Two kernels: the tile kernel (blocks that sum the pieces of
+ * long rows, then one block per row tile: TMA staging of the x window
+ * [tT-W, tT+T) and of the half-storage middle entries with their in-tile
+ * mirrored sums in shared memory, the full-storage outer rows) and the fold
+ * kernel (cross-tile halo sums and long-row piece sums, fixed order).  x and
+ * y must not overlap.  The call only enqueues work: a failure inside a
+ * kernel shows in pars3_check.  Errors: EINVAL, ESTATE (not uploaded),
+ * EUNSUPPORTED (precision not packed), ECUDA. */
 int pars3_spmv(const pars3_handle *h, int32_t dtype, double alpha, const void *x, void *y,
                void *stream);
 
@@ -276,7 +278,10 @@ int pars3_spmv_host(pars3_handle *h, int32_t dtype, double alpha, const void *x_
  * library-wide device array of 4 MiB that every GPU loading the library
  * holds until the process exits; the call allocates nothing.  The array's
  * device address is looked up on the first call with a given device
- * current, and that first call should come before any stream capture.
+ * current.  CUDA loads a library's device code lazily by default, so that
+ * first call may also load the code that holds the array, which reserves
+ * its 4 MiB on that device then: make the first call on each device before
+ * any stream capture and before any memory budget takes effect.
  * Every call shares the array (its contents are overwritten before they
  * are read), so calls that overlap on the GPU race.  Returns
  * PARS3_EUNSUPPORTED when the handle needs more scratch than the array
@@ -286,7 +291,12 @@ int pars3_spmv_noalloc(const pars3_handle *h, int32_t dtype, double alpha, const
                        void *stream);
 
 /* Reads and clears the handle's device error word (synchronizes the
- * stream).  Returns PARS3_OK, PARS3_ETIMEOUT or PARS3_ECUDA. */
+ * stream).  Returns PARS3_OK, PARS3_ETIMEOUT or PARS3_ECUDA.  PARS3_ETIMEOUT
+ * means a bounded device-side wait for a staged copy gave up (about a
+ * second) in some call since the last check: the outputs of the tiles
+ * concerned were written as NaN and the results of those calls are invalid
+ * (a copy still in flight may also have landed in a later block's shared
+ * memory, so treat every result since the last PARS3_OK as invalid). */
 int pars3_check(const pars3_handle *h, void *stream);
 
 /* pars3_autotune -- times pars3_spmm (k right-hand sides) on the current

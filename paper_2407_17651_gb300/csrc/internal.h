@@ -12,7 +12,7 @@ namespace pars3 {
 constexpr int kNumDtypes = 3;
 constexpr int kAlignHalf = 8;          // half-path tile segments start on 16-byte boundaries (u16, bf16)
 constexpr int kAlignFull = 16;         // full-path tile segments: 64 B for int32 columns, 128 B for fp64
-constexpr int kBlock = 512;            // threads of the tile kernel (one block per row tile or long chunk)
+constexpr int kBlock = 512;            // threads of the tile kernel (a row tile or a set of long-row slices)
 constexpr int kPieceLen = 192;         // default entries per long-row piece
 constexpr int kPieceMax = 255;         // longest piece the layout allows
 constexpr int kLongSlices = 32;        // long-row slices per block

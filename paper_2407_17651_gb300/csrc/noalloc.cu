@@ -15,7 +15,10 @@
 // Host code cannot use the array's name as a device address (it names a
 // host-side stand-in), so the address is looked up with
 // cudaGetSymbolAddress, once per device, on the first call made with that
-// device current; that first call should come before any stream capture.
+// device current.  With CUDA's default lazy loading that lookup may also
+// load this file's device code and so reserve the array on the device: the
+// first call on each device should come before any stream capture and
+// before any memory budget applies.
 // Every call shares the array and leaves its contents behind: the kernels
 // overwrite every scratch entry before reading it, so nothing needs
 // clearing, but two calls that overlap on the GPU (different streams, no

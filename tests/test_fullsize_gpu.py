@@ -122,3 +122,21 @@ def test_cfg4_batched_autotuned(dtype, k):
         y = np.empty_like(ref)
         y[p] = Y.double().cpu().numpy()
         assert np.all(np.abs(y - ref) <= TAU[dtype] * bound + 1e-30)
+
+
+@pytest.mark.parametrize("dtype,k", [(P.F32, 4), (P.F64, 4), (P.F32, 32)], ids=["f32k4", "f64k4", "f32k32"])
+def test_cfg2_spmm_long_rows(dtype, k):
+    """The multi-vector product on the R-MAT matrix: its power-law rows are
+    summed in k-wide pieces (long_row = 32, pieces of 255, the autotuner's
+    usual choice there); every entry of Y against the fp64 oracle on the
+    original X."""
+    A, alpha, x = W.config2()
+    perm = P.pars3_reorder(A.n, A.rowptr, A.col)[0]
+    h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=2048, W=32, long_row=32, piece=255, long_slices=16,
+                      dtypes=P.dtype_bit(dtype))
+    P.pars3_upload(h)
+    info = P.pars3_info_get(h)
+    assert info["long_rows"] > 100000 and info["long_pieces"] > info["long_rows"]
+    X = W.vector("uniform", (A.n, k), 77)
+    compare(A, perm, h, dtype, 0.5, X, O.Full(A))
+    h.close()
