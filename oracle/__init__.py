@@ -178,15 +178,17 @@ def bandwidth(A, perm=None) -> int:
     return int(_L().orc_bandwidth(A.n, _p(rp), _p(ci), None if p is None else _p(p)))
 
 
-def rcm(A, guard: bool = True, peripheral: bool = False):
+def rcm(A, guard: bool = True, peripheral: bool = False, local: bool = False):
     """(perm new->old, bandwidth before, bandwidth after); peripheral: start
-    each component at a George-Liu pseudo-peripheral vertex."""
+    each component at a George-Liu pseudo-peripheral vertex; local: RCM of the
+    pattern's local edges only, those on a triangle or a 4-cycle
+    (orc_rcm_local)."""
     rp, ci, _ = _csr(A)
     perm = np.empty(A.n, dtype=np.int32)
     b0 = np.zeros(1, dtype=np.int64)
     b1 = np.zeros(1, dtype=np.int64)
-    rc = _L().orc_rcm(A.n, _p(rp), _p(ci), (1 if guard else 0) | (2 if peripheral else 0), _p(perm), _p(b0),
-                      _p(b1))
+    flags = (1 if guard else 0) | (2 if peripheral else 0) | (4 if local else 0)
+    rc = _L().orc_rcm(A.n, _p(rp), _p(ci), flags, _p(perm), _p(b0), _p(b1))
     if rc != 0:
         raise RuntimeError(f"orc_rcm failed ({rc})")
     return perm, int(b0[0]), int(b1[0])

@@ -230,13 +230,110 @@ static int32_t orc_pseudo_peripheral(const int64_t *arp, const int32_t *adj, con
     }
 }
 
+static int cmp_i32(const void *pa, const void *pb)
+{
+    int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+int orc_rcm(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flags,
+            int32_t *perm, int64_t *bw_before, int64_t *bw_after);
+
+/* 1 when v is in the sorted list adj[lo .. hi) */
+static int orc_in_sorted(const int32_t *adj, int64_t lo, int64_t hi, int32_t v)
+{
+    const int64_t end = hi;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (adj[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < end && adj[lo] == v ? 1 : 0;
+}
+
+/* Local-edge RCM (flags bit 2), a reordering for small-world patterns, where
+ * a few long-range "shortcut" edges make every breadth-first level huge (the
+ * paper notes that RCM's benefit depends on the pattern, Sec. 4.1, Fig. 5):
+ * RCM, with the caller's start rule, of the pattern restricted to its local
+ * edges.  An edge {u, v} is local when it lies on a triangle or a 4-cycle
+ * (u and v have a common neighbour, or a neighbour a of u other than v is
+ * adjacent to a neighbour b of v other than u and a), or when deg(u) deg(v) >
+ * ORC_LOCAL_DEG (then it is kept untested).  The other edges stay in the
+ * matrix; only the ordering ignores them.  The guard is applied by the
+ * caller to the final order over all edges. */
+#define ORC_LOCAL_DEG 4096
+static int orc_rcm_local(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flags, int32_t *perm)
+{
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    int64_t m = rp[n];
+    int64_t *arp = (int64_t *)calloc(nn + 1, sizeof(int64_t));
+    int32_t *adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
+    int64_t *fill = (int64_t *)calloc(nn, sizeof(int64_t));
+    int32_t *rp2 = (int32_t *)malloc(sizeof(int32_t) * (nn + 1));
+    int32_t *ci2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    if (!arp || !adj || !fill || !rp2 || !ci2) {
+        free(arp); free(adj); free(fill); free(rp2); free(ci2);
+        return ORC_ENOMEM;
+    }
+    /* sorted adjacency lists of the symmetric pattern */
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) { arp[i + 1]++; arp[ci[k] + 1]++; }
+    for (int32_t i = 0; i < n; i++) arp[i + 1] += arp[i];
+    for (int32_t i = 0; i < n; i++) fill[i] = arp[i];
+    for (int32_t i = 0; i < n; i++)
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+            adj[fill[i]++] = ci[k];
+            adj[fill[ci[k]]++] = i;
+        }
+    for (int32_t i = 0; i < n; i++) qsort(adj + arp[i], (size_t)(arp[i + 1] - arp[i]), sizeof(int32_t), cmp_i32);
+    /* the local edges, in the order of the input */
+    int32_t q = 0;
+    rp2[0] = 0;
+    for (int32_t u = 0; u < n; u++) {
+        for (int32_t k = rp[u]; k < rp[u + 1]; k++) {
+            int32_t v = ci[k];
+            int64_t du = arp[u + 1] - arp[u], dv = arp[v + 1] - arp[v];
+            int local = du * dv > ORC_LOCAL_DEG;
+            for (int64_t x = arp[u]; !local && x < arp[u + 1]; x++) {
+                int32_t a = adj[x];
+                if (a == v) continue;
+                if (orc_in_sorted(adj, arp[v], arp[v + 1], a)) { local = 1; break; }      /* triangle */
+                for (int64_t y = arp[v]; y < arp[v + 1]; y++) {
+                    int32_t b = adj[y];
+                    if (b == u || b == a) continue;
+                    if (orc_in_sorted(adj, arp[a], arp[a + 1], b)) { local = 1; break; } /* 4-cycle */
+                }
+            }
+            if (local) ci2[q++] = v;
+        }
+        rp2[u + 1] = q;
+    }
+    int rc = orc_rcm(n, rp2, ci2, flags & 2, perm, NULL, NULL);
+    free(arp); free(adj); free(fill); free(rp2); free(ci2);
+    return rc;
+}
+
 /* flags: bit 0 (1) the identity guard, bit 1 (2) start each component at a
- * pseudo-peripheral vertex found from the (degree, index) candidate. */
+ * pseudo-peripheral vertex found from the (degree, index) candidate, bit 2
+ * (4) RCM of the local edges only (orc_rcm_local). */
 int orc_rcm(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flags,
             int32_t *perm, int64_t *bw_before, int64_t *bw_after)
 {
     const int32_t guard = flags & 1, peripheral = flags & 2;
     if (n < 0) return ORC_EINVAL;
+    if (flags & 4) {
+        int rc = orc_rcm_local(n, rp, ci, flags, perm);
+        if (rc != ORC_OK) return rc;
+        int64_t b0 = orc_bandwidth(n, rp, ci, NULL);
+        int64_t b1 = orc_bandwidth(n, rp, ci, perm);
+        if (guard && b1 > b0) {
+            for (int32_t k = 0; k < n; k++) perm[k] = k;
+            b1 = b0;
+        }
+        if (bw_before) *bw_before = b0;
+        if (bw_after) *bw_after = b1;
+        return ORC_OK;
+    }
     size_t nn = (size_t)(n > 0 ? n : 1);
     int64_t nnz = rp[n];
     int64_t *arp = (int64_t *)calloc(nn + 1, sizeof(int64_t));
