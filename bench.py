@@ -202,10 +202,10 @@ def extra_section(args, peak):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     both = P.dtype_bit(P.F64) | P.dtype_bit(P.F32)
 
-    def single(name, A, alpha, x, desc, symmetric=False, precisions=("f64", "f32")):
+    def single(name, A, alpha, x, desc, symmetric=False, precisions=("f64", "f32"), reorder_flags=P.RCM_GUARD):
         """Split parameters autotuned separately for each precision."""
         t0 = time.perf_counter()
-        perm, bw0, bw1 = P.pars3_reorder(A.n, A.rowptr, A.col)
+        perm, bw0, bw1 = P.pars3_reorder(A.n, A.rowptr, A.col, reorder_flags)
         t_rcm = time.perf_counter() - t0
         row = {"workload": desc, "n": A.n, "nnz_stored": A.nnz, "alpha": alpha, "rcm_bandwidth": bw1,
                "rcm_s": t_rcm}
@@ -252,6 +252,11 @@ def extra_section(args, peak):
     A, alpha, x = W.config1()
     single("cfg1", A, alpha, x, "grid3d 128^3 + 1% random long-range edges, N(0,1), alpha=0.5")
     out["cfg1"]["section_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    single("cfg1_local_rcm", A, alpha, x, "the 128^3 + 1% matrix ordered by the RCM of its local edges "
+           "(PARS3_RCM_LOCAL: the random long-range edges do not steer the ordering), alpha=0.5",
+           reorder_flags=P.RCM_GUARD | P.RCM_LOCAL)
+    out["cfg1_local_rcm"]["section_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     single("cfg1_symmetric", A, alpha, x, "the 128^3 + 1% matrix as the symmetric S = L + L^T "
            "(PARS3_SPLIT_SYMMETRIC), alpha=0.5", symmetric=True)
@@ -505,6 +510,8 @@ def main():
     ap.add_argument("--k", type=int, default=1, help="right-hand sides (k > 1 times pars3_spmm on an n x k block)")
     ap.add_argument("--T", type=int, default=-1, help="tile rows (default: pars3_autotune)")
     ap.add_argument("--W", type=int, default=-1, help="middle bandwidth (with --T)")
+    ap.add_argument("--split", default="", help="split parameters as JSON (the keys of an autotune result); "
+                                                "skips the autotuner, e.g. to profile a known choice")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-spmvs", type=int, default=10)
@@ -536,7 +543,10 @@ def main():
     perm, bw0, bw1 = P.pars3_reorder(A.n, A.rowptr, A.col)
     t_rcm = time.perf_counter() - t0
     t_tune = None
-    if args.T >= 0:
+    if args.split:
+        split_kw = dict(json.loads(args.split))
+        split_kw.setdefault("dtypes", P.dtype_bit(dt))
+    elif args.T >= 0:
         split_kw = dict(T=args.T, W=args.W, dtypes=P.dtype_bit(dt))
     else:   # split parameters from the autotuner (untimed preprocessing)
         t0 = time.perf_counter()

@@ -72,6 +72,10 @@ extern "C" {
                                   vertex (from the (degree, index) candidate, move to the smallest
                                   (degree, index) vertex of the last BFS level while that strictly
                                   increases the eccentricity) */
+#define PARS3_RCM_LOCAL 4 /* pars3_reorder: order by the RCM of the local edges only -- those on a
+                             triangle or a 4-cycle, plus those between two vertices whose degree
+                             product exceeds 4096 -- so that the random long-range "shortcut" edges
+                             of a small-world pattern do not steer it (they stay in the matrix) */
 #define PARS3_SPLIT_SYMMETRIC 1 /* pars3_split_params.flags: S = L + L^T (the symmetric variant the
                                    paper's method also covers, abstract and Sec. 5) instead of the
                                    skew-symmetric S = L - L^T */
@@ -177,9 +181,11 @@ int pars3_version(int32_t *major, int32_t *minor, int32_t *cuda_arch);
  * (degree, index) order; the whole visit order is reversed.  perm_out[n]
  * (caller-allocated) receives new -> old.  With PARS3_RCM_GUARD the identity
  * is returned when the RCM bandwidth would exceed the original (Sec. 4.1:
- * already banded matrices gain nothing).  bw_before/bw_after may be NULL.
- * Errors: EINVAL (n < 0, null pointer), ENOTSKEW (pattern not strict lower),
- * ENOMEM. */
+ * already banded matrices gain nothing).  PARS3_RCM_PERIPHERAL and
+ * PARS3_RCM_LOCAL select the variants described at the flags (both may be
+ * combined with the guard; bandwidths and the guard always count every
+ * stored entry).  bw_before/bw_after may be NULL.  Errors: EINVAL (n < 0,
+ * null pointer, unknown flag), ENOTSKEW (pattern not strict lower), ENOMEM. */
 int pars3_reorder(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t flags,
                   int32_t *perm_out, int64_t *bw_before, int64_t *bw_after);
 

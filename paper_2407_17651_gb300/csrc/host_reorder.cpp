@@ -168,6 +168,64 @@ static int rcm_core(int32_t n, const int32_t *rowptr, const int32_t *col, bool p
 
 }  // namespace pars3
 
+// The local edges of the pattern (PARS3_RCM_LOCAL): a stored {u, v} is local
+// when it lies on a triangle or a 4-cycle, or when deg(u) deg(v) exceeds
+// kLocalDeg (then it is kept untested).  Output: strict-lower CSR of the local
+// edges, in the input's order.  Neighbour lists are index-sorted for free:
+// the lower neighbours of u (its stored columns) precede its upper ones (the
+// rows that store u, in increasing order).
+constexpr int64_t kLocalDeg = 4096;
+static void local_edges(int32_t n, const int32_t *rowptr, const int32_t *col, std::vector<int32_t> &rp2,
+                        std::vector<int32_t> &ci2) {
+    const int64_t nnz = rowptr[n];
+    std::vector<int64_t> tptr(static_cast<size_t>(n) + 1, 0);
+    for (int64_t k = 0; k < nnz; ++k) ++tptr[col[k] + 1];
+    for (int32_t i = 0; i < n; ++i) tptr[i + 1] += tptr[i];
+    std::vector<int32_t> trow(static_cast<size_t>(nnz));
+    {
+        std::vector<int64_t> fill(tptr.begin(), tptr.end() - 1);
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) trow[fill[col[k]]++] = i;
+    }
+    std::vector<int64_t> aptr(static_cast<size_t>(n) + 1, 0);
+    for (int32_t i = 0; i < n; ++i)
+        aptr[i + 1] = aptr[i] + (rowptr[i + 1] - rowptr[i]) + (tptr[i + 1] - tptr[i]);
+    std::vector<int32_t> adj(static_cast<size_t>(2 * nnz));
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t q = aptr[i];
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) adj[q++] = col[k];
+        for (int64_t k = tptr[i]; k < tptr[i + 1]; ++k) adj[q++] = trow[k];
+    }
+    auto has = [&](int32_t a, int32_t b) {
+        return std::binary_search(adj.begin() + aptr[a], adj.begin() + aptr[a + 1], b);
+    };
+    rp2.assign(static_cast<size_t>(n) + 1, 0);
+    ci2.clear();
+    for (int32_t u = 0; u < n; ++u) {
+        for (int32_t k = rowptr[u]; k < rowptr[u + 1]; ++k) {
+            const int32_t v = col[k];
+            bool local = (aptr[u + 1] - aptr[u]) * (aptr[v + 1] - aptr[v]) > kLocalDeg;
+            for (int64_t x = aptr[u]; !local && x < aptr[u + 1]; ++x) {   // triangles
+                const int32_t a = adj[x];
+                local = a != v && has(v, a);
+            }
+            for (int64_t x = aptr[u]; !local && x < aptr[u + 1]; ++x) {   // 4-cycles u-a-b-v
+                const int32_t a = adj[x];
+                if (a == v) continue;
+                for (int64_t y = aptr[v]; y < aptr[v + 1]; ++y) {
+                    const int32_t b = adj[y];
+                    if (b != u && b != a && has(a, b)) {
+                        local = true;
+                        break;
+                    }
+                }
+            }
+            if (local) ci2.push_back(v);
+        }
+        rp2[u + 1] = static_cast<int32_t>(ci2.size());
+    }
+}
+
 extern "C" int pars3_reorder(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t flags,
                              int32_t *perm_out, int64_t *bw_before, int64_t *bw_after) {
     using namespace pars3;
@@ -175,8 +233,14 @@ extern "C" int pars3_reorder(int32_t n, const int32_t *rowptr, const int32_t *co
     int rc = validate_lower(n, rowptr, col);
     if (rc != PARS3_OK) return rc;
     try {
-        if (flags & ~(PARS3_RCM_GUARD | PARS3_RCM_PERIPHERAL)) return PARS3_EINVAL;
-        rc = rcm_core(n, rowptr, col, (flags & PARS3_RCM_PERIPHERAL) != 0, perm_out);
+        if (flags & ~(PARS3_RCM_GUARD | PARS3_RCM_PERIPHERAL | PARS3_RCM_LOCAL)) return PARS3_EINVAL;
+        if (flags & PARS3_RCM_LOCAL) {
+            std::vector<int32_t> rp2, ci2;
+            local_edges(n, rowptr, col, rp2, ci2);
+            rc = rcm_core(n, rp2.data(), ci2.data(), (flags & PARS3_RCM_PERIPHERAL) != 0, perm_out);
+        } else {
+            rc = rcm_core(n, rowptr, col, (flags & PARS3_RCM_PERIPHERAL) != 0, perm_out);
+        }
         if (rc != PARS3_OK) return rc;
         std::vector<int32_t> pinv(n);
         for (int32_t k = 0; k < n; ++k) pinv[perm_out[k]] = k;

@@ -18,6 +18,7 @@ from . import _build
 F64, F32, BF16 = 0, 1, 2
 RCM_GUARD = 1
 RCM_PERIPHERAL = 2
+RCM_LOCAL = 4
 SPLIT_SYMMETRIC = 1
 VARIANT_LOOKAHEAD = 1
 

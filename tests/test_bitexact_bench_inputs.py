@@ -63,6 +63,10 @@ def test_rcm_and_split_bit_exact_full_size(name):
     perm = _assert_rcm_equal(A, P.RCM_GUARD, True, False)
     _assert_rcm_equal(A, 0, False, False)
     _assert_rcm_equal(A, P.RCM_GUARD | P.RCM_PERIPHERAL, True, True)
+    if name == "cfg1":   # the local-edge variant the benchmark also reports on this matrix
+        pl, b0, b1 = P.pars3_reorder(A.n, A.rowptr, A.col, P.RCM_GUARD | P.RCM_LOCAL)
+        po, ob0, ob1 = O.rcm(A, guard=True, local=True)
+        assert np.array_equal(pl, po) and (b0, b1) == (ob0, ob1)
     cuts = [(2048, 32), (1024, 32)] if name == "cfg2" else [(2048, 32)]
     for T, Wc in cuts:
         _assert_split_equal(A, perm, T, Wc)

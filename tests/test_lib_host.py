@@ -54,6 +54,27 @@ def test_rcm_bit_exact(idx):
         assert (b0, b1) == (ob0, ob1)
 
 
+@pytest.mark.parametrize("idx", range(9))
+def test_local_rcm_bit_exact(idx):
+    """PARS3_RCM_LOCAL (with and without the guard and pseudo-peripheral
+    starts) against the oracle's local-edge RCM."""
+    A = list(_mats())[idx]
+    for flags in (P.RCM_LOCAL, P.RCM_LOCAL | P.RCM_GUARD, P.RCM_LOCAL | P.RCM_PERIPHERAL,
+                  P.RCM_LOCAL | P.RCM_GUARD | P.RCM_PERIPHERAL):
+        perm, b0, b1 = P.pars3_reorder(A.n, A.rowptr, A.col, flags)
+        po, ob0, ob1 = O.rcm(A, guard=bool(flags & P.RCM_GUARD), peripheral=bool(flags & P.RCM_PERIPHERAL),
+                             local=True)
+        assert np.array_equal(perm, po), flags
+        assert (b0, b1) == (ob0, ob1)
+
+
+def test_unknown_reorder_flag_rejected():
+    A = W.grid((10, 10), "uniform", 1)
+    with pytest.raises(P.Pars3Error) as e:
+        P.pars3_reorder(A.n, A.rowptr, A.col, 8)
+    assert e.value.code == P.EINVAL
+
+
 def test_rcm_bit_exact_config0_and_hand_example():
     A, _, _ = W.config0()
     perm, b0, b1 = P.pars3_reorder(A.n, A.rowptr, A.col)

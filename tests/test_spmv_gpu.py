@@ -174,3 +174,23 @@ def test_fp64_fma_rate_probe():
     r2 = P.pars3_fp64_fma_rate()
     assert 5e10 < r1 < 1e13 and 5e10 < r2 < 1e13
     assert 0.5 < r1 / r2 < 2.0
+
+
+def test_product_with_local_rcm_order():
+    """A grid with shortcuts ordered by PARS3_RCM_LOCAL: the product in that
+    numbering matches the oracle (fp64 and fp32)."""
+    A = W.grid_plus_random((40, 30, 8), 0.01, "normal", 41)
+    perm = P.pars3_reorder(A.n, A.rowptr, A.col, P.RCM_GUARD | P.RCM_LOCAL)[0]
+    F = O.Full(A)
+    x = W.vector("uniform", A.n, 42)
+    for dtype, tau in ((P.F64, 1e-12), (P.F32, 2e-6)):
+        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, T=1024, W=64, dtypes=P.dtype_bit(dtype))
+        P.pars3_upload(h)
+        vt = torch.float64 if dtype == P.F64 else torch.float32
+        xp = torch.from_numpy(x[perm]).to("cuda", vt)
+        y = torch.full_like(xp, float("nan"))
+        P.pars3_spmv(h, dtype, 0.5, xp, y)
+        torch.cuda.synchronize()
+        ref = F.apply(0.5, x)[perm]
+        assert np.all(np.abs(y.double().cpu().numpy() - ref) <= tau * F.abs_bound(0.5, x)[perm] + 1e-30)
+        h.close()
