@@ -78,7 +78,31 @@ __global__ void __launch_bounds__(256) batched_fold_kernel(const FoldArgs *__res
                                                            const AT *const *__restrict__ halos,
                                                            const AT *const *__restrict__ lparts,
                                                            XT *const *__restrict__ ys, const int64_t *__restrict__ fpre,
-                                                           int count, int64_t total, int k) {
+                                                           int count, int64_t total, int k,
+                                                           const int2 *__restrict__ heavy, int nheavy) {
+    // heavy (matrix, row, column) items first, a warp each, as in the
+    // single-matrix folds
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t w = gw; w < static_cast<int64_t>(nheavy) * k; w += nw) {
+        const int2 mf = heavy[w / k];
+        const int c = static_cast<int>(w % k);
+        const FoldLists &F = fa[mf.x].F;
+        const int f = mf.y;
+        const AT s = heavy_pieces_warp<AT>(F.p0[f], F.np[f], lparts[mf.x], k, c);
+        if (lane == 0) {
+            const int64_t r = F.row[f];
+            XT *y = ys[mf.x];
+            AT v = static_cast<AT>(y[r * k + c]);
+            const int hh = F.halo[f];
+            if (hh >= 0) v += halos[mf.x][static_cast<int64_t>(hh) * k + c];
+            v += s;
+            const int rem = F.rem[f];
+            if (rem >= 0) v += lparts[mf.x][static_cast<int64_t>(rem) * k + c];
+            y[r * k + c] = static_cast<XT>(v);
+        }
+    }
     for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
          q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         int lo = 0, hi = count;
@@ -91,6 +115,7 @@ __global__ void __launch_bounds__(256) batched_fold_kernel(const FoldArgs *__res
         const int64_t local = q - fpre[m];
         const int f = static_cast<int>(local / k), c = static_cast<int>(local - static_cast<int64_t>(f) * k);
         const FoldArgs F = fa[m];
+        if (F.F.np[f] >= kFoldHeavy) continue;
         const int64_t r = F.F.row[f];
         XT *y = ys[m];
         AT v = static_cast<AT>(y[r * k + c]);
@@ -110,14 +135,15 @@ struct BatchCache {
     std::vector<void *> Y;
     int dtype = -1, k = 0;
     void *args = nullptr, *upre = nullptr, *fa = nullptr, *halos = nullptr, *lparts = nullptr, *ys = nullptr,
-         *fpre = nullptr;
+         *fpre = nullptr, *heavy = nullptr;
+    int nheavy = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t capture = nullptr;
     void release() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
-        for (void *p : {args, upre, fa, halos, lparts, ys, fpre})
+        for (void *p : {args, upre, fa, halos, lparts, ys, fpre, heavy})
             if (p) cudaFree(p);
         if (capture) cudaStreamDestroy(capture);
         *this = BatchCache();
@@ -162,7 +188,8 @@ static int enqueue(BatchCache &C, int count, int64_t total_units, int64_t total_
         batched_fold_kernel<XT, AT><<<blocks, 256, 0, st>>>(
             static_cast<const FoldArgs *>(C.fa), static_cast<const AT *const *>(C.halos),
             static_cast<const AT *const *>(C.lparts), static_cast<XT *const *>(C.ys),
-            static_cast<const int64_t *>(C.fpre), count, total_fold, k);
+            static_cast<const int64_t *>(C.fpre), count, total_fold, k, static_cast<const int2 *>(C.heavy),
+            C.nheavy);
     }
     return cuda_status(cudaGetLastError());
 }
@@ -208,13 +235,15 @@ static int run_batched(BatchCache &C, pars3_handle *const *hs, int count, int dt
         C.release();
         std::vector<SpmvArgs<VT, XT, AT>> args;
         std::vector<FoldArgs> fa;
+        std::vector<int2> heavy;
         std::vector<const void *> halos, lparts;
         std::vector<void *> ys;
         for (int m = 0; m < count; ++m) {
             const pars3_handle *h = hs[m];
             args.push_back(make_args<VT, XT, AT>(h, dtype, alpha[m], X[m], Y[m]));
             const DevLayout &D = h->D;
-            fa.push_back(FoldArgs{static_cast<int32_t>(h->L.fold_row.size()), fold_lists(D)});
+            fa.push_back(FoldArgs{static_cast<int32_t>(h->L.fold_row.size()), fold_lists(D, h->L)});
+            for (int32_t f : h->L.fold_heavy) heavy.push_back(make_int2(m, f));
             halos.push_back(D.halo);
             lparts.push_back(D.lpart);
             ys.push_back(Y[m]);
@@ -227,6 +256,8 @@ static int run_batched(BatchCache &C, pars3_handle *const *hs, int count, int dt
         if ((rc = upload_vec(&C.lparts, lparts)) != PARS3_OK) return rc;
         if ((rc = upload_vec(&C.ys, ys)) != PARS3_OK) return rc;
         if ((rc = upload_vec(&C.fpre, fpre)) != PARS3_OK) return rc;
+        if ((rc = upload_vec(&C.heavy, heavy)) != PARS3_OK) return rc;
+        C.nheavy = static_cast<int>(heavy.size());
         for (int m = 0; m < count; ++m) C.serial.push_back(hs[m]->serial);
         C.alpha.assign(alpha, alpha + count);
         C.X.assign(X, X + count);

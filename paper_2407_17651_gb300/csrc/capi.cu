@@ -95,6 +95,7 @@ static int upload_impl(pars3_handle *h, cudaStream_t st) {
     UP(D.fold_p0, L.fold_p0);
     UP(D.fold_np, L.fold_np);
     UP(D.fold_rem, L.fold_rem);
+    UP(D.fold_heavy, L.fold_heavy);
     UP(D.perm, h->perm);
     if (h->dtypes & PARS3_DTYPE_BIT(PARS3_F64)) {
         double *a, *b, *c;

@@ -500,6 +500,7 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
                 L.fold_p0.push_back(l >= 0 ? L.lp0[l] : 0);
                 L.fold_np.push_back(l >= 0 ? L.lp0[l + 1] - L.lp0[l] : 0);
                 L.fold_rem.push_back(l >= 0 ? L.lrem[l] : -1);
+                if (L.fold_np.back() >= kFoldHeavy) L.fold_heavy.push_back(static_cast<int32_t>(L.fold_row.size()) - 1);
             }
     }
     // ---- 7. values per precision
@@ -871,6 +872,16 @@ extern "C" int pars3_layout_check(const pars3_handle *h) {
             }
         }
         if (nh != L.hhrow.size() || nl != L.lrow.size()) return PARS3_EINVAL;
+        // the heavy list: exactly the items of at least kFoldHeavy full pieces, in order
+        {
+            size_t q = 0;
+            for (size_t f = 0; f < L.fold_row.size(); ++f)
+                if (L.fold_np[f] >= kFoldHeavy) {
+                    if (q >= L.fold_heavy.size() || L.fold_heavy[q] != static_cast<int32_t>(f)) return PARS3_EINVAL;
+                    ++q;
+                }
+            if (q != L.fold_heavy.size()) return PARS3_EINVAL;
+        }
     } catch (const std::bad_alloc &) {
         return PARS3_ENOMEM;
     }

@@ -21,6 +21,7 @@ constexpr int kSellMax = 128;          // longer full-path rows go to the long p
 constexpr int kHalfMinFrac = 4;        // a tile keeps its middle entries on the half path only when they
                                        // are at least 1/kHalfMinFrac of its stored entries
 constexpr int kHalfMinShare = 16;      // ... and the half path only when it holds 1/kHalfMinShare of all
+constexpr int kFoldHeavy = 64;         // long rows of at least this many full pieces are folded by a warp
 constexpr int kSlice = 32;             // rows per sliced-ELL slice (one warp)
 constexpr int kSmemLimit = 227 * 1024; // opt-in shared memory per block on sm_100/sm_103
 
@@ -73,6 +74,7 @@ struct Layout {
     // sums: its halo index (or -1), its full pieces fold_p0 .. fold_p0 +
     // fold_np - 1 and its last piece fold_rem (or -1)
     std::vector<int32_t> fold_row, fold_halo, fold_p0, fold_np, fold_rem;
+    std::vector<int32_t> fold_heavy;   // the fold items with at least kFoldHeavy full pieces
     // values per precision (fp64 / fp32 / bf16 bits)
     std::vector<double> hval64, fval64, lval64;
     std::vector<float> hval32, fval32, lval32;
@@ -100,7 +102,7 @@ struct DevLayout {
     uint16_t *ls_len = nullptr;
     int32_t *lcol = nullptr;
     int32_t *fold_row = nullptr, *fold_halo = nullptr, *fold_p0 = nullptr, *fold_np = nullptr,
-            *fold_rem = nullptr;
+            *fold_rem = nullptr, *fold_heavy = nullptr;
     void *hval[kNumDtypes] = {nullptr, nullptr, nullptr};
     void *fval[kNumDtypes] = {nullptr, nullptr, nullptr};
     void *lval[kNumDtypes] = {nullptr, nullptr, nullptr};

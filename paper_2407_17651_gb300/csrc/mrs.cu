@@ -49,11 +49,29 @@ __global__ void __launch_bounds__(kRedBlock) fold_mrs_kernel(
     XT *y = m.w[j % 3];
     const AT scale = static_cast<AT>(st->e_scale);   // 1 / beta_{j-1}
     double nrm = 0.0;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int w = gw; w < F.nheavy; w += nw) {   // heavy rows, a warp each (as in the plain fold)
+        const int f = __ldg(F.heavy + w);
+        const AT sp = heavy_pieces_warp<AT>(__ldg(F.p0 + f), __ldg(F.np + f), lpart, 1, 0);
+        if (lane == 0) {
+            const int r = __ldg(F.row + f), hi = __ldg(F.halo + f), rem = __ldg(F.rem + f);
+            AT s = AT(0);
+            if (hi >= 0) s += halo[hi];
+            s += sp;
+            if (rem >= 0) s += lpart[rem];
+            const XT wx = static_cast<XT>(static_cast<AT>(y[r]) + s * scale);
+            y[r] = wx;
+            nrm += static_cast<double>(wx) * static_cast<double>(wx);
+        }
+    }
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nitems; f += gridDim.x * blockDim.x) {
+        const int np = __ldg(F.np + f);
+        if (np >= kFoldHeavy) continue;
         const int r = __ldg(F.row + f), hi = __ldg(F.halo + f);
         AT s = AT(0);
         if (hi >= 0) s += halo[hi];
-        s = long_row_sum<AT>(__ldg(F.p0 + f), __ldg(F.np + f), __ldg(F.rem + f), lpart, 1, 0, s);
+        s = long_row_sum<AT>(__ldg(F.p0 + f), np, __ldg(F.rem + f), lpart, 1, 0, s);
         const XT wx = static_cast<XT>(static_cast<AT>(y[r]) + s * scale);
         y[r] = wx;
         nrm += static_cast<double>(wx) * static_cast<double>(wx);
@@ -313,7 +331,7 @@ static int build_graph(pars3_handle *h, int dtype, MrsWork &W) {
         else tile_kernel_mrs<VT, XT, AT, false, false><<<grid, kBlock, smem, W.capture>>>(a, m, G.cond);
         if (!fused)
             fold_mrs_kernel<XT, AT><<<fold_blocks(h), kRedBlock, 0, W.capture>>>(
-                static_cast<int>(L.fold_row.size()), fold_lists(D), static_cast<const AT *>(D.halo),
+                static_cast<int>(L.fold_row.size()), fold_lists(D, L), static_cast<const AT *>(D.halo),
                 static_cast<const AT *>(D.lpart),
                 m, h->ntiles, G.cond, 1);
     }

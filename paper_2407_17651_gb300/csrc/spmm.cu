@@ -26,15 +26,33 @@ template <typename XT, typename AT>
 __global__ void __launch_bounds__(256) fold_spmm_kernel(int nitems, int k, const FoldLists F,
                                                         const AT *__restrict__ halo, const AT *__restrict__ lpart,
                                                         XT *__restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t w = gw; w < static_cast<int64_t>(F.nheavy) * k; w += nw) {   // heavy (row, column), a warp each
+        const int f = __ldg(F.heavy + w / k), c = static_cast<int>(w % k);
+        const AT s = heavy_pieces_warp<AT>(__ldg(F.p0 + f), __ldg(F.np + f), lpart, k, c);
+        if (lane == 0) {
+            const int64_t r = __ldg(F.row + f);
+            const int hi = __ldg(F.halo + f), rem = __ldg(F.rem + f);
+            AT v = static_cast<AT>(y[r * k + c]);
+            if (hi >= 0) v += halo[static_cast<int64_t>(hi) * k + c];
+            v += s;
+            if (rem >= 0) v += lpart[static_cast<int64_t>(rem) * k + c];
+            y[r * k + c] = static_cast<XT>(v);
+        }
+    }
     const int64_t total = static_cast<int64_t>(nitems) * k;
     for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
          q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int f = static_cast<int>(q / k), c = static_cast<int>(q - static_cast<int64_t>(f) * k);
+        const int np = __ldg(F.np + f);
+        if (np >= kFoldHeavy) continue;
         const int64_t r = __ldg(F.row + f);
         const int hi = __ldg(F.halo + f);
         AT v = static_cast<AT>(y[r * k + c]);
         if (hi >= 0) v += halo[static_cast<int64_t>(hi) * k + c];
-        v = long_row_sum<AT>(__ldg(F.p0 + f), __ldg(F.np + f), __ldg(F.rem + f), lpart, k, c, v);
+        v = long_row_sum<AT>(__ldg(F.p0 + f), np, __ldg(F.rem + f), lpart, k, c, v);
         y[r * k + c] = static_cast<XT>(v);
     }
 }
@@ -74,7 +92,7 @@ static int launch_spmm_lpr(const pars3_handle *h, int dtype, double alpha, int k
     if (nf > 0) {
         const int64_t total = static_cast<int64_t>(nf) * k;
         const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 8LL * sm_count()));
-        fold_spmm_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, k, fold_lists(D), static_cast<const AT *>(halo),
+        fold_spmm_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, k, fold_lists(D, L), static_cast<const AT *>(halo),
                                                          static_cast<const AT *>(lpart), static_cast<XT *>(Y));
     }
     return cuda_status(cudaGetLastError());

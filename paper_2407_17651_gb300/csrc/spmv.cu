@@ -69,7 +69,7 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     const int nf = static_cast<int>(L.fold_row.size());
     if (nf > 0) {
         const int blocks = static_cast<int>(std::min<int64_t>((nf + 255) / 256, 8LL * sm_count()));
-        fold_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, fold_lists(D), static_cast<const AT *>(halo),
+        fold_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, fold_lists(D, L), static_cast<const AT *>(halo),
                                                     static_cast<const AT *>(lpart), static_cast<XT *>(y));
     }
     return cuda_status(cudaGetLastError());

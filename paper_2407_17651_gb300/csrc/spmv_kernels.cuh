@@ -900,9 +900,27 @@ __device__ __forceinline__ AT long_row_sum(int p0, int np, int rem, const AT *__
     return v;
 }
 
-// The fold lists of a handle (device pointers).
+// The full pieces p0 .. p0+np-1 (column c of k) of a heavy long row (at least
+// kFoldHeavy of them; an R-MAT hub row has 257) summed by one warp: lane l
+// adds pieces p0 + l, p0 + l + 32, ... in order, then five butterfly steps;
+// lane 0's result is used, so the order of every addition is fixed.  A
+// thread walking such a row alone made the fold the longest step of the
+// product (18 us on the R-MAT matrix).
+template <typename AT>
+__device__ __forceinline__ AT heavy_pieces_warp(int p0, int np, const AT *__restrict__ lpart, int64_t k, int c) {
+    const int lane = threadIdx.x & 31;
+    AT s = AT(0);
+    for (int q = lane; q < np; q += 32) s += lpart[static_cast<int64_t>(p0 + q) * k + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// The fold lists of a handle (device pointers); items with at least
+// kFoldHeavy full pieces are also listed in `heavy` and folded by warps.
 struct FoldLists {
-    const int32_t *row, *halo, *p0, *np, *rem;
+    const int32_t *row, *halo, *p0, *np, *rem, *heavy;
+    int32_t nheavy;
 };
 
 // One thread per receiving row: y[row] += halo sum, then the row's long-row
@@ -910,9 +928,25 @@ struct FoldLists {
 template <typename XT, typename AT>
 __global__ void __launch_bounds__(256) fold_kernel(int nitems, const FoldLists F, const AT *__restrict__ halo,
                                                    const AT *__restrict__ lpart, XT *__restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int w = gw; w < F.nheavy; w += nw) {   // heavy rows, a warp each
+        const int f = __ldg(F.heavy + w);
+        const AT s = heavy_pieces_warp<AT>(__ldg(F.p0 + f), __ldg(F.np + f), lpart, 1, 0);
+        if (lane == 0) {
+            const int r = __ldg(F.row + f), hi = __ldg(F.halo + f), rem = __ldg(F.rem + f);
+            AT v = static_cast<AT>(y[r]);
+            if (hi >= 0) v += halo[hi];
+            v += s;
+            if (rem >= 0) v += lpart[rem];
+            y[r] = static_cast<XT>(v);
+        }
+    }
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nitems; f += gridDim.x * blockDim.x) {
+        const int np = __ldg(F.np + f);
+        if (np >= kFoldHeavy) continue;
         const int r = __ldg(F.row + f), hi = __ldg(F.halo + f);
-        const int p0 = __ldg(F.p0 + f), np = __ldg(F.np + f), rem = __ldg(F.rem + f);
+        const int p0 = __ldg(F.p0 + f), rem = __ldg(F.rem + f);
         AT v = static_cast<AT>(y[r]);
         if (hi >= 0) v += halo[hi];
         v = long_row_sum<AT>(p0, np, rem, lpart, 1, 0, v);
@@ -920,8 +954,9 @@ __global__ void __launch_bounds__(256) fold_kernel(int nitems, const FoldLists F
     }
 }
 
-inline FoldLists fold_lists(const DevLayout &D) {
-    return FoldLists{D.fold_row, D.fold_halo, D.fold_p0, D.fold_np, D.fold_rem};
+inline FoldLists fold_lists(const DevLayout &D, const Layout &L) {
+    return FoldLists{D.fold_row, D.fold_halo, D.fold_p0, D.fold_np, D.fold_rem, D.fold_heavy,
+                     static_cast<int32_t>(L.fold_heavy.size())};
 }
 
 // Kernel arguments of handle h for precision dtype (values of that

@@ -100,6 +100,35 @@ def test_batched_equals_single_and_oracle(members, dtype, k, capture):
         oracle_check(A, perm, dtype, alphas[m], Xn[m], Ys[m].double().cpu().numpy())
 
 
+def test_batched_with_heavy_long_rows_equals_single():
+    """A member with rows of at least 64 pieces (folded by warps): the batched
+    result equals the single-matrix call bit for bit and the oracle."""
+    u, v = W.grid_edges((60, 60))
+    n = 3601
+    hub = n - 1
+    u = np.concatenate([np.asarray(u, np.int64), np.full(3600, hub, np.int64)])
+    v = np.concatenate([np.asarray(v, np.int64), np.arange(3600, dtype=np.int64)])
+    A = W.from_keys(n, np.unique(np.maximum(u, v) * n + np.minimum(u, v)), "normal", 6)
+    B = W.grid((50, 40), "normal", 7)
+    mem = []
+    for M, kw in ((A, dict(T=512, W=32, long_row=32, piece=8)), (B, dict(T=256, W=64))):
+        perm = P.pars3_reorder(M.n, M.rowptr, M.col)[0]
+        h = P.pars3_split(M.n, M.rowptr, M.col, M.val, perm, dtypes=ALL, **kw)
+        P.pars3_upload(h)
+        mem.append((M, perm, h))
+    for dtype in (P.F64, P.F32):
+        for k in (1, 4):
+            Xs, Ys, Xn = operands(mem, dtype, k, 300 + k)
+            P.pars3_spmm_batched([h for _, _, h in mem], dtype, [0.5, 1.0], Xs, Ys, capture=False)
+            torch.cuda.synchronize()
+            for m, (M, perm, h) in enumerate(mem):
+                Y1 = torch.full_like(Xs[m], float("nan"))
+                P.pars3_spmm(h, dtype, [0.5, 1.0][m], Xs[m], Y1)
+                torch.cuda.synchronize()
+                assert torch.equal(Ys[m], Y1), (dtype, k, m)
+                oracle_check(M, perm, dtype, [0.5, 1.0][m], Xn[m], Ys[m].double().cpu().numpy())
+
+
 def test_graph_replay_follows_buffer_contents(members):
     hs = [h for _, _, h in members]
     alphas = [1.0] * len(members)

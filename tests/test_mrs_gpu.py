@@ -86,6 +86,25 @@ def test_long_rows_and_halo_in_the_loop():
         assert rel <= 1e-10 * 1.05, (inner, rel)
 
 
+def test_heavy_long_rows_in_the_loop():
+    """Rows of at least 64 pieces are folded by a warp in the MRS fold too (a
+    hub joined to 3,600 grid vertices, pieces of 8 entries: 450 pieces)."""
+    u, v = W.grid_edges((60, 60))
+    n = 3601
+    hub = n - 1
+    u = np.concatenate([np.asarray(u, np.int64), np.full(3600, hub, np.int64)])
+    v = np.concatenate([np.asarray(v, np.int64), np.arange(3600, dtype=np.int64)])
+    A = W.from_keys(n, np.unique(np.maximum(u, v) * n + np.minimum(u, v)), "normal", 5)
+    h, perm = setup(A, T=512, W=32, long_row=32, piece=8)
+    assert P.pars3_info_get(h)["long_pieces"] >= 450
+    b = W.vector("uniform", A.n, 9)
+    F = O.Full(A)
+    for inner in (P.F64, P.F32):
+        x, res = solve(h, perm, 1.0, b, inner=inner, rtol=1e-10, inner_rtol=1e-4)
+        rel = np.linalg.norm(b - F.apply(1.0, x)) / np.linalg.norm(b)
+        assert rel <= 1e-10 * 1.05, (inner, rel)
+
+
 def test_config3_alpha1_fp64_and_fp32():
     A, _, _ = W.config1()
     h, perm = setup(A, T=2048, W=32)
