@@ -475,9 +475,11 @@ def mrs_summary(mrs):
     return out
 
 
-def traffic_from_profile(key: str, kernel_hash: str, split_kw: dict):
+def traffic_from_profile(key: str, kernel_hash: str, split_kw: dict, layout_bytes: int):
     """DRAM bytes per launch from the committed ncu summary of `key`, if it
-    was taken on the current kernel source with the same split parameters."""
+    was taken on the current kernel source with the same split parameters, or
+    with parameters (the autotuner's choice may differ from run to run) whose
+    layout streams the same bytes within 2 %."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -486,7 +488,9 @@ def traffic_from_profile(key: str, kernel_hash: str, split_kw: dict):
     if not ent or ent.get("source_hash") != kernel_hash:
         return None
     if ent.get("split_params") not in (None, split_kw):
-        return None
+        lb = ent.get("layout_bytes_per_launch")
+        if not lb or abs(layout_bytes - lb) > 0.02 * lb:
+            return None
     return float(ent["dram_bytes_per_launch"])
 
 
@@ -630,7 +634,8 @@ def main():
     avg_spmv_s = tot_s_local / (REPEATS * args.steps)   # average product (launch) duration, timed region
     achieved = ub / avg_spmv_s / 1e9
     khash = kernel_source_hash()
-    traffic = traffic_from_profile(f"tile_kernel_{args.dtype}_{args.workload}", khash, split_kw) if k == 1 else None
+    traffic = (traffic_from_profile(f"tile_kernel_{args.dtype}_{args.workload}", khash, split_kw,
+                                    info["bytes_per_spmv"][dt]) if k == 1 else None)
     # the fp64 products do one FMA per stored entry and direction: measure the
     # device's fp64 FMA rate in the same run (a kernel of independent chains)
     fp64 = None
