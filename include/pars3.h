@@ -189,6 +189,28 @@ int pars3_version(int32_t *major, int32_t *minor, int32_t *cuda_arch);
 int pars3_reorder(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t flags,
                   int32_t *perm_out, int64_t *bw_before, int64_t *bw_after);
 
+/* pars3_reorder_device -- the ordering of pars3_reorder, computed on the GPU
+ * (Sec. 1 and Sec. 3.1.2; the paper leaves preprocessing out of its timings,
+ * Sec. 4, but a batch of matrices pays it every time).  rowptr[n+1] and
+ * col[nnz] are DEVICE arrays holding the strict lower pattern, perm_out[n]
+ * a caller-allocated DEVICE array that receives new -> old.  The result is
+ * identical, element for element, to pars3_reorder with the same flags:
+ * components are placed in the order of their (degree, index)-smallest
+ * vertex, searched level by level with every vertex appended by the first
+ * vertex of the previous level adjacent to it, in (degree, index) order.
+ * Flags: PARS3_RCM_GUARD and PARS3_RCM_PERIPHERAL (PARS3_RCM_LOCAL returns
+ * EUNSUPPORTED).  bw_before/bw_after (host, may be NULL) as for
+ * pars3_reorder.  Runs on `stream` and returns after the result is
+ * complete (it synchronizes the stream a few times to size its work).
+ * Allocates device scratch of about 52 bytes per stored entry plus 130 per
+ * vertex, freed before returning.  Requires nnz < 2^30.
+ * Errors: EINVAL (n < 0, null pointer, unknown flag), ENOTSKEW (pattern
+ * not strict lower; checked on the device before any other use of it),
+ * ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT (the bounded union-find retries ran
+ * out; not expected). */
+int pars3_reorder_device(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t flags,
+                         int32_t *perm_out, int64_t *bw_before, int64_t *bw_after, void *stream);
+
 /* pars3_split -- Sec. 3.1.2 and Figs. 7-8: reorder S by perm (new -> old;
  * NULL = identity), re-triangularize (an entry landing above the diagonal is
  * stored mirrored with its sign flipped, Eq. 2), classify every stored entry

@@ -1,0 +1,818 @@
+// device_reorder.cu -- pars3_reorder_device: the reverse Cuthill-McKee
+// ordering of pars3_reorder (Sec. 1 and Sec. 3.1.2), computed on the GPU from
+// a strict-lower pattern already in device memory.  The result is the same
+// permutation, element for element, as the host ordering.
+//
+// Serial Cuthill-McKee dequeues vertices in order and appends each one's
+// unvisited neighbours in (degree, index) order.  The same order is built
+// one breadth-first level at a time:
+//   * the vertices of level l+1 are the unvisited neighbours of level l;
+//     each is appended by the FIRST vertex of level l (in queue order) that
+//     is adjacent to it, so every such vertex is claimed by the smallest
+//     queue position among its level-l neighbours (an atomic minimum);
+//   * a parent's children keep its adjacency order, and adjacency lists are
+//     sorted by the neighbours' (degree, index) rank once, up front, so no
+//     sort runs per level;
+//   * parents append in queue order, so a parent's first child slot is a
+//     prefix sum of the children counts over the level.
+// Connected components do not interact, so all of them are searched at once:
+// components are placed in the order of their (degree, index)-smallest
+// vertex (the serial start rule), each owns a contiguous queue segment, and
+// a level step processes the current level of every unfinished component.
+//
+// Supporting pieces, all on the device: input validation, degrees, a stable
+// LSD radix sort (32-bit keys with 32-bit values), connected components by
+// union-find with hooking towards the smaller root, and single-block prefix
+// sums for sizes that live in device memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <vector>
+
+#include "internal.h"
+
+namespace pars3 {
+namespace {
+
+constexpr int kThreads = 256;                       // block size of the element-wise kernels
+constexpr int kSortItems = 16;                      // keys per thread in a sort tile
+constexpr int kSortTile = kThreads * kSortItems;    // 4096 keys per tile
+constexpr int kSortWarps = kThreads / 32;
+constexpr int kSortWarpKeys = kSortTile / kSortWarps;   // 512 consecutive keys per warp
+constexpr int kScanThreads = 1024;                  // single-block prefix sums
+constexpr int kScanItems = 8;
+constexpr int kHookRounds = 1 << 22;                // bound on the union-find retries of one edge
+constexpr int kLevelsPerCheck = 8;                  // level steps between two host checks
+
+// error bits of Ctl::err
+constexpr int kErrPattern = 1;    // not a valid strict lower pattern
+constexpr int kErrHook = 2;       // union-find retries ran out
+constexpr int kErrPlaced = 4;     // a vertex was left without a position
+
+struct Ctl {
+    int err;
+    int nact[2];                  // unfinished frontier entries, per buffer
+    int level;                    // level steps taken
+    int active;                   // components still moving their start (pseudo-peripheral search)
+    unsigned long long bw0, bw1;  // bandwidth before / after
+};
+
+// One frontier entry: queue positions [fb, fe) are the current level of one
+// component (comp is that component's index in start order).
+struct Front {
+    int fb, fe, comp, pad;
+};
+
+__device__ __forceinline__ int lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return static_cast<int>(m);
+}
+
+// ------------------------------------------------------------ prefix sums
+
+// Exclusive prefix of one value per thread across a block of kScanThreads
+// threads; *total receives the block sum.  ws holds 32 partial sums.
+template <typename T>
+__device__ T block_excl_scan(T v, T *ws, T *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += t;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < (kScanThreads >> 5) ? ws[lane] : T(0);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T t = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += t;
+        }
+        ws[lane] = w;   // inclusive sums of the warp totals
+    }
+    __syncthreads();
+    const T before = (warp > 0 ? ws[warp - 1] : T(0)) + inc - v;
+    *total = ws[31];
+    __syncthreads();   // ws is reused by the next call
+    return before;
+}
+
+// out[0..len) = exclusive prefix sums of in[0..len), out[len] = the total.
+// Called by all kScanThreads threads of one block.
+__device__ void block_scan_array(const int32_t *in, int32_t *out, int len, int *ws) {
+    int carry = 0;
+    for (int base = 0; base < len; base += kScanThreads * kScanItems) {
+        const int i0 = base + threadIdx.x * kScanItems;
+        int v[kScanItems];
+        int s = 0;
+#pragma unroll
+        for (int t = 0; t < kScanItems; ++t) {
+            v[t] = i0 + t < len ? in[i0 + t] : 0;
+            s += v[t];
+        }
+        int total;
+        int run = carry + block_excl_scan<int>(s, ws, &total);
+#pragma unroll
+        for (int t = 0; t < kScanItems; ++t) {
+            if (i0 + t < len) out[i0 + t] = run;
+            run += v[t];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) out[len] = carry;
+}
+
+// Single-block exclusive scan; the length is *len_dev when len_dev is not
+// null (a size the host does not know), else len.
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(const int32_t *__restrict__ in,
+                                                            int32_t *__restrict__ out, const int32_t *len_dev,
+                                                            int len) {
+    __shared__ int ws[32];
+    block_scan_array(in, out, len_dev ? *len_dev : len, ws);
+}
+
+// ------------------------------------------------------------ validation
+
+// Rows must satisfy 0 <= rowptr[i] <= rowptr[i+1] <= nnz and hold strictly
+// increasing columns below the diagonal; entries are read only inside a row
+// whose bounds passed.  Also writes the row of every entry and the row
+// lengths (the lower part of each degree).
+__global__ void validate_kernel(int n, int nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                int32_t *__restrict__ rowof, int32_t *__restrict__ deg, Ctl *ctl) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int a = rp[i], b = rp[i + 1];
+        if ((i == 0 && a != 0) || a < 0 || b < a || b > nnz) {
+            atomicOr(&ctl->err, kErrPattern);
+            deg[i] = 0;
+            continue;
+        }
+        int prev = -1;
+        bool ok = true;
+        for (int k = a; k < b; ++k) {
+            const int j = ci[k];
+            if (j <= prev || j >= i) ok = false;
+            prev = j;
+            rowof[k] = i;
+        }
+        if (!ok) atomicOr(&ctl->err, kErrPattern);
+        deg[i] = b - a;
+    }
+}
+
+// deg[j] += number of rows holding column j (the upper part of each degree)
+__global__ void degree_kernel(int nnz, const int32_t *__restrict__ ci, int32_t *deg) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x)
+        atomicAdd(&deg[ci[k]], 1);
+}
+
+// ------------------------------------------------------------ radix sort
+
+// hist[d * ntiles + t] = keys of tile t whose digit (key >> shift) & 255 is d
+__global__ void __launch_bounds__(kThreads) sort_hist_kernel(const uint32_t *__restrict__ key, int count,
+                                                             int shift, int ntiles, int32_t *__restrict__ hist) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int t = blockIdx.x;
+    const int base = t * kSortTile;
+    for (int i = threadIdx.x; i < kSortTile; i += kThreads)
+        if (base + i < count) atomicAdd(&h[(key[base + i] >> shift) & 255], 1);
+    __syncthreads();
+    hist[threadIdx.x * ntiles + t] = h[threadIdx.x];
+}
+
+// Stable scatter of one tile: warp w owns keys [base + 512 w, base + 512 (w+1)),
+// taken 32 at a time in order; keys with equal digits are ranked by lane
+// within a round and by round within the warp, and warps are ranked by
+// index, so equal digits keep their input order.
+__global__ void __launch_bounds__(kThreads) sort_scatter_kernel(const uint32_t *__restrict__ key,
+                                                                const int32_t *__restrict__ val, int count,
+                                                                int shift, int ntiles,
+                                                                const int32_t *__restrict__ off,
+                                                                uint32_t *__restrict__ key_out,
+                                                                int32_t *__restrict__ val_out) {
+    __shared__ int cnt[kSortWarps][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = lane; d < 256; d += 32) cnt[warp][d] = 0;
+    __syncwarp();
+    const int t = blockIdx.x;
+    const int base = t * kSortTile + warp * kSortWarpKeys;
+    for (int r = 0; r < kSortWarpKeys; r += 32) {
+        const int i = base + r + lane;
+        const bool ok = i < count;
+        const int d = ok ? static_cast<int>((key[i] >> shift) & 255) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (ok && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;   // kThreads == 256 digits
+        int run = off[d * ntiles + t];
+        for (int w = 0; w < kSortWarps; ++w) {
+            const int c = cnt[w][d];
+            cnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < kSortWarpKeys; r += 32) {
+        const int i = base + r + lane;
+        const bool ok = i < count;
+        const uint32_t k = ok ? key[i] : 0u;
+        const int d = ok ? static_cast<int>((k >> shift) & 255) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (ok) {
+            const int p = cnt[warp][d] + __popc(peers & static_cast<unsigned>(lanemask_lt()));
+            key_out[p] = k;
+            val_out[p] = val[i];
+        }
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+
+// ------------------------------------------------------------ components
+
+// Root of x.  Parents always point to a smaller index, so the walk ends
+// after at most x steps; the path is halved on the way (every write stores
+// an ancestor, so concurrent walks stay valid).
+__device__ __forceinline__ int find_root(int *parent, int x) {
+    volatile int *p = parent;
+    int px = p[x];
+    while (px != x) {
+        const int g = p[px];
+        if (g != px) p[x] = g;
+        x = px;
+        px = p[x];
+    }
+    return x;
+}
+
+// Union of the two ends of every stored entry: the larger root is hooked
+// below the smaller one, so every component ends with its smallest vertex as
+// root.  A failed compare-and-swap means the root was hooked meanwhile; the
+// retries are bounded (each failure removes a root).
+__global__ void hook_kernel(int nnz, const int32_t *__restrict__ rowof, const int32_t *__restrict__ ci,
+                            int *parent, Ctl *ctl) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
+        const int i = rowof[k], j = ci[k];
+        bool done = false;
+        for (int it = 0; it < kHookRounds && !done; ++it) {
+            const int ri = find_root(parent, i), rj = find_root(parent, j);
+            if (ri == rj) {
+                done = true;
+            } else {
+                const int lo = min(ri, rj), hi = max(ri, rj);
+                done = atomicCAS(&parent[hi], hi, lo) == hi;
+            }
+        }
+        if (!done) atomicOr(&ctl->err, kErrHook);
+    }
+}
+
+// comp[v] = root of v (the smallest vertex of its component); the smallest
+// (degree, index) rank of each component and its size are gathered at the root.
+__global__ void comp_kernel(int n, int *parent, const int32_t *__restrict__ rank, int32_t *__restrict__ comp,
+                            int32_t *cmin, int32_t *csize) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int r = find_root(parent, v);
+        comp[v] = r;
+        atomicMin(&cmin[r], rank[v]);
+        atomicAdd(&csize[r], 1);
+    }
+}
+
+// rank[by_deg[i]] = i
+__global__ void rank_kernel(int n, const int32_t *__restrict__ by_deg, int32_t *__restrict__ rank) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) rank[by_deg[i]] = i;
+}
+
+// flag[i] = 1 when the vertex of rank i is the (degree, index)-smallest of
+// its component, i.e. the vertex serial Cuthill-McKee starts that component at
+__global__ void start_flag_kernel(int n, const int32_t *__restrict__ by_deg, const int32_t *__restrict__ comp,
+                                  const int32_t *__restrict__ cmin, int32_t *__restrict__ flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flag[i] = cmin[comp[by_deg[i]]] == i ? 1 : 0;
+}
+
+// Components in start order: cstart[c] = the start candidate of the c-th
+// component, csz[c] its size.
+__global__ void start_list_kernel(int n, const int32_t *__restrict__ by_deg, const int32_t *__restrict__ comp,
+                                  const int32_t *__restrict__ csize, const int32_t *__restrict__ flag,
+                                  const int32_t *__restrict__ sidx, int32_t *__restrict__ cstart,
+                                  int32_t *__restrict__ csz) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!flag[i]) continue;
+        const int v = by_deg[i];
+        cstart[sidx[i]] = v;
+        csz[sidx[i]] = csize[comp[v]];
+    }
+}
+
+// ------------------------------------------------------------ adjacency
+
+// Every directed edge (v -> u), listed source by source in (degree, index)
+// order of the source: key = u, value = v.  One warp per source.  aun/cur
+// is the unordered adjacency (filled with atomics, any order).
+__global__ void edges_by_rank_kernel(int n, const int32_t *__restrict__ by_deg, const int32_t *__restrict__ arp,
+                                     const int32_t *__restrict__ aun, const int32_t *__restrict__ epos,
+                                     uint32_t *__restrict__ key, int32_t *__restrict__ val) {
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+        const int v = by_deg[i];
+        const int a = arp[v], d = arp[v + 1] - a, o = epos[i];
+        for (int t = lane; t < d; t += 32) {
+            key[o + t] = static_cast<uint32_t>(aun[a + t]);
+            val[o + t] = v;
+        }
+    }
+}
+
+// unordered adjacency: both directions of every stored entry
+__global__ void scatter_adj_kernel(int nnz, const int32_t *__restrict__ rowof, const int32_t *__restrict__ ci,
+                                   const int32_t *__restrict__ arp, int32_t *cur, int32_t *__restrict__ aun) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
+        const int i = rowof[k], j = ci[k];
+        aun[arp[i] + atomicAdd(&cur[i], 1)] = j;
+        aun[arp[j] + atomicAdd(&cur[j], 1)] = i;
+    }
+}
+
+// sdeg[i] = degree of the vertex of rank i
+__global__ void gather_kernel(int n, const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
+                              int32_t *__restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];
+}
+
+__global__ void iota_kernel(int n, int32_t *__restrict__ a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+
+__global__ void fill_kernel(int n, int32_t v, int32_t *__restrict__ a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
+}
+
+
+// ------------------------------------------------------------ level steps
+//
+// The current level is a list of frontier entries act[0 .. nact) (nact =
+// ctl->nact[b]); fpre[s] is the number of frontier vertices before entry s,
+// so flat index f in [0, fpre[nact]) names one frontier vertex.  One warp
+// handles one frontier vertex and walks its adjacency list.
+
+__device__ __forceinline__ int entry_of(const int32_t *__restrict__ fpre, int nact, int f) {
+    int lo = 0, hi = nact;   // fpre[lo] <= f < fpre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (fpre[mid] <= f) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// start positions: component c begins its queue segment at cbase[c] with root[c]
+__global__ void bfs_init_kernel(int ncomp, const int32_t *__restrict__ root, const int32_t *__restrict__ cbase,
+                                int32_t *__restrict__ cm, int32_t *__restrict__ pos, Front *__restrict__ act,
+                                int32_t *__restrict__ fpre, Ctl *ctl) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp; c += gridDim.x * blockDim.x) {
+        const int v = root[c], q = cbase[c];
+        cm[q] = v;
+        pos[v] = q;
+        act[c] = Front{q, q + 1, c, 0};
+        fpre[c] = c;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        fpre[ncomp] = ncomp;
+        ctl->nact[0] = ncomp;
+        ctl->nact[1] = 0;
+        ctl->level = 0;
+    }
+}
+
+// Every unvisited neighbour u of frontier vertex q takes claim[u] = min(claim[u], q).
+__global__ void __launch_bounds__(kThreads) claim_kernel(const Ctl *ctl, int b, const Front *__restrict__ act,
+                                                         const int32_t *__restrict__ fpre,
+                                                         const int32_t *__restrict__ cm,
+                                                         const int32_t *__restrict__ arp,
+                                                         const int32_t *__restrict__ adj,
+                                                         const int32_t *__restrict__ pos, int32_t *claim) {
+    const int nact = ctl->nact[b];
+    const int F = fpre[nact];
+    const int lane = threadIdx.x & 31;
+    for (int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < F; f += (gridDim.x * blockDim.x) >> 5) {
+        const int s = entry_of(fpre, nact, f);
+        const int q = act[s].fb + f - fpre[s];
+        const int v = cm[q];
+        for (int e = arp[v] + lane; e < arp[v + 1]; e += 32) {
+            const int u = adj[e];
+            if (pos[u] < 0) atomicMin(&claim[u], q);
+        }
+    }
+}
+
+// cnt[f] = children of frontier vertex f (neighbours it claimed)
+__global__ void __launch_bounds__(kThreads) count_kernel(const Ctl *ctl, int b, const Front *__restrict__ act,
+                                                         const int32_t *__restrict__ fpre,
+                                                         const int32_t *__restrict__ cm,
+                                                         const int32_t *__restrict__ arp,
+                                                         const int32_t *__restrict__ adj,
+                                                         const int32_t *__restrict__ claim,
+                                                         int32_t *__restrict__ cnt) {
+    const int nact = ctl->nact[b];
+    const int F = fpre[nact];
+    const int lane = threadIdx.x & 31;
+    for (int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < F; f += (gridDim.x * blockDim.x) >> 5) {
+        const int s = entry_of(fpre, nact, f);
+        const int q = act[s].fb + f - fpre[s];
+        const int v = cm[q];
+        int c = 0;
+        for (int e0 = arp[v]; e0 < arp[v + 1]; e0 += 32) {
+            const int e = e0 + lane;
+            c += __popc(__ballot_sync(0xffffffffu, e < arp[v + 1] && claim[adj[e]] == q));
+        }
+        if (lane == 0) cnt[f] = c;
+    }
+}
+
+// One block: coff = exclusive prefix of cnt over the level; the entries with
+// children become the next level's entries (in order), each starting where
+// its component's current level ends.  An entry without children closes its
+// component's search: with track set, its level number (the eccentricity of
+// the start) and its last level are recorded.
+__global__ void __launch_bounds__(kScanThreads) plan_kernel(Ctl *ctl, int b, const Front *__restrict__ act,
+                                                            const int32_t *__restrict__ fpre,
+                                                            const int32_t *__restrict__ cnt,
+                                                            int32_t *__restrict__ coff, Front *__restrict__ act2,
+                                                            int32_t *__restrict__ fpre2, int32_t *__restrict__ ecc,
+                                                            int2 *__restrict__ last) {
+    __shared__ int ws[32];
+    __shared__ long long wl[32];
+    const int nact = ctl->nact[b];
+    const int level = ctl->level;
+    block_scan_array(cnt, coff, fpre[nact], ws);
+    __syncthreads();
+    long long carry = 0;   // (entries kept) << 32 | children so far
+    for (int base = 0; base < nact; base += kScanThreads) {
+        const int s = base + threadIdx.x;
+        int ch = 0;
+        Front e{};
+        if (s < nact) {
+            e = act[s];
+            ch = coff[fpre[s + 1]] - coff[fpre[s]];
+            if (ch == 0 && ecc) {
+                ecc[e.comp] = level;
+                last[e.comp] = make_int2(e.fb, e.fe);
+            }
+        }
+        const long long mine = ch > 0 ? ((1LL << 32) | ch) : 0LL;
+        long long total;
+        const long long before = carry + block_excl_scan<long long>(mine, wl, &total);
+        if (ch > 0) {
+            const int k = static_cast<int>(before >> 32);
+            act2[k] = Front{e.fe, e.fe + ch, e.comp, 0};
+            fpre2[k] = static_cast<int>(before & 0xffffffffLL);
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        const int kept = static_cast<int>(carry >> 32);
+        fpre2[kept] = static_cast<int>(carry & 0xffffffffLL);
+        ctl->nact[b ^ 1] = kept;
+        ctl->level = level + 1;
+    }
+}
+
+// Frontier vertex q appends the neighbours it claimed, in adjacency order,
+// from slot fe(entry) + coff[f] - coff[first f of the entry].
+__global__ void __launch_bounds__(kThreads) write_kernel(const Ctl *ctl, int b, const Front *__restrict__ act,
+                                                         const int32_t *__restrict__ fpre,
+                                                         const int32_t *__restrict__ coff, int32_t *cm,
+                                                         const int32_t *__restrict__ arp,
+                                                         const int32_t *__restrict__ adj,
+                                                         const int32_t *__restrict__ claim,
+                                                         int32_t *__restrict__ pos) {
+    const int nact = ctl->nact[b];
+    const int F = fpre[nact];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = static_cast<unsigned>(lanemask_lt());
+    for (int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < F; f += (gridDim.x * blockDim.x) >> 5) {
+        const int s = entry_of(fpre, nact, f);
+        const Front e = act[s];
+        const int q = e.fb + f - fpre[s];
+        const int v = cm[q];
+        int slot = e.fe + coff[f] - coff[fpre[s]];
+        const int end = arp[v + 1];
+        for (int e0 = arp[v]; e0 < end; e0 += 32) {
+            const int i = e0 + lane;
+            const int u = i < end ? adj[i] : -1;
+            const bool hit = u >= 0 && claim[u] == q;
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int p = slot + __popc(m & lt);
+                cm[p] = u;
+                pos[u] = p;
+            }
+            slot += __popc(m);
+        }
+    }
+}
+
+// x[c] = the vertex of smallest (degree, index) rank in the last level of c
+__global__ void last_min_kernel(int ncomp, const int2 *__restrict__ last, const int32_t *__restrict__ cm,
+                                const int32_t *__restrict__ rank, const int32_t *__restrict__ by_deg,
+                                int32_t *__restrict__ x) {
+    const int lane = threadIdx.x & 31;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncomp; c += (gridDim.x * blockDim.x) >> 5) {
+        const int2 L = last[c];
+        int best = INT_MAX;
+        for (int q = L.x + lane; q < L.y; q += 32) best = min(best, rank[cm[q]]);
+        best = __reduce_min_sync(0xffffffffu, best);
+        if (lane == 0) x[c] = by_deg[best];
+    }
+}
+
+// One George-Liu step per still-active component: the search from x[c]
+// reached eccentricity ex[c]; when that exceeds e[c], r moves to x and x to
+// y (the smallest vertex of the new last level), else the component is done.
+__global__ void peripheral_step_kernel(int ncomp, int32_t *__restrict__ active, int32_t *__restrict__ r,
+                                       int32_t *__restrict__ e, int32_t *__restrict__ x,
+                                       const int32_t *__restrict__ ex, const int32_t *__restrict__ y, Ctl *ctl) {
+    int still = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp; c += gridDim.x * blockDim.x) {
+        if (!active[c]) continue;
+        if (ex[c] > e[c]) {
+            r[c] = x[c];
+            e[c] = ex[c];
+            x[c] = y[c];
+            ++still;
+        } else {
+            active[c] = 0;
+        }
+    }
+    still = __reduce_add_sync(0xffffffffu, still);
+    if ((threadIdx.x & 31) == 0 && still) atomicAdd(&ctl->active, still);
+}
+
+// start of every component for the next search: x[c] while active, else r[c]
+__global__ void select_kernel(int ncomp, const int32_t *__restrict__ active, const int32_t *__restrict__ r,
+                              const int32_t *__restrict__ x, int32_t *__restrict__ out) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp; c += gridDim.x * blockDim.x)
+        out[c] = active[c] ? x[c] : r[c];
+}
+
+// ------------------------------------------------------------ result
+
+__global__ void perm_kernel(int n, const int32_t *__restrict__ cm, const int32_t *__restrict__ pos,
+                            int32_t *__restrict__ perm, Ctl *ctl) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        perm[k] = cm[n - 1 - k];
+        if (pos[k] < 0) atomicOr(&ctl->err, kErrPlaced);
+    }
+}
+
+// bandwidths before (i - j over stored (i, j)) and after (|pos i - pos j|,
+// the same distance in the reversed order)
+__global__ void bandwidth_kernel(int nnz, const int32_t *__restrict__ rowof, const int32_t *__restrict__ ci,
+                                 const int32_t *__restrict__ pos, Ctl *ctl) {
+    unsigned m0 = 0, m1 = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
+        const int i = rowof[k], j = ci[k];
+        m0 = max(m0, static_cast<unsigned>(i - j));
+        m1 = max(m1, static_cast<unsigned>(abs(pos[i] - pos[j])));
+    }
+    m0 = __reduce_max_sync(0xffffffffu, m0);
+    m1 = __reduce_max_sync(0xffffffffu, m1);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&ctl->bw0, static_cast<unsigned long long>(m0));
+        atomicMax(&ctl->bw1, static_cast<unsigned long long>(m1));
+    }
+}
+
+
+// ------------------------------------------------------------ host side
+
+// Device scratch of one call, released on every return path.
+class Scratch {
+public:
+    ~Scratch() {
+        for (void *p : ptrs_) cudaFree(p);
+    }
+    template <typename T>
+    T *get(size_t count) {
+        void *p = nullptr;
+        if (err_ == cudaSuccess) err_ = cudaMalloc(&p, std::max<size_t>(16, count * sizeof(T)));
+        if (err_ != cudaSuccess) return nullptr;
+        ptrs_.push_back(p);
+        return static_cast<T *>(p);
+    }
+    cudaError_t err() const { return err_; }
+
+private:
+    std::vector<void *> ptrs_;
+    cudaError_t err_ = cudaSuccess;
+};
+
+int grid_for(int64_t items, int per_block) {
+    const int64_t g = (items + per_block - 1) / per_block;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, 8LL * sm_count())));
+}
+
+int bits_for(int n) {   // bits needed for the values 0 .. n-1
+    int b = 0;
+    while (b < 31 && (1LL << b) < n) ++b;
+    return b;
+}
+
+// Stable sort of (key, val) pairs by the low `bits` bits of key.  The pairs
+// start in (k0, v0); on return *ko/*vo point at whichever buffer holds the
+// sorted pairs.
+void radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int count, int bits, int32_t *hist,
+                int32_t *hoff, cudaStream_t st, uint32_t **ko, int32_t **vo) {
+    const int ntiles = (count + kSortTile - 1) / kSortTile;
+    for (int shift = 0; shift < bits && count > 0; shift += 8) {
+        sort_hist_kernel<<<ntiles, kThreads, 0, st>>>(k0, count, shift, ntiles, hist);
+        scan_kernel<<<1, kScanThreads, 0, st>>>(hist, hoff, nullptr, 256 * ntiles);
+        sort_scatter_kernel<<<ntiles, kThreads, 0, st>>>(k0, v0, count, shift, ntiles, hoff, k1, v1);
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    *ko = k0;
+    *vo = v0;
+}
+
+int fetch_ctl(const Ctl *d, Ctl *h, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(h, d, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_status(e);
+}
+
+int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flags, int32_t *perm,
+                   int64_t *bw_before, int64_t *bw_after, cudaStream_t st) {
+    if (n < 0 || (flags & ~(PARS3_RCM_GUARD | PARS3_RCM_PERIPHERAL | PARS3_RCM_LOCAL))) return PARS3_EINVAL;
+    if (flags & PARS3_RCM_LOCAL) return PARS3_EUNSUPPORTED;
+    if (bw_before) *bw_before = 0;
+    if (bw_after) *bw_after = 0;
+    if (n == 0) return PARS3_OK;
+    if (!rp || !perm) return PARS3_EINVAL;
+    int32_t nnz = 0;
+    cudaError_t ce = cudaMemcpyAsync(&nnz, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    if (nnz < 0) return PARS3_ENOTSKEW;
+    if (nnz > 0 && !ci) return PARS3_EINVAL;
+    if (nnz > INT32_MAX / 2) return PARS3_EUNSUPPORTED;   // 2 nnz directed edges are indexed by int32
+    const int m2 = 2 * nnz;
+    const int G = kThreads;
+
+    Scratch S;
+    Ctl *ctl = S.get<Ctl>(1);
+    int32_t *rowof = S.get<int32_t>(nnz), *deg = S.get<int32_t>(n + 1);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    Ctl hc{};
+    if ((ce = cudaMemsetAsync(ctl, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_status(ce);
+
+    // validation, then degrees
+    validate_kernel<<<grid_for(n, G), G, 0, st>>>(n, nnz, rp, ci, rowof, deg, ctl);
+    int rc = fetch_ctl(ctl, &hc, st);
+    if (rc != PARS3_OK) return rc;
+    if (hc.err) return PARS3_ENOTSKEW;
+    degree_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, ci, deg);
+
+    // vertices in (degree, index) order: a stable sort by degree of 0 .. n-1
+    const int nbits = bits_for(n);
+    const int sort_max = std::max(n, m2);
+    const int ntiles = (sort_max + kSortTile - 1) / kSortTile;
+    uint32_t *ka = S.get<uint32_t>(sort_max), *kb = S.get<uint32_t>(sort_max);
+    int32_t *va = S.get<int32_t>(sort_max), *vb = S.get<int32_t>(sort_max);
+    int32_t *hist = S.get<int32_t>(256 * static_cast<size_t>(ntiles) + 1);
+    int32_t *hoff = S.get<int32_t>(256 * static_cast<size_t>(ntiles) + 1);
+    int32_t *by_deg = S.get<int32_t>(n), *rank = S.get<int32_t>(n);
+    int32_t *arp = S.get<int32_t>(n + 1), *cur = S.get<int32_t>(n), *aun = S.get<int32_t>(m2);
+    int32_t *sdeg = S.get<int32_t>(n), *epos = S.get<int32_t>(n + 1), *adj = S.get<int32_t>(m2);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    uint32_t *ko;
+    int32_t *vo;
+    cudaMemcpyAsync(ka, deg, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
+    iota_kernel<<<grid_for(n, G), G, 0, st>>>(n, va);
+    radix_sort(ka, va, kb, vb, n, nbits, hist, hoff, st, &ko, &vo);
+    cudaMemcpyAsync(by_deg, vo, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
+    rank_kernel<<<grid_for(n, G), G, 0, st>>>(n, by_deg, rank);
+
+    // adjacency lists sorted by the neighbours' rank: the directed edges are
+    // listed source by source in rank order, then sorted stably by target
+    scan_kernel<<<1, kScanThreads, 0, st>>>(deg, arp, nullptr, n);
+    cudaMemsetAsync(cur, 0, sizeof(int32_t) * n, st);
+    scatter_adj_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, ci, arp, cur, aun);
+    gather_kernel<<<grid_for(n, G), G, 0, st>>>(n, by_deg, deg, sdeg);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(sdeg, epos, nullptr, n);
+    edges_by_rank_kernel<<<grid_for(static_cast<int64_t>(n) * 32, G), G, 0, st>>>(n, by_deg, arp, aun, epos, ka, va);
+    radix_sort(ka, va, kb, vb, m2, nbits, hist, hoff, st, &ko, &vo);
+    cudaMemcpyAsync(adj, vo, sizeof(int32_t) * m2, cudaMemcpyDeviceToDevice, st);
+
+    // connected components, their start candidates (in start order) and sizes
+    int32_t *parent = S.get<int32_t>(n), *comp = S.get<int32_t>(n), *cmin = S.get<int32_t>(n);
+    int32_t *csize = S.get<int32_t>(n), *flag = S.get<int32_t>(n), *sidx = S.get<int32_t>(n + 1);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    iota_kernel<<<grid_for(n, G), G, 0, st>>>(n, parent);
+    hook_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, ci, parent, ctl);
+    fill_kernel<<<grid_for(n, G), G, 0, st>>>(n, INT_MAX, cmin);
+    cudaMemsetAsync(csize, 0, sizeof(int32_t) * n, st);
+    comp_kernel<<<grid_for(n, G), G, 0, st>>>(n, parent, rank, comp, cmin, csize);
+    start_flag_kernel<<<grid_for(n, G), G, 0, st>>>(n, by_deg, comp, cmin, flag);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(flag, sidx, nullptr, n);
+    int32_t ncomp = 0;
+    cudaMemcpyAsync(&ncomp, sidx + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if ((rc = fetch_ctl(ctl, &hc, st)) != PARS3_OK) return rc;
+    if (hc.err & kErrHook) return PARS3_ETIMEOUT;
+    if (ncomp < 1 || ncomp > n) return PARS3_ECUDA;
+    int32_t *cstart = S.get<int32_t>(ncomp), *csz = S.get<int32_t>(ncomp), *cbase = S.get<int32_t>(ncomp + 1);
+    int32_t *cm = S.get<int32_t>(n), *pos = S.get<int32_t>(n), *claim = S.get<int32_t>(n);
+    int32_t *cnt = S.get<int32_t>(n), *coff = S.get<int32_t>(n + 1);
+    Front *act[2] = {S.get<Front>(ncomp), S.get<Front>(ncomp)};
+    int32_t *fpre[2] = {S.get<int32_t>(ncomp + 1), S.get<int32_t>(ncomp + 1)};
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    start_list_kernel<<<grid_for(n, G), G, 0, st>>>(n, by_deg, comp, csize, flag, sidx, cstart, csz);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(csz, cbase, nullptr, ncomp);
+
+    // one breadth-first search of every component from root[c]; with ecc and
+    // last set, each component's eccentricity and last level are recorded
+    auto search = [&](const int32_t *root, int32_t *ecc, int2 *last) -> int {
+        cudaMemsetAsync(pos, 0xff, sizeof(int32_t) * n, st);
+        fill_kernel<<<grid_for(n, G), G, 0, st>>>(n, INT_MAX, claim);
+        bfs_init_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, root, cbase, cm, pos, act[0], fpre[0], ctl);
+        const int wg = 4 * sm_count();   // warp-per-vertex kernels: grid-stride over the level
+        int b = 0;
+        for (int64_t steps = 0;; steps += kLevelsPerCheck) {
+            for (int l = 0; l < kLevelsPerCheck; ++l) {
+                claim_kernel<<<wg, G, 0, st>>>(ctl, b, act[b], fpre[b], cm, arp, adj, pos, claim);
+                count_kernel<<<wg, G, 0, st>>>(ctl, b, act[b], fpre[b], cm, arp, adj, claim, cnt);
+                plan_kernel<<<1, kScanThreads, 0, st>>>(ctl, b, act[b], fpre[b], cnt, coff, act[b ^ 1], fpre[b ^ 1],
+                                                        ecc, last);
+                write_kernel<<<wg, G, 0, st>>>(ctl, b, act[b], fpre[b], coff, cm, arp, adj, claim, pos);
+                b ^= 1;
+            }
+            int r2 = fetch_ctl(ctl, &hc, st);
+            if (r2 != PARS3_OK) return r2;
+            if (hc.nact[b] == 0) return PARS3_OK;
+            if (steps > static_cast<int64_t>(n) + kLevelsPerCheck) return PARS3_ECUDA;   // more levels than vertices
+        }
+    };
+
+    const int32_t *root = cstart;
+    if (flags & PARS3_RCM_PERIPHERAL) {
+        // George-Liu pseudo-peripheral starts for all components at once
+        int32_t *r = S.get<int32_t>(ncomp), *e = S.get<int32_t>(ncomp), *x = S.get<int32_t>(ncomp);
+        int32_t *ex = S.get<int32_t>(ncomp), *y = S.get<int32_t>(ncomp), *active = S.get<int32_t>(ncomp);
+        int32_t *sel = S.get<int32_t>(ncomp);
+        int2 *last = S.get<int2>(ncomp);
+        if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+        cudaMemcpyAsync(r, cstart, sizeof(int32_t) * ncomp, cudaMemcpyDeviceToDevice, st);
+        if ((rc = search(r, e, last)) != PARS3_OK) return rc;
+        last_min_kernel<<<grid_for(static_cast<int64_t>(ncomp) * 32, G), G, 0, st>>>(ncomp, last, cm, rank, by_deg, x);
+        fill_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, 1, active);
+        for (int round = 0;; ++round) {
+            select_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, active, r, x, sel);
+            if ((rc = search(sel, ex, last)) != PARS3_OK) return rc;
+            last_min_kernel<<<grid_for(static_cast<int64_t>(ncomp) * 32, G), G, 0, st>>>(ncomp, last, cm, rank, by_deg, y);
+            cudaMemsetAsync(&ctl->active, 0, sizeof(int), st);
+            peripheral_step_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, active, r, e, x, ex, y, ctl);
+            if ((rc = fetch_ctl(ctl, &hc, st)) != PARS3_OK) return rc;
+            if (hc.active == 0) break;
+            if (round > n) return PARS3_ECUDA;   // each round raises an eccentricity, which is below n
+        }
+        root = r;
+    }
+    if ((rc = search(root, nullptr, nullptr)) != PARS3_OK) return rc;
+
+    // reverse, bandwidths, guard
+    perm_kernel<<<grid_for(n, G), G, 0, st>>>(n, cm, pos, perm, ctl);
+    bandwidth_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, ci, pos, ctl);
+    if ((rc = fetch_ctl(ctl, &hc, st)) != PARS3_OK) return rc;
+    if (hc.err & kErrPlaced) return PARS3_ECUDA;
+    int64_t b0 = static_cast<int64_t>(hc.bw0), b1 = static_cast<int64_t>(hc.bw1);
+    if ((flags & PARS3_RCM_GUARD) && b1 > b0) {
+        iota_kernel<<<grid_for(n, G), G, 0, st>>>(n, perm);
+        b1 = b0;
+        if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(ce);
+    }
+    if (bw_before) *bw_before = b0;
+    if (bw_after) *bw_after = b1;
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+}  // namespace pars3
+
+extern "C" int pars3_reorder_device(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t flags,
+                                    int32_t *perm_out, int64_t *bw_before, int64_t *bw_after, void *stream) {
+    return pars3::reorder_device(n, rowptr, col, flags, perm_out, bw_before, bw_after,
+                                 static_cast<cudaStream_t>(stream));
+}

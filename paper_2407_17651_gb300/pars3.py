@@ -101,6 +101,7 @@ def lib() -> C.CDLL:
         "pars3_strerror": ([C.c_int], C.c_char_p),
         "pars3_version": ([P, P, P], C.c_int),
         "pars3_reorder": ([i32, P, P, i32, P, P, P], C.c_int),
+        "pars3_reorder_device": ([i32, P, P, i32, P, P, P, P], C.c_int),
         "pars3_split": ([i32, P, P, P, P, P, P], C.c_int),
         "pars3_split_export": ([P, P], C.c_int),
         "pars3_info_get": ([P, P], C.c_int),
@@ -132,7 +133,8 @@ def exported_symbols():
     return ["pars3_strerror", "pars3_version", "pars3_reorder", "pars3_split", "pars3_split_export",
             "pars3_info_get", "pars3_layout_check", "pars3_upload", "pars3_spmv", "pars3_spmm",
             "pars3_spmm_batched", "pars3_mrs", "pars3_permute", "pars3_unpermute", "pars3_spmv_host",
-            "pars3_check", "pars3_autotune", "pars3_free", "pars3_spmv_noalloc", "pars3_fp64_fma_rate"]
+            "pars3_check", "pars3_autotune", "pars3_free", "pars3_spmv_noalloc", "pars3_fp64_fma_rate",
+            "pars3_reorder_device"]
 
 
 def _chk(rc: int, where: str):
@@ -199,6 +201,24 @@ def pars3_reorder(n: int, rowptr, col, flags: int = RCM_GUARD):
          "pars3_reorder")
     return perm, b0.value, b1.value
 
+
+
+def pars3_reorder_device(n: int, rowptr, col, flags: int = RCM_GUARD, stream=None):
+    """The same ordering as pars3_reorder, computed on the GPU: rowptr / col
+    are int32 CUDA tensors of the strict lower pattern.  Returns (perm new->old
+    as an int32 CUDA tensor, bandwidth before, bandwidth after)."""
+    import torch
+    for t, what in ((rowptr, "rowptr"), (col, "col")):
+        if t.dtype != torch.int32:
+            raise ValueError(f"{what} must be int32")
+    if rowptr.numel() != int(n) + 1:
+        raise ValueError("rowptr must hold n + 1 entries")
+    perm = torch.empty(max(int(n), 0), dtype=torch.int32, device=rowptr.device)
+    b0, b1 = C.c_int64(), C.c_int64()
+    colp = _dptr(col) if col.numel() else None
+    _chk(lib().pars3_reorder_device(int(n), _dptr(rowptr), colp, int(flags), _dptr(perm) if n else None,
+                                    C.byref(b0), C.byref(b1), _stream(stream)), "pars3_reorder_device")
+    return perm, b0.value, b1.value
 
 class Handle:
     """Owns a pars3_handle*; released by pars3_free on close/garbage collection."""
