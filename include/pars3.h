@@ -211,6 +211,22 @@ int pars3_reorder(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t 
 int pars3_reorder_device(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t flags,
                          int32_t *perm_out, int64_t *bw_before, int64_t *bw_after, void *stream);
 
+/* pars3_reorder_device_batched -- pars3_reorder_device for `count` matrices
+ * in one call, searched together (the work is the block-diagonal union of
+ * the patterns, so the number of sequential level steps is that of the
+ * deepest matrix, not the sum over matrices).  n[count], rowptr[count],
+ * col[count], perm_out[count] are HOST arrays; rowptr[m], col[m] and
+ * perm_out[m] are DEVICE arrays of matrix m as for pars3_reorder_device
+ * (col[m] and perm_out[m] may be NULL when matrix m has no entries or no
+ * vertices).  bw_before/bw_after are host arrays of count values, or NULL.
+ * Every perm_out[m] equals pars3_reorder of matrix m alone with the same
+ * flags.  The union must have fewer than 2^31 vertices and 2^30 entries.
+ * Errors as for pars3_reorder_device; ENOTSKEW when any matrix fails the
+ * check (then no perm_out is written). */
+int pars3_reorder_device_batched(int32_t count, const int32_t *n, const int32_t *const *rowptr,
+                                 const int32_t *const *col, int32_t flags, int32_t *const *perm_out,
+                                 int64_t *bw_before, int64_t *bw_after, void *stream);
+
 /* pars3_split -- Sec. 3.1.2 and Figs. 7-8: reorder S by perm (new -> old;
  * NULL = identity), re-triangularize (an entry landing above the diagonal is
  * stored mirrored with its sign flipped, Eq. 2), classify every stored entry

@@ -138,20 +138,31 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const int32_t *__res
 
 // ------------------------------------------------------------ validation
 
-// Rows must satisfy 0 <= rowptr[i] <= rowptr[i+1] <= nnz and hold strictly
-// increasing columns below the diagonal; entries are read only inside a row
+// The pattern may be the block-diagonal union of several matrices: vertex i
+// belongs to matrix mid[i] (all to matrix 0 when mid is null), whose
+// vertices are [moff[m], moff[m+1]) and entries [eoff[m], eoff[m+1]).
+struct Blocks {
+    const int32_t *mid;
+    const int32_t *moff, *eoff;   // device, count + 1 each
+};
+
+// Rows must satisfy eoff[m] <= rowptr[i] <= rowptr[i+1] <= eoff[m+1] (with
+// rowptr at the matrix's first row equal to eoff[m]) and hold strictly
+// increasing columns in [moff[m], i); entries are read only inside a row
 // whose bounds passed.  Also writes the row of every entry and the row
 // lengths (the lower part of each degree).
-__global__ void validate_kernel(int n, int nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void validate_kernel(int n, Blocks B, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                 int32_t *__restrict__ rowof, int32_t *__restrict__ deg, Ctl *ctl) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int m = B.mid ? B.mid[i] : 0;
+        const int v0 = B.moff[m], e0 = B.eoff[m], e1 = B.eoff[m + 1];
         const int a = rp[i], b = rp[i + 1];
-        if ((i == 0 && a != 0) || a < 0 || b < a || b > nnz) {
+        if ((i == v0 && a != e0) || a < e0 || b < a || b > e1) {
             atomicOr(&ctl->err, kErrPattern);
             deg[i] = 0;
             continue;
         }
-        int prev = -1;
+        int prev = v0 - 1;
         bool ok = true;
         for (int k = a; k < b; ++k) {
             const int j = ci[k];
@@ -568,34 +579,97 @@ __global__ void select_kernel(int ncomp, const int32_t *__restrict__ active, con
         out[c] = active[c] ? x[c] : r[c];
 }
 
+
 // ------------------------------------------------------------ result
 
-__global__ void perm_kernel(int n, const int32_t *__restrict__ cm, const int32_t *__restrict__ pos,
-                            int32_t *__restrict__ perm, Ctl *ctl) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        perm[k] = cm[n - 1 - k];
-        if (pos[k] < 0) atomicOr(&ctl->err, kErrPlaced);
+// Each matrix's vertices hold the queue positions [moff[m], moff[m+1]) (its
+// components come first in rank order); its permutation is that segment
+// reversed, in the matrix's own numbering.
+__global__ void perm_kernel(int n, Blocks B, const int32_t *__restrict__ cm, const int32_t *__restrict__ pos,
+                            int32_t *const *__restrict__ perms, Ctl *ctl) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const int m = B.mid ? B.mid[g] : 0;
+        const int o = B.moff[m], nm = B.moff[m + 1] - o;
+        const int k = g - o;
+        perms[m][k] = cm[o + nm - 1 - k] - o;
+        if (pos[g] < 0) atomicOr(&ctl->err, kErrPlaced);
     }
 }
 
-// bandwidths before (i - j over stored (i, j)) and after (|pos i - pos j|,
-// the same distance in the reversed order)
-__global__ void bandwidth_kernel(int nnz, const int32_t *__restrict__ rowof, const int32_t *__restrict__ ci,
-                                 const int32_t *__restrict__ pos, Ctl *ctl) {
-    unsigned m0 = 0, m1 = 0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
-        const int i = rowof[k], j = ci[k];
-        m0 = max(m0, static_cast<unsigned>(i - j));
-        m1 = max(m1, static_cast<unsigned>(abs(pos[i] - pos[j])));
-    }
-    m0 = __reduce_max_sync(0xffffffffu, m0);
-    m1 = __reduce_max_sync(0xffffffffu, m1);
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(&ctl->bw0, static_cast<unsigned long long>(m0));
-        atomicMax(&ctl->bw1, static_cast<unsigned long long>(m1));
+// Bandwidths of every matrix before (i - j over its stored (i, j)) and
+// after (|pos i - pos j|, the same distance in the reversed order):
+// bw[2m] and bw[2m+1].
+__global__ void bandwidth_kernel(int nnz, const int32_t *mid, const int32_t *__restrict__ rowof,
+                                 const int32_t *__restrict__ ci, const int32_t *__restrict__ pos,
+                                 unsigned long long *bw) {
+    const int lane = threadIdx.x & 31;
+    for (int k0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; k0 < nnz; k0 += gridDim.x * blockDim.x) {
+        const int k = k0 + lane;
+        unsigned d0 = 0, d1 = 0;
+        int m = -1;
+        if (k < nnz) {
+            const int i = rowof[k], j = ci[k];
+            m = mid ? mid[i] : 0;
+            d0 = static_cast<unsigned>(i - j);
+            d1 = static_cast<unsigned>(abs(pos[i] - pos[j]));
+        }
+        const int m0 = __shfl_sync(0xffffffffu, m, 0);
+        if (__all_sync(0xffffffffu, m == m0 || m < 0)) {   // one matrix in this warp
+            d0 = __reduce_max_sync(0xffffffffu, d0);
+            d1 = __reduce_max_sync(0xffffffffu, d1);
+            if (lane == 0 && m0 >= 0) {
+                atomicMax(&bw[2 * m0], static_cast<unsigned long long>(d0));
+                atomicMax(&bw[2 * m0 + 1], static_cast<unsigned long long>(d1));
+            }
+        } else if (m >= 0) {
+            atomicMax(&bw[2 * m], static_cast<unsigned long long>(d0));
+            atomicMax(&bw[2 * m + 1], static_cast<unsigned long long>(d1));
+        }
     }
 }
 
+// ------------------------------------------------------------ batches
+
+// nnz of every matrix: nz[m] = rowptr_m[n_m]
+__global__ void nnz_kernel(int count, const int32_t *const *__restrict__ rps, const int32_t *__restrict__ ns,
+                           int32_t *__restrict__ nz) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < count; m += gridDim.x * blockDim.x)
+        nz[m] = rps[m][ns[m]];
+}
+
+__device__ __forceinline__ int block_of(const int32_t *__restrict__ off, int count, int x) {
+    int lo = 0, hi = count;   // off[lo] <= x < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// the union's row pointers (each matrix's shifted by its first entry) and
+// the matrix of every vertex (the search lands on the matrix whose range
+// holds g, so matrices without vertices are passed over)
+__global__ void union_rows_kernel(int n, int count, const int32_t *const *__restrict__ rps,
+                                  const int32_t *__restrict__ moff, const int32_t *__restrict__ eoff,
+                                  int32_t *__restrict__ rp, int32_t *__restrict__ mid) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const int m = block_of(moff, count, g);
+        mid[g] = m;
+        rp[g] = rps[m][g - moff[m]] + eoff[m];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) rp[n] = eoff[count];
+}
+
+// the union's columns: each matrix's shifted by its first vertex
+__global__ void union_cols_kernel(int nnz, int count, const int32_t *const *__restrict__ cis,
+                                  const int32_t *__restrict__ moff, const int32_t *__restrict__ eoff,
+                                  int32_t *__restrict__ ci) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x) {
+        const int m = block_of(eoff, count, e);
+        ci[e] = cis[m][e - eoff[m]] + moff[m];
+    }
+}
 
 // ------------------------------------------------------------ host side
 
@@ -625,7 +699,7 @@ int grid_for(int64_t items, int per_block) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, 8LL * sm_count())));
 }
 
-int bits_for(int n) {   // bits needed for the values 0 .. n-1
+int bits_for(int64_t n) {   // bits needed for the values 0 .. n-1
     int b = 0;
     while (b < 31 && (1LL << b) < n) ++b;
     return b;
@@ -648,45 +722,44 @@ void radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int count,
     *vo = v0;
 }
 
-int fetch_ctl(const Ctl *d, Ctl *h, cudaStream_t st) {
-    cudaError_t e = cudaMemcpyAsync(h, d, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+int fetch(void *h, const void *d, size_t bytes, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(e);
 }
 
-int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flags, int32_t *perm,
-                   int64_t *bw_before, int64_t *bw_after, cudaStream_t st) {
-    if (n < 0 || (flags & ~(PARS3_RCM_GUARD | PARS3_RCM_PERIPHERAL | PARS3_RCM_LOCAL))) return PARS3_EINVAL;
-    if (flags & PARS3_RCM_LOCAL) return PARS3_EUNSUPPORTED;
-    if (bw_before) *bw_before = 0;
-    if (bw_after) *bw_after = 0;
-    if (n == 0) return PARS3_OK;
-    if (!rp || !perm) return PARS3_EINVAL;
-    int32_t nnz = 0;
-    cudaError_t ce = cudaMemcpyAsync(&nnz, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) return cuda_status(ce);
-    if (nnz < 0) return PARS3_ENOTSKEW;
-    if (nnz > 0 && !ci) return PARS3_EINVAL;
-    if (nnz > INT32_MAX / 2) return PARS3_EUNSUPPORTED;   // 2 nnz directed edges are indexed by int32
-    const int m2 = 2 * nnz;
-    const int G = kThreads;
+// One pattern (the union of `count` matrices when count > 1, see Blocks) in
+// device memory; perms[m] (device array of device pointers) receive the
+// orderings, bw0/bw1 (host, count each) the bandwidths.
+struct Problem {
+    int n, nnz, count;
+    const int32_t *rp, *ci;
+    Blocks B;
+    int32_t *const *perms;
+    std::vector<int32_t> moff_h;   // host copy of B.moff
+    std::vector<int32_t *> perms_h;
+};
 
+int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaStream_t st) {
+    const int n = P.n, nnz = P.nnz, m2 = 2 * P.nnz;
+    const int G = kThreads;
     Scratch S;
     Ctl *ctl = S.get<Ctl>(1);
     int32_t *rowof = S.get<int32_t>(nnz), *deg = S.get<int32_t>(n + 1);
     if (S.err() != cudaSuccess) return PARS3_ENOMEM;
     Ctl hc{};
-    if ((ce = cudaMemsetAsync(ctl, 0, sizeof(Ctl), st)) != cudaSuccess) return cuda_status(ce);
+    cudaError_t ce = cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);
+    if (ce != cudaSuccess) return cuda_status(ce);
 
     // validation, then degrees
-    validate_kernel<<<grid_for(n, G), G, 0, st>>>(n, nnz, rp, ci, rowof, deg, ctl);
-    int rc = fetch_ctl(ctl, &hc, st);
+    validate_kernel<<<grid_for(n, G), G, 0, st>>>(n, P.B, P.rp, P.ci, rowof, deg, ctl);
+    int rc = fetch(&hc, ctl, sizeof(Ctl), st);
     if (rc != PARS3_OK) return rc;
     if (hc.err) return PARS3_ENOTSKEW;
-    degree_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, ci, deg);
+    degree_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, P.ci, deg);
 
-    // vertices in (degree, index) order: a stable sort by degree of 0 .. n-1
+    // vertices in (matrix, degree, index) order: stable sorts of 0 .. n-1 by
+    // degree, then by matrix
     const int nbits = bits_for(n);
     const int sort_max = std::max(n, m2);
     const int ntiles = (sort_max + kSortTile - 1) / kSortTile;
@@ -703,6 +776,15 @@ int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flag
     cudaMemcpyAsync(ka, deg, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
     iota_kernel<<<grid_for(n, G), G, 0, st>>>(n, va);
     radix_sort(ka, va, kb, vb, n, nbits, hist, hoff, st, &ko, &vo);
+    if (P.B.mid) {
+        uint32_t *kx = ko == ka ? kb : ka;
+        int32_t *vx = vo == va ? vb : va;
+        gather_kernel<<<grid_for(n, G), G, 0, st>>>(n, vo, P.B.mid, reinterpret_cast<int32_t *>(kx));
+        uint32_t *k2;
+        int32_t *v2;
+        radix_sort(kx, vo, ko, vx, n, bits_for(P.count), hist, hoff, st, &k2, &v2);
+        vo = v2;
+    }
     cudaMemcpyAsync(by_deg, vo, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
     rank_kernel<<<grid_for(n, G), G, 0, st>>>(n, by_deg, rank);
 
@@ -710,7 +792,7 @@ int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flag
     // listed source by source in rank order, then sorted stably by target
     scan_kernel<<<1, kScanThreads, 0, st>>>(deg, arp, nullptr, n);
     cudaMemsetAsync(cur, 0, sizeof(int32_t) * n, st);
-    scatter_adj_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, ci, arp, cur, aun);
+    scatter_adj_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, P.ci, arp, cur, aun);
     gather_kernel<<<grid_for(n, G), G, 0, st>>>(n, by_deg, deg, sdeg);
     scan_kernel<<<1, kScanThreads, 0, st>>>(sdeg, epos, nullptr, n);
     edges_by_rank_kernel<<<grid_for(static_cast<int64_t>(n) * 32, G), G, 0, st>>>(n, by_deg, arp, aun, epos, ka, va);
@@ -722,7 +804,7 @@ int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flag
     int32_t *csize = S.get<int32_t>(n), *flag = S.get<int32_t>(n), *sidx = S.get<int32_t>(n + 1);
     if (S.err() != cudaSuccess) return PARS3_ENOMEM;
     iota_kernel<<<grid_for(n, G), G, 0, st>>>(n, parent);
-    hook_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, ci, parent, ctl);
+    hook_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, P.ci, parent, ctl);
     fill_kernel<<<grid_for(n, G), G, 0, st>>>(n, INT_MAX, cmin);
     cudaMemsetAsync(csize, 0, sizeof(int32_t) * n, st);
     comp_kernel<<<grid_for(n, G), G, 0, st>>>(n, parent, rank, comp, cmin, csize);
@@ -730,7 +812,7 @@ int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flag
     scan_kernel<<<1, kScanThreads, 0, st>>>(flag, sidx, nullptr, n);
     int32_t ncomp = 0;
     cudaMemcpyAsync(&ncomp, sidx + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-    if ((rc = fetch_ctl(ctl, &hc, st)) != PARS3_OK) return rc;
+    if ((rc = fetch(&hc, ctl, sizeof(Ctl), st)) != PARS3_OK) return rc;
     if (hc.err & kErrHook) return PARS3_ETIMEOUT;
     if (ncomp < 1 || ncomp > n) return PARS3_ECUDA;
     int32_t *cstart = S.get<int32_t>(ncomp), *csz = S.get<int32_t>(ncomp), *cbase = S.get<int32_t>(ncomp + 1);
@@ -759,7 +841,7 @@ int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flag
                 write_kernel<<<wg, G, 0, st>>>(ctl, b, act[b], fpre[b], coff, cm, arp, adj, claim, pos);
                 b ^= 1;
             }
-            int r2 = fetch_ctl(ctl, &hc, st);
+            const int r2 = fetch(&hc, ctl, sizeof(Ctl), st);
             if (r2 != PARS3_OK) return r2;
             if (hc.nact[b] == 0) return PARS3_OK;
             if (steps > static_cast<int64_t>(n) + kLevelsPerCheck) return PARS3_ECUDA;   // more levels than vertices
@@ -774,17 +856,18 @@ int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flag
         int32_t *sel = S.get<int32_t>(ncomp);
         int2 *last = S.get<int2>(ncomp);
         if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+        const int cg = grid_for(static_cast<int64_t>(ncomp) * 32, G);
         cudaMemcpyAsync(r, cstart, sizeof(int32_t) * ncomp, cudaMemcpyDeviceToDevice, st);
         if ((rc = search(r, e, last)) != PARS3_OK) return rc;
-        last_min_kernel<<<grid_for(static_cast<int64_t>(ncomp) * 32, G), G, 0, st>>>(ncomp, last, cm, rank, by_deg, x);
+        last_min_kernel<<<cg, G, 0, st>>>(ncomp, last, cm, rank, by_deg, x);
         fill_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, 1, active);
         for (int round = 0;; ++round) {
             select_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, active, r, x, sel);
             if ((rc = search(sel, ex, last)) != PARS3_OK) return rc;
-            last_min_kernel<<<grid_for(static_cast<int64_t>(ncomp) * 32, G), G, 0, st>>>(ncomp, last, cm, rank, by_deg, y);
+            last_min_kernel<<<cg, G, 0, st>>>(ncomp, last, cm, rank, by_deg, y);
             cudaMemsetAsync(&ctl->active, 0, sizeof(int), st);
             peripheral_step_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, active, r, e, x, ex, y, ctl);
-            if ((rc = fetch_ctl(ctl, &hc, st)) != PARS3_OK) return rc;
+            if ((rc = fetch(&hc, ctl, sizeof(Ctl), st)) != PARS3_OK) return rc;
             if (hc.active == 0) break;
             if (round > n) return PARS3_ECUDA;   // each round raises an eccentricity, which is below n
         }
@@ -792,20 +875,117 @@ int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flag
     }
     if ((rc = search(root, nullptr, nullptr)) != PARS3_OK) return rc;
 
-    // reverse, bandwidths, guard
-    perm_kernel<<<grid_for(n, G), G, 0, st>>>(n, cm, pos, perm, ctl);
-    bandwidth_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, ci, pos, ctl);
-    if ((rc = fetch_ctl(ctl, &hc, st)) != PARS3_OK) return rc;
+    // reverse per matrix, bandwidths, guard
+    unsigned long long *bw = S.get<unsigned long long>(2 * static_cast<size_t>(P.count));
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    cudaMemsetAsync(bw, 0, sizeof(unsigned long long) * 2 * P.count, st);
+    perm_kernel<<<grid_for(n, G), G, 0, st>>>(n, P.B, cm, pos, P.perms, ctl);
+    bandwidth_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, P.B.mid, rowof, P.ci, pos, bw);
+    std::vector<unsigned long long> bw_h(2 * static_cast<size_t>(P.count));
+    cudaMemcpyAsync(bw_h.data(), bw, sizeof(unsigned long long) * bw_h.size(), cudaMemcpyDeviceToHost, st);
+    if ((rc = fetch(&hc, ctl, sizeof(Ctl), st)) != PARS3_OK) return rc;
     if (hc.err & kErrPlaced) return PARS3_ECUDA;
-    int64_t b0 = static_cast<int64_t>(hc.bw0), b1 = static_cast<int64_t>(hc.bw1);
-    if ((flags & PARS3_RCM_GUARD) && b1 > b0) {
-        iota_kernel<<<grid_for(n, G), G, 0, st>>>(n, perm);
-        b1 = b0;
-        if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(ce);
+    bool reset = false;
+    for (int m = 0; m < P.count; ++m) {
+        int64_t b0 = static_cast<int64_t>(bw_h[2 * m]), b1 = static_cast<int64_t>(bw_h[2 * m + 1]);
+        const int nm = P.moff_h[m + 1] - P.moff_h[m];
+        if ((flags & PARS3_RCM_GUARD) && b1 > b0) {
+            if (nm > 0) iota_kernel<<<grid_for(nm, G), G, 0, st>>>(nm, P.perms_h[m]);
+            b1 = b0;
+            reset = true;
+        }
+        if (bw0) bw0[m] = b0;
+        if (bw1) bw1[m] = b1;
     }
-    if (bw_before) *bw_before = b0;
-    if (bw_after) *bw_after = b1;
+    if (reset && (ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(ce);
     return cuda_status(cudaGetLastError());
+}
+
+int check_flags(int32_t flags) {
+    if (flags & ~(PARS3_RCM_GUARD | PARS3_RCM_PERIPHERAL | PARS3_RCM_LOCAL)) return PARS3_EINVAL;
+    if (flags & PARS3_RCM_LOCAL) return PARS3_EUNSUPPORTED;
+    return PARS3_OK;
+}
+
+int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flags, int32_t *perm,
+                   int64_t *bw_before, int64_t *bw_after, cudaStream_t st) {
+    if (n < 0) return PARS3_EINVAL;
+    int rc = check_flags(flags);
+    if (rc != PARS3_OK) return rc;
+    if (bw_before) *bw_before = 0;
+    if (bw_after) *bw_after = 0;
+    if (n == 0) return PARS3_OK;
+    if (!rp || !perm) return PARS3_EINVAL;
+    int32_t nnz = 0;
+    if ((rc = fetch(&nnz, rp + n, sizeof(int32_t), st)) != PARS3_OK) return rc;
+    if (nnz < 0) return PARS3_ENOTSKEW;
+    if (nnz > 0 && !ci) return PARS3_EINVAL;
+    if (nnz >= (1 << 30)) return PARS3_EUNSUPPORTED;   // 2 nnz directed edges are indexed by int32
+    Scratch S;
+    int32_t *off = S.get<int32_t>(4);
+    int32_t **perms = S.get<int32_t *>(1);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    const int32_t off_h[4] = {0, n, 0, nnz};   // moff = {0, n}, eoff = {0, nnz}
+    cudaError_t ce = cudaMemcpyAsync(off, off_h, sizeof(off_h), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(perms, &perm, sizeof(int32_t *), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);   // the host sources above are stack memory
+    if (ce != cudaSuccess) return cuda_status(ce);
+    Problem P{n, nnz, 1, rp, ci, Blocks{nullptr, off, off + 2}, perms, {0, n}, {perm}};
+    return rcm_core(P, flags, bw_before, bw_after, st);
+}
+
+int reorder_device_batched(int32_t count, const int32_t *ns, const int32_t *const *rps,
+                           const int32_t *const *cis, int32_t flags, int32_t *const *perms, int64_t *bw_before,
+                           int64_t *bw_after, cudaStream_t st) {
+    if (count < 0 || (count > 0 && (!ns || !rps || !cis || !perms))) return PARS3_EINVAL;
+    int rc = check_flags(flags);
+    if (rc != PARS3_OK) return rc;
+    if (count == 0) return PARS3_OK;
+    std::vector<int32_t> moff(count + 1, 0), eoff(count + 1, 0);
+    for (int m = 0; m < count; ++m) {
+        if (ns[m] < 0 || !rps[m] || (ns[m] > 0 && !perms[m])) return PARS3_EINVAL;
+        if (bw_before) bw_before[m] = 0;
+        if (bw_after) bw_after[m] = 0;
+        if (static_cast<int64_t>(moff[m]) + ns[m] > INT32_MAX) return PARS3_EUNSUPPORTED;
+        moff[m + 1] = moff[m] + ns[m];
+    }
+    Scratch S;
+    int32_t *ns_d = S.get<int32_t>(count), *nz_d = S.get<int32_t>(count);
+    const int32_t **rps_d = S.get<const int32_t *>(count), **cis_d = S.get<const int32_t *>(count);
+    int32_t **perms_d = S.get<int32_t *>(count);
+    int32_t *off_d = S.get<int32_t>(2 * (static_cast<size_t>(count) + 1));
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    cudaError_t ce = cudaMemcpyAsync(ns_d, ns, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(rps_d, rps, sizeof(int32_t *) * count, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(cis_d, cis, sizeof(int32_t *) * count, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(perms_d, perms, sizeof(int32_t *) * count, cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    nnz_kernel<<<grid_for(count, kThreads), kThreads, 0, st>>>(count, rps_d, ns_d, nz_d);
+    std::vector<int32_t> nz(count);
+    if ((rc = fetch(nz.data(), nz_d, sizeof(int32_t) * count, st)) != PARS3_OK) return rc;
+    for (int m = 0; m < count; ++m) {
+        if (nz[m] < 0) return PARS3_ENOTSKEW;
+        if (nz[m] > 0 && !cis[m]) return PARS3_EINVAL;
+        if (static_cast<int64_t>(eoff[m]) + nz[m] >= (1 << 30)) return PARS3_EUNSUPPORTED;
+        eoff[m + 1] = eoff[m] + nz[m];
+    }
+    const int n = moff[count], nnz = eoff[count];
+    if (n == 0) return PARS3_OK;
+    int32_t *rp = S.get<int32_t>(n + 1), *ci = S.get<int32_t>(nnz), *mid = S.get<int32_t>(n);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    int32_t *moff_d = off_d, *eoff_d = off_d + count + 1;
+    ce = cudaMemcpyAsync(moff_d, moff.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(eoff_d, eoff.data(), sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    union_rows_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(n, count, rps_d, moff_d, eoff_d, rp, mid);
+    union_cols_kernel<<<grid_for(nnz, kThreads), kThreads, 0, st>>>(nnz, count, cis_d, moff_d, eoff_d, ci);
+    Problem P{n, nnz, count, rp, ci, Blocks{mid, moff_d, eoff_d}, perms_d, moff,
+              std::vector<int32_t *>(perms, perms + count)};
+    rc = rcm_core(P, flags, bw_before, bw_after, st);
+    // the host vectors copied from above must outlive the copies
+    const cudaError_t se = cudaStreamSynchronize(st);
+    return rc != PARS3_OK ? rc : cuda_status(se);
 }
 
 }  // namespace
@@ -815,4 +995,11 @@ extern "C" int pars3_reorder_device(int32_t n, const int32_t *rowptr, const int3
                                     int32_t *perm_out, int64_t *bw_before, int64_t *bw_after, void *stream) {
     return pars3::reorder_device(n, rowptr, col, flags, perm_out, bw_before, bw_after,
                                  static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int pars3_reorder_device_batched(int32_t count, const int32_t *n, const int32_t *const *rowptr,
+                                            const int32_t *const *col, int32_t flags, int32_t *const *perm_out,
+                                            int64_t *bw_before, int64_t *bw_after, void *stream) {
+    return pars3::reorder_device_batched(count, n, rowptr, col, flags, perm_out, bw_before, bw_after,
+                                         static_cast<cudaStream_t>(stream));
 }

@@ -102,6 +102,7 @@ def lib() -> C.CDLL:
         "pars3_version": ([P, P, P], C.c_int),
         "pars3_reorder": ([i32, P, P, i32, P, P, P], C.c_int),
         "pars3_reorder_device": ([i32, P, P, i32, P, P, P, P], C.c_int),
+        "pars3_reorder_device_batched": ([i32, P, P, P, i32, P, P, P, P], C.c_int),
         "pars3_split": ([i32, P, P, P, P, P, P], C.c_int),
         "pars3_split_export": ([P, P], C.c_int),
         "pars3_info_get": ([P, P], C.c_int),
@@ -134,7 +135,7 @@ def exported_symbols():
             "pars3_info_get", "pars3_layout_check", "pars3_upload", "pars3_spmv", "pars3_spmm",
             "pars3_spmm_batched", "pars3_mrs", "pars3_permute", "pars3_unpermute", "pars3_spmv_host",
             "pars3_check", "pars3_autotune", "pars3_free", "pars3_spmv_noalloc", "pars3_fp64_fma_rate",
-            "pars3_reorder_device"]
+            "pars3_reorder_device", "pars3_reorder_device_batched"]
 
 
 def _chk(rc: int, where: str):
@@ -219,6 +220,32 @@ def pars3_reorder_device(n: int, rowptr, col, flags: int = RCM_GUARD, stream=Non
     _chk(lib().pars3_reorder_device(int(n), _dptr(rowptr), colp, int(flags), _dptr(perm) if n else None,
                                     C.byref(b0), C.byref(b1), _stream(stream)), "pars3_reorder_device")
     return perm, b0.value, b1.value
+
+
+def pars3_reorder_device_batched(patterns, flags: int = RCM_GUARD, stream=None):
+    """pars3_reorder_device for a list of (n, rowptr, col) with int32 CUDA
+    tensors, all searched in one call.  Returns a list of (perm CUDA tensor,
+    bandwidth before, bandwidth after)."""
+    import torch
+    count = len(patterns)
+    ns = np.array([int(n) for n, _, _ in patterns], dtype=np.int32)
+    perms, keep = [], []
+    for (n, rp, ci) in patterns:
+        if rp.dtype != torch.int32 or ci.dtype != torch.int32:
+            raise ValueError("rowptr and col must be int32")
+        if rp.numel() != int(n) + 1:
+            raise ValueError("rowptr must hold n + 1 entries")
+        perms.append(torch.empty(max(int(n), 0), dtype=torch.int32, device=rp.device))
+        keep += [rp, ci]
+    ptrs = lambda ts: (C.c_void_p * max(count, 1))(*[t.data_ptr() if t.numel() else None for t in ts])
+    rps = ptrs([p[1] for p in patterns])
+    cis = ptrs([p[2] for p in patterns])
+    pps = ptrs(perms)
+    b0 = np.zeros(max(count, 1), dtype=np.int64)
+    b1 = np.zeros(max(count, 1), dtype=np.int64)
+    _chk(lib().pars3_reorder_device_batched(count, _p(ns) if count else None, rps, cis, int(flags), pps,
+                                            _p(b0), _p(b1), _stream(stream)), "pars3_reorder_device_batched")
+    return [(perms[m], int(b0[m]), int(b1[m])) for m in range(count)]
 
 class Handle:
     """Owns a pars3_handle*; released by pars3_free on close/garbage collection."""

@@ -165,3 +165,55 @@ def test_full_size_bit_exact(name):
 def test_all_batched_matrices_bit_exact():
     for m, shp in enumerate(W.config4_shapes()):
         _check(W.config4_matrix(m, shp), P.RCM_GUARD)
+
+
+def _batch_cases():
+    cases = [_from_pairs(0, [], "empty"), _from_pairs(1, [], "one vertex"), _from_pairs(9, [], "no edges")]
+    cases += [_random_graph(int(n), int(2 * n), s) for s, n in enumerate((5, 17, 60, 150, 301))]
+    cases += [W.grid((21, 13), "normal", 11), W.grid((6, 5, 4), "normal", 12),
+              W.grid_plus_random((25, 25), 0.05, "normal", 13), W.rmat(10, 6000, seed=14),
+              _from_pairs(0, [], "empty again"), _from_pairs(40, [(0, i) for i in range(1, 40)], "star")]
+    return cases
+
+
+@pytest.mark.parametrize("flags", FLAGS)
+def test_batched_matches_oracle_per_matrix(flags):
+    cases = _batch_cases()
+    pats = [(A.n,) + _dev(A) for A in cases]
+    out = P.pars3_reorder_device_batched(pats, flags)
+    assert len(out) == len(cases)
+    for A, (perm, b0, b1) in zip(cases, out):
+        po, ob0, ob1 = O.rcm(A, guard=bool(flags & P.RCM_GUARD), peripheral=bool(flags & P.RCM_PERIPHERAL))
+        assert np.array_equal(perm.cpu().numpy(), po), (A.name, flags)
+        assert (b0, b1) == (ob0, ob1), (A.name, flags)
+
+
+def test_batched_rejects_a_bad_matrix():
+    import torch
+    cases = _batch_cases()[:6]
+    pats = [(A.n,) + _dev(A) for A in cases]
+    bad = (3, torch.tensor([0, 0, 1, 3], dtype=torch.int32, device="cuda"),
+           torch.tensor([0, 1, 1], dtype=torch.int32, device="cuda"))   # duplicate column in row 2
+    with pytest.raises(P.Pars3Error) as ei:
+        P.pars3_reorder_device_batched(pats[:3] + [bad] + pats[3:])
+    assert ei.value.code == P.ENOTSKEW
+    # a row pointer reaching past its own matrix's entries, into the next
+    # matrix's (rows 1 and 2 claim entries [0, 3) and [3, 2) of two stored)
+    bad2 = (3, torch.tensor([0, 0, 3, 2], dtype=torch.int32, device="cuda"),
+            torch.tensor([0, 1], dtype=torch.int32, device="cuda"))
+    with pytest.raises(P.Pars3Error) as ei:
+        P.pars3_reorder_device_batched([bad2] + pats)
+    assert ei.value.code == P.ENOTSKEW
+    out = P.pars3_reorder_device_batched(pats)   # still usable
+    assert len(out) == len(pats)
+    assert P.pars3_reorder_device_batched([]) == []
+
+
+@pytest.mark.slow
+def test_batched_all_64_matrices_in_one_call():
+    mats = [W.config4_matrix(m, shp) for m, shp in enumerate(W.config4_shapes())]
+    for flags in (P.RCM_GUARD, P.RCM_GUARD | P.RCM_PERIPHERAL):
+        out = P.pars3_reorder_device_batched([(A.n,) + _dev(A) for A in mats], flags)
+        for A, (perm, b0, b1) in zip(mats, out):
+            po, ob0, ob1 = O.rcm(A, guard=True, peripheral=bool(flags & P.RCM_PERIPHERAL))
+            assert np.array_equal(perm.cpu().numpy(), po) and (b0, b1) == (ob0, ob1), A.name
