@@ -237,6 +237,21 @@ int pars3_reorder_device_batched(int32_t count, const int32_t *n, const int32_t 
 int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
                 const int32_t *perm, const pars3_split_params *p, pars3_handle **out);
 
+/* pars3_split_device -- pars3_split with the canonical split computed on
+ * the GPU (Sec. 3.1.2, Eq. 2, Figs. 7-8): rowptr[n+1], col[nnz], val[nnz]
+ * (fp64) and perm[n] (new -> old, NULL = identity) are DEVICE arrays.  On
+ * the device the pattern, values and permutation are checked, the entries
+ * are permuted and re-triangularized (sign flip, Eq. 2), sorted by
+ * (row, col), classified for (T, W) and listed per tile and in CSR / CSC
+ * order; those arrays are copied into the new handle and its layout is then
+ * built on the host as pars3_split builds it.  The result -- every array
+ * pars3_split_export shows, and the layout -- is identical to pars3_split
+ * with the same inputs and parameters.  Runs on `stream` and returns after
+ * the handle is complete.  Allocates temporary device memory (about 90 bytes
+ * per stored entry).  Errors as for pars3_split, plus ECUDA. */
+int pars3_split_device(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                       const int32_t *perm, const pars3_split_params *p, pars3_handle **out, void *stream);
+
 /* Canonical split of a handle (host view; see pars3_canonical). */
 int pars3_split_export(const pars3_handle *h, pars3_canonical *out);
 

@@ -24,30 +24,15 @@
 // LSD radix sort (32-bit keys with 32-bit values), connected components by
 // union-find with hooking towards the smaller root, and single-block prefix
 // sums for sizes that live in device memory.
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <climits>
-#include <cstdint>
-#include <vector>
-
-#include "internal.h"
+#include "device_prims.cuh"
 
 namespace pars3 {
 namespace {
 
-constexpr int kThreads = 256;                       // block size of the element-wise kernels
-constexpr int kSortItems = 16;                      // keys per thread in a sort tile
-constexpr int kSortTile = kThreads * kSortItems;    // 4096 keys per tile
-constexpr int kSortWarps = kThreads / 32;
-constexpr int kSortWarpKeys = kSortTile / kSortWarps;   // 512 consecutive keys per warp
-constexpr int kScanThreads = 1024;                  // single-block prefix sums
-constexpr int kScanItems = 8;
 constexpr int kHookRounds = 1 << 22;                // bound on the union-find retries of one edge
 constexpr int kLevelsPerCheck = 8;                  // level steps between two host checks
 
-// error bits of Ctl::err
-constexpr int kErrPattern = 1;    // not a valid strict lower pattern
+// error bits of Ctl::err (bit kErrPattern is the pattern check's)
 constexpr int kErrHook = 2;       // union-find retries ran out
 constexpr int kErrPlaced = 4;     // a vertex was left without a position
 
@@ -56,7 +41,6 @@ struct Ctl {
     int nact[2];                  // unfinished frontier entries, per buffer
     int level;                    // level steps taken
     int active;                   // components still moving their start (pseudo-peripheral search)
-    unsigned long long bw0, bw1;  // bandwidth before / after
 };
 
 // One frontier entry: queue positions [fb, fe) are the current level of one
@@ -65,190 +49,11 @@ struct Front {
     int fb, fe, comp, pad;
 };
 
-__device__ __forceinline__ int lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return static_cast<int>(m);
-}
-
-// ------------------------------------------------------------ prefix sums
-
-// Exclusive prefix of one value per thread across a block of kScanThreads
-// threads; *total receives the block sum.  ws holds 32 partial sums.
-template <typename T>
-__device__ T block_excl_scan(T v, T *ws, T *total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T inc = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const T t = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += t;
-    }
-    if (lane == 31) ws[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        T w = lane < (kScanThreads >> 5) ? ws[lane] : T(0);
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const T t = __shfl_up_sync(0xffffffffu, w, d);
-            if (lane >= d) w += t;
-        }
-        ws[lane] = w;   // inclusive sums of the warp totals
-    }
-    __syncthreads();
-    const T before = (warp > 0 ? ws[warp - 1] : T(0)) + inc - v;
-    *total = ws[31];
-    __syncthreads();   // ws is reused by the next call
-    return before;
-}
-
-// out[0..len) = exclusive prefix sums of in[0..len), out[len] = the total.
-// Called by all kScanThreads threads of one block.
-__device__ void block_scan_array(const int32_t *in, int32_t *out, int len, int *ws) {
-    int carry = 0;
-    for (int base = 0; base < len; base += kScanThreads * kScanItems) {
-        const int i0 = base + threadIdx.x * kScanItems;
-        int v[kScanItems];
-        int s = 0;
-#pragma unroll
-        for (int t = 0; t < kScanItems; ++t) {
-            v[t] = i0 + t < len ? in[i0 + t] : 0;
-            s += v[t];
-        }
-        int total;
-        int run = carry + block_excl_scan<int>(s, ws, &total);
-#pragma unroll
-        for (int t = 0; t < kScanItems; ++t) {
-            if (i0 + t < len) out[i0 + t] = run;
-            run += v[t];
-        }
-        carry += total;
-    }
-    if (threadIdx.x == 0) out[len] = carry;
-}
-
-// Single-block exclusive scan; the length is *len_dev when len_dev is not
-// null (a size the host does not know), else len.
-__global__ void __launch_bounds__(kScanThreads) scan_kernel(const int32_t *__restrict__ in,
-                                                            int32_t *__restrict__ out, const int32_t *len_dev,
-                                                            int len) {
-    __shared__ int ws[32];
-    block_scan_array(in, out, len_dev ? *len_dev : len, ws);
-}
-
-// ------------------------------------------------------------ validation
-
-// The pattern may be the block-diagonal union of several matrices: vertex i
-// belongs to matrix mid[i] (all to matrix 0 when mid is null), whose
-// vertices are [moff[m], moff[m+1]) and entries [eoff[m], eoff[m+1]).
-struct Blocks {
-    const int32_t *mid;
-    const int32_t *moff, *eoff;   // device, count + 1 each
-};
-
-// Rows must satisfy eoff[m] <= rowptr[i] <= rowptr[i+1] <= eoff[m+1] (with
-// rowptr at the matrix's first row equal to eoff[m]) and hold strictly
-// increasing columns in [moff[m], i); entries are read only inside a row
-// whose bounds passed.  Also writes the row of every entry and the row
-// lengths (the lower part of each degree).
-__global__ void validate_kernel(int n, Blocks B, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                int32_t *__restrict__ rowof, int32_t *__restrict__ deg, Ctl *ctl) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int m = B.mid ? B.mid[i] : 0;
-        const int v0 = B.moff[m], e0 = B.eoff[m], e1 = B.eoff[m + 1];
-        const int a = rp[i], b = rp[i + 1];
-        if ((i == v0 && a != e0) || a < e0 || b < a || b > e1) {
-            atomicOr(&ctl->err, kErrPattern);
-            deg[i] = 0;
-            continue;
-        }
-        int prev = v0 - 1;
-        bool ok = true;
-        for (int k = a; k < b; ++k) {
-            const int j = ci[k];
-            if (j <= prev || j >= i) ok = false;
-            prev = j;
-            rowof[k] = i;
-        }
-        if (!ok) atomicOr(&ctl->err, kErrPattern);
-        deg[i] = b - a;
-    }
-}
-
 // deg[j] += number of rows holding column j (the upper part of each degree)
 __global__ void degree_kernel(int nnz, const int32_t *__restrict__ ci, int32_t *deg) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x)
         atomicAdd(&deg[ci[k]], 1);
 }
-
-// ------------------------------------------------------------ radix sort
-
-// hist[d * ntiles + t] = keys of tile t whose digit (key >> shift) & 255 is d
-__global__ void __launch_bounds__(kThreads) sort_hist_kernel(const uint32_t *__restrict__ key, int count,
-                                                             int shift, int ntiles, int32_t *__restrict__ hist) {
-    __shared__ int h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int t = blockIdx.x;
-    const int base = t * kSortTile;
-    for (int i = threadIdx.x; i < kSortTile; i += kThreads)
-        if (base + i < count) atomicAdd(&h[(key[base + i] >> shift) & 255], 1);
-    __syncthreads();
-    hist[threadIdx.x * ntiles + t] = h[threadIdx.x];
-}
-
-// Stable scatter of one tile: warp w owns keys [base + 512 w, base + 512 (w+1)),
-// taken 32 at a time in order; keys with equal digits are ranked by lane
-// within a round and by round within the warp, and warps are ranked by
-// index, so equal digits keep their input order.
-__global__ void __launch_bounds__(kThreads) sort_scatter_kernel(const uint32_t *__restrict__ key,
-                                                                const int32_t *__restrict__ val, int count,
-                                                                int shift, int ntiles,
-                                                                const int32_t *__restrict__ off,
-                                                                uint32_t *__restrict__ key_out,
-                                                                int32_t *__restrict__ val_out) {
-    __shared__ int cnt[kSortWarps][256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = lane; d < 256; d += 32) cnt[warp][d] = 0;
-    __syncwarp();
-    const int t = blockIdx.x;
-    const int base = t * kSortTile + warp * kSortWarpKeys;
-    for (int r = 0; r < kSortWarpKeys; r += 32) {
-        const int i = base + r + lane;
-        const bool ok = i < count;
-        const int d = ok ? static_cast<int>((key[i] >> shift) & 255) : 256;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (ok && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    {
-        const int d = threadIdx.x;   // kThreads == 256 digits
-        int run = off[d * ntiles + t];
-        for (int w = 0; w < kSortWarps; ++w) {
-            const int c = cnt[w][d];
-            cnt[w][d] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-    for (int r = 0; r < kSortWarpKeys; r += 32) {
-        const int i = base + r + lane;
-        const bool ok = i < count;
-        const uint32_t k = ok ? key[i] : 0u;
-        const int d = ok ? static_cast<int>((k >> shift) & 255) : 256;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (ok) {
-            const int p = cnt[warp][d] + __popc(peers & static_cast<unsigned>(lanemask_lt()));
-            key_out[p] = k;
-            val_out[p] = val[i];
-        }
-        __syncwarp();
-        if (ok && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
-        __syncwarp();
-    }
-}
-
 
 // ------------------------------------------------------------ components
 
@@ -356,21 +161,6 @@ __global__ void scatter_adj_kernel(int nnz, const int32_t *__restrict__ rowof, c
         aun[arp[j] + atomicAdd(&cur[j], 1)] = i;
     }
 }
-
-// sdeg[i] = degree of the vertex of rank i
-__global__ void gather_kernel(int n, const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
-                              int32_t *__restrict__ dst) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];
-}
-
-__global__ void iota_kernel(int n, int32_t *__restrict__ a) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
-}
-
-__global__ void fill_kernel(int n, int32_t v, int32_t *__restrict__ a) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
-}
-
 
 // ------------------------------------------------------------ level steps
 //
@@ -673,60 +463,6 @@ __global__ void union_cols_kernel(int nnz, int count, const int32_t *const *__re
 
 // ------------------------------------------------------------ host side
 
-// Device scratch of one call, released on every return path.
-class Scratch {
-public:
-    ~Scratch() {
-        for (void *p : ptrs_) cudaFree(p);
-    }
-    template <typename T>
-    T *get(size_t count) {
-        void *p = nullptr;
-        if (err_ == cudaSuccess) err_ = cudaMalloc(&p, std::max<size_t>(16, count * sizeof(T)));
-        if (err_ != cudaSuccess) return nullptr;
-        ptrs_.push_back(p);
-        return static_cast<T *>(p);
-    }
-    cudaError_t err() const { return err_; }
-
-private:
-    std::vector<void *> ptrs_;
-    cudaError_t err_ = cudaSuccess;
-};
-
-int grid_for(int64_t items, int per_block) {
-    const int64_t g = (items + per_block - 1) / per_block;
-    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, 8LL * sm_count())));
-}
-
-int bits_for(int64_t n) {   // bits needed for the values 0 .. n-1
-    int b = 0;
-    while (b < 31 && (1LL << b) < n) ++b;
-    return b;
-}
-
-// Stable sort of (key, val) pairs by the low `bits` bits of key.  The pairs
-// start in (k0, v0); on return *ko/*vo point at whichever buffer holds the
-// sorted pairs.
-void radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int count, int bits, int32_t *hist,
-                int32_t *hoff, cudaStream_t st, uint32_t **ko, int32_t **vo) {
-    const int ntiles = (count + kSortTile - 1) / kSortTile;
-    for (int shift = 0; shift < bits && count > 0; shift += 8) {
-        sort_hist_kernel<<<ntiles, kThreads, 0, st>>>(k0, count, shift, ntiles, hist);
-        scan_kernel<<<1, kScanThreads, 0, st>>>(hist, hoff, nullptr, 256 * ntiles);
-        sort_scatter_kernel<<<ntiles, kThreads, 0, st>>>(k0, v0, count, shift, ntiles, hoff, k1, v1);
-        std::swap(k0, k1);
-        std::swap(v0, v1);
-    }
-    *ko = k0;
-    *vo = v0;
-}
-
-int fetch(void *h, const void *d, size_t bytes, cudaStream_t st) {
-    cudaError_t e = cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return cuda_status(e);
-}
 
 // One pattern (the union of `count` matrices when count > 1, see Blocks) in
 // device memory; perms[m] (device array of device pointers) receive the
@@ -752,7 +488,7 @@ int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaSt
     if (ce != cudaSuccess) return cuda_status(ce);
 
     // validation, then degrees
-    validate_kernel<<<grid_for(n, G), G, 0, st>>>(n, P.B, P.rp, P.ci, rowof, deg, ctl);
+    validate_kernel<<<grid_for(n, G), G, 0, st>>>(n, P.B, P.rp, P.ci, rowof, deg, &ctl->err);
     int rc = fetch(&hc, ctl, sizeof(Ctl), st);
     if (rc != PARS3_OK) return rc;
     if (hc.err) return PARS3_ENOTSKEW;

@@ -581,6 +581,32 @@ static void set_layout_params(pars3_handle *h, const pars3_split_params &p) {
     h->variant = p.variant;
 }
 
+// Checks and normalises the parameters of a split (dtypes 0 -> F64 only):
+// PARS3_OK or PARS3_EINVAL.  T = W = 0, the default cut rule, passes.
+int split_params_normalize(pars3_split_params *prm) {
+    if (prm->dtypes == 0) prm->dtypes = PARS3_DTYPE_BIT(PARS3_F64);
+    if (prm->dtypes & ~7) return PARS3_EINVAL;
+    if (prm->flags & ~PARS3_SPLIT_SYMMETRIC) return PARS3_EINVAL;
+    if ((prm->T == 0) != (prm->W == 0)) return PARS3_EINVAL;
+    return check_layout_params(*prm);
+}
+
+int check_cut(int32_t T, int32_t W) {
+    return (!is_pow2(T) || !is_pow2(W) || W < 32 || W > T || T > 32768) ? PARS3_EINVAL : PARS3_OK;
+}
+
+// Completes a handle whose canonical split (perm, rowptr, col, val, cls,
+// tile and outer lists, counts, bw, T, W, ntiles) was filled elsewhere (the
+// GPU split): the layout parameters of p and the device layout.
+int split_finish(pars3_handle *h, const pars3_split_params &p) {
+    set_layout_params(h, p);
+    try {
+        return build_layout(h);
+    } catch (const std::bad_alloc &) {
+        return PARS3_ENOMEM;
+    }
+}
+
 // A handle with the same reordered matrix as src (perm, band CSR, packed
 // precisions, mirror sign) and the cut points and layout parameters of p:
 // only the cut-dependent stages run.  Used by the autotuner.
@@ -631,11 +657,7 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
         if (!std::isfinite(val[k])) return PARS3_ENONFINITE;
     pars3_split_params prm{};
     if (p) prm = *p;
-    if (prm.dtypes == 0) prm.dtypes = PARS3_DTYPE_BIT(PARS3_F64);
-    if (prm.dtypes & ~7) return PARS3_EINVAL;
-    if (prm.flags & ~PARS3_SPLIT_SYMMETRIC) return PARS3_EINVAL;
-    if ((prm.T == 0) != (prm.W == 0)) return PARS3_EINVAL;
-    if (check_layout_params(prm) != PARS3_OK) return PARS3_EINVAL;
+    if (split_params_normalize(&prm) != PARS3_OK) return PARS3_EINVAL;
     pars3_handle *h = nullptr;
     try {
         h = new pars3_handle();
@@ -661,7 +683,7 @@ extern "C" int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col,
             int32_t wcap = (prm.dtypes & PARS3_DTYPE_BIT(PARS3_F64)) ? 1024 : 2048;
             auto_cut(bw, 32, wcap, 1024, &prm.T, &prm.W);
         }
-        if (!is_pow2(prm.T) || !is_pow2(prm.W) || prm.W < 32 || prm.W > prm.T || prm.T > 32768) {
+        if (check_cut(prm.T, prm.W) != PARS3_OK) {
             delete h;
             return PARS3_EINVAL;
         }

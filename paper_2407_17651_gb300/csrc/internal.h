@@ -159,6 +159,9 @@ int64_t bandwidth(int32_t n, const int32_t *rowptr, const int32_t *col, const in
 // host_split.cpp
 int split_recut(const pars3_handle *src, const pars3_split_params &p, pars3_handle **out);
 int check_layout_params(const pars3_split_params &p);
+int split_params_normalize(pars3_split_params *prm);
+int check_cut(int32_t T, int32_t W);
+int split_finish(pars3_handle *h, const pars3_split_params &p);
 // bit of the calling thread's current CUDA device (kernel attributes are set
 // once per device and kernel)
 uint64_t device_bit();

@@ -104,6 +104,7 @@ def lib() -> C.CDLL:
         "pars3_reorder_device": ([i32, P, P, i32, P, P, P, P], C.c_int),
         "pars3_reorder_device_batched": ([i32, P, P, P, i32, P, P, P, P], C.c_int),
         "pars3_split": ([i32, P, P, P, P, P, P], C.c_int),
+        "pars3_split_device": ([i32, P, P, P, P, P, P, P], C.c_int),
         "pars3_split_export": ([P, P], C.c_int),
         "pars3_info_get": ([P, P], C.c_int),
         "pars3_layout_check": ([P], C.c_int),
@@ -135,7 +136,7 @@ def exported_symbols():
             "pars3_info_get", "pars3_layout_check", "pars3_upload", "pars3_spmv", "pars3_spmm",
             "pars3_spmm_batched", "pars3_mrs", "pars3_permute", "pars3_unpermute", "pars3_spmv_host",
             "pars3_check", "pars3_autotune", "pars3_free", "pars3_spmv_noalloc", "pars3_fp64_fma_rate",
-            "pars3_reorder_device", "pars3_reorder_device_batched"]
+            "pars3_reorder_device", "pars3_reorder_device_batched", "pars3_split_device"]
 
 
 def _chk(rc: int, where: str):
@@ -285,6 +286,29 @@ def pars3_split(n: int, rowptr, col, val, perm=None, T: int = 0, W: int = 0, dty
     out = C.c_void_p()
     _chk(lib().pars3_split(int(n), _p(rp), _p(ci), _p(v), None if pm is None else _p(pm), C.byref(prm),
                            C.byref(out)), "pars3_split")
+    return Handle(out, n)
+
+
+def pars3_split_device(n: int, rowptr, col, val, perm=None, T: int = 0, W: int = 0, dtypes: int = 0,
+                       long_row: int = 0, symmetric: bool = False, piece: int = 0, long_slices: int = 0,
+                       lane_bytes: int = 0, variant: int = 0, stream=None) -> Handle:
+    """pars3_split with the canonical split computed on the GPU: rowptr / col /
+    perm are int32 CUDA tensors, val a float64 CUDA tensor."""
+    import torch
+    for t, what, dt in ((rowptr, "rowptr", torch.int32), (col, "col", torch.int32), (val, "val", torch.float64)):
+        if t.dtype != dt:
+            raise ValueError(f"{what} must be {dt}")
+    if perm is not None and perm.dtype != torch.int32:
+        raise ValueError("perm must be int32")
+    if rowptr.numel() != int(n) + 1:
+        raise ValueError("rowptr must hold n + 1 entries")
+    prm = pars3_split_params(T=T, W=W, dtypes=dtypes, long_row=long_row,
+                             flags=SPLIT_SYMMETRIC if symmetric else 0, piece=piece, long_slices=long_slices,
+                             lane_bytes=lane_bytes, variant=variant)
+    out = C.c_void_p()
+    nz = lambda t: _dptr(t) if t is not None and t.numel() else None
+    _chk(lib().pars3_split_device(int(n), _dptr(rowptr), nz(col), nz(val), nz(perm), C.byref(prm), C.byref(out),
+                                  _stream(stream)), "pars3_split_device")
     return Handle(out, n)
 
 
