@@ -284,24 +284,40 @@ def extra_section(args, peak):
     torch.cuda.synchronize()
     prep["rcm_device_batched"] = time.perf_counter() - t1
     perms = [p.cpu().numpy() for p, _, _ in outs]
-    del pats, outs
     t1 = time.perf_counter()
     host_perms = [P.pars3_reorder(A.n, A.rowptr, A.col)[0] for A in mats]
     prep["rcm_host"] = time.perf_counter() - t1
     prep["rcm_device_same_as_host"] = all(np.array_equal(a, b) for a, b in zip(perms, host_perms))
     del host_perms
+    # split parameters from the autotuner; the handles the products run on come
+    # from the GPU split (pars3_split_device), the host split is timed beside it
     hs, ns, nnzs, cuts = [], [], [], []
-    prep["autotune"] = prep["split_upload"] = 0.0
-    for A, perm in zip(mats, perms):
+    prep["autotune"] = prep["split_device"] = prep["split_host"] = prep["upload"] = 0.0
+    same = True
+    for A, perm, (_, rp_d, ci_d), (perm_d, _, _) in zip(mats, perms, pats, outs):
         t1 = time.perf_counter()
         tune = P.pars3_autotune(A.n, A.rowptr, A.col, A.val, perm, dtype=P.F32, k=4, dtypes=both)
+        kw = P.split_kwargs(tune)
+        val_d = torch.from_numpy(A.val).cuda()
+        torch.cuda.synchronize()
         t2 = time.perf_counter()
-        h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, **P.split_kwargs(tune))
+        h = P.pars3_split_device(A.n, rp_d, ci_d, val_d, perm_d, **kw)
+        t3 = time.perf_counter()
+        hh = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, **kw)
+        t4 = time.perf_counter()
+        ed, eh = P.pars3_split_export(h), P.pars3_split_export(hh)
+        same = same and all(np.array_equal(np.asarray(ed[k]), np.asarray(eh[k])) for k in ed)
+        hh.close()
+        del val_d
+        t5 = time.perf_counter()
         P.pars3_upload(h)
         prep["autotune"] += t2 - t1
-        prep["split_upload"] += time.perf_counter() - t2
+        prep["split_device"] += t3 - t2
+        prep["split_host"] += t4 - t3
+        prep["upload"] += time.perf_counter() - t5
         hs.append(h); ns.append(A.n); nnzs.append(A.nnz); cuts.append((tune["T"], tune["W"], tune["lane_bytes"]))
-    del mats
+    prep["split_device_same_as_host"] = same
+    del mats, pats, outs
     t_prep = time.perf_counter() - t0
     rows = {}
     st = torch.cuda.current_stream()
@@ -593,6 +609,17 @@ def main():
     t0 = time.perf_counter()
     h = P.pars3_split(A.n, A.rowptr, A.col, A.val, perm, **split_kw)
     t_split = time.perf_counter() - t0
+    # the same split with its canonical part on the GPU (pars3_split_device)
+    dev_in = [torch.from_numpy(a).cuda() for a in (A.rowptr, A.col, A.val, perm)]
+    P.pars3_split_device(A.n, *dev_in, **split_kw).close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hd = P.pars3_split_device(A.n, *dev_in, **split_kw)
+    t_split_dev = time.perf_counter() - t0
+    ed, eh = P.pars3_split_export(hd), P.pars3_split_export(h)
+    split_dev_same = all(np.array_equal(np.asarray(ed[k]), np.asarray(eh[k])) for k in ed)
+    hd.close()
+    del dev_in, ed, eh
     t0 = time.perf_counter()
     P.pars3_upload(h)
     t_up = time.perf_counter() - t0
@@ -737,7 +764,8 @@ def main():
             "mrs": mrs,
             "clocks": clk,
             "preprocess_s": {"rcm": t_rcm, "rcm_device": t_rcm_dev, "rcm_device_same_as_host": rcm_dev_same,
-                             "autotune": t_tune, "split": t_split, "upload": t_up},
+                             "autotune": t_tune, "split": t_split, "split_device": t_split_dev,
+                             "split_device_same_as_host": split_dev_same, "upload": t_up},
             "other_workloads": extra,
             "spmv_us": {"mean": 1e6 * avg_spmv_s,
                         "single_products": {"median": 1e3 * statistics.median(spmv_ms), "min": 1e3 * min(spmv_ms),

@@ -247,7 +247,7 @@ int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col, const doub
  * built on the host as pars3_split builds it.  The result -- every array
  * pars3_split_export shows, and the layout -- is identical to pars3_split
  * with the same inputs and parameters.  Runs on `stream` and returns after
- * the handle is complete.  Allocates temporary device memory (about 90 bytes
+ * the handle is complete.  Allocates temporary device memory (about 80 bytes
  * per stored entry).  Errors as for pars3_split, plus ECUDA. */
 int pars3_split_device(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
                        const int32_t *perm, const pars3_split_params *p, pars3_handle **out, void *stream);
