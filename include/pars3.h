@@ -294,7 +294,9 @@ int pars3_spmm(const pars3_handle *h, int32_t dtype, double alpha, int32_t k, co
  * launch; with capture != 0 the pair is recorded once in a CUDA graph kept
  * by the first handle and replayed on later calls with the same arguments.
  * hs[count], alpha[count] (host), X[count], Y[count] (device pointers, host
- * array).  Errors: as pars3_spmm. */
+ * array).  One SpMM lane width serves the whole batch: the handles'
+ * lane_bytes when all of them carry the same value, else the rule (see
+ * pars3_split_params).  Errors: as pars3_spmm. */
 int pars3_spmm_batched(pars3_handle *const *hs, int32_t count, int32_t dtype, const double *alpha,
                        int32_t k, const void *const *X, void *const *Y, int32_t capture,
                        void *stream);

@@ -270,7 +270,12 @@ static int run_batched(BatchCache &C, pars3_handle *const *hs, int count, int dt
     bool aligned = true;
     for (int m = 0; m < count; ++m)
         aligned = aligned && ((reinterpret_cast<uintptr_t>(X[m]) | reinterpret_cast<uintptr_t>(Y[m])) & 15u) == 0;
-    const int nv = spmm_lane_elems<XT>(k, hs[0]->lane_bytes, aligned);
+    // one lane width serves every matrix: a tuned width when all handles carry
+    // the same one, else the rule
+    int lane_bytes = hs[0]->lane_bytes;
+    for (int m = 1; m < count; ++m)
+        if (hs[m]->lane_bytes != lane_bytes) lane_bytes = 0;
+    const int nv = spmm_lane_elems<XT>(k, lane_bytes, aligned);
     const int lpr = spmm_lpr(k, nv);
     const int64_t nu = upre.back(), nfold = fpre.back();
     auto launch = [&](cudaStream_t s) {
