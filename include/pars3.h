@@ -255,6 +255,13 @@ int pars3_split_device(int32_t n, const int32_t *rowptr, const int32_t *col, con
 /* Canonical split of a handle (host view; see pars3_canonical). */
 int pars3_split_export(const pars3_handle *h, pars3_canonical *out);
 
+/* pars3_layout_digest -- a 64-bit FNV-1a digest of the handle's device
+ * layout (every array with its length, and the scalars the kernels read),
+ * for checking that two handles hold the same layout (e.g. one from
+ * pars3_split and one from pars3_split_device).  Host only.
+ * Errors: EINVAL (null pointer). */
+int pars3_layout_digest(const pars3_handle *h, uint64_t *digest);
+
 /* Device-layout sizes of a handle. */
 int pars3_info_get(const pars3_handle *h, pars3_info *out);
 

@@ -188,7 +188,7 @@ int spmv_smem_bytes(const pars3_handle *h, int dtype) {
     return static_cast<int>(s.rowacc + static_cast<uint32_t>(h->T) * asz);
 }
 
-static int max_smem_all(const pars3_handle *h) {
+int max_smem_all(const pars3_handle *h) {
     int m = 0;
     for (int d = 0; d < kNumDtypes; ++d)
         if (h->dtypes & PARS3_DTYPE_BIT(d)) m = std::max(m, smem_bytes_for(h, d));
@@ -196,7 +196,7 @@ static int max_smem_all(const pars3_handle *h) {
 }
 
 // half-path entries a tile may hold, for every packed precision
-static int64_t half_room(const pars3_handle *h) {
+int64_t half_room(const pars3_handle *h) {
     int64_t best = INT64_MAX;
     for (int d = 0; d < kNumDtypes; ++d) {
         if (!(h->dtypes & PARS3_DTYPE_BIT(d))) continue;
@@ -208,6 +208,198 @@ static int64_t half_room(const pars3_handle *h) {
         best = std::min<int64_t>(best, room > 0 ? room / per : -1);
     }
     return std::min<int64_t>(best, 65535 - kAlignHalf);
+}
+
+// ---- decisions of the layout build that look at rows and tiles only; the
+// host builder below and the GPU builder (device_split.cu) both use them
+
+// Step 1: tcount[t] holds the middle entries of tile t on entry.  A tile
+// whose middle entries do not fit shared memory (more than mcap), or are too
+// few to repay staging the x window (under 1/kHalfMinFrac of the tile's
+// stored entries), takes them on the full path (tcount[t] = 0).  The launch
+// reserves the largest tile's staging area for every block, which takes
+// that shared memory away from L1 on every SM: when the half path would hold
+// under 1/kHalfMinShare of all stored entries it is not used at all.  Fills
+// hoff, hcnt and max_tile_half.
+void half_tiles(pars3_handle *h, int64_t mcap, std::vector<int32_t> &tcount) {
+    Layout &L = h->L;
+    const int32_t n = h->n, T = h->T, nt = h->ntiles;
+    const std::vector<int32_t> &rp = h->rowptr;
+    for (int32_t t = 0; t < nt; ++t) {
+        const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+        const int64_t stored = static_cast<int64_t>(rp[r1]) - rp[r0];
+        if (tcount[t] > mcap || static_cast<int64_t>(tcount[t]) * kHalfMinFrac < stored) tcount[t] = 0;
+    }
+    int64_t hsum = 0;
+    for (int32_t t = 0; t < nt; ++t) hsum += tcount[t];
+    if (hsum * kHalfMinShare < h->nnz) std::fill(tcount.begin(), tcount.end(), 0);
+    L.hoff.assign(static_cast<size_t>(nt) + 1, 0);
+    L.hcnt.assign(nt, 0);
+    for (int32_t t = 0; t < nt; ++t) {
+        L.hcnt[t] = tcount[t];
+        L.hoff[t + 1] = static_cast<int32_t>(L.hoff[t] + round_up(tcount[t], kAlignHalf));
+        L.max_tile_half = std::max(L.max_tile_half, tcount[t]);
+    }
+}
+
+// Step 3: long rows -- longer than the cap, or the heaviest rows of a tile
+// whose full entries exceed the cap (rows of at least kLongMin entries,
+// longest first, ties by index).  Sets cap_full.
+void long_rows(pars3_handle *h, const std::vector<int32_t> &flen, int64_t ftotal, int64_t cap_in,
+               std::vector<uint8_t> &is_long) {
+    Layout &L = h->L;
+    const int32_t n = h->n, T = h->T, nt = h->ntiles;
+    const int64_t avg = nt > 0 ? (ftotal + nt - 1) / nt : 0;
+    const int64_t cap = cap_in > 0 ? cap_in : std::max<int64_t>(2048, round_up(2 * avg, kAlignFull));
+    L.cap_full = static_cast<int32_t>(std::min<int64_t>(cap, INT32_MAX));
+    const int64_t long_thr = std::min<int64_t>(h->long_row > 0 ? h->long_row : kSellMax, kSellMax);
+    is_long.assign(n, 0);
+    for (int32_t i = 0; i < n; ++i)
+        if (flen[i] > long_thr) is_long[i] = 1;
+    for (int32_t t = 0; t < nt; ++t) {
+        const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+        int64_t f = 0;
+        for (int32_t i = r0; i < r1; ++i)
+            if (!is_long[i]) f += flen[i];
+        if (f <= cap) continue;
+        // balance: rows of at least kLongMin entries, longest first (ties by
+        // index); then, if the tile is still above the cap, any row
+        for (int pass = 0; pass < 2 && f > cap; ++pass) {
+            std::vector<int32_t> cand;
+            for (int32_t i = r0; i < r1; ++i)
+                if (!is_long[i] && flen[i] > 0 && (pass == 1 || flen[i] >= kLongMin)) cand.push_back(i);
+            std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
+                return flen[a] != flen[b] ? flen[a] > flen[b] : a < b;
+            });
+            for (int32_t i : cand) {
+                if (f <= cap) break;
+                is_long[i] = 1;
+                f -= flen[i];
+            }
+        }
+    }
+}
+
+// Step 4: the sliced-ELL slices.  rows[r0 .. r1) lists tile t's rows sorted
+// by full-path length slen (longest first, ties by row); every row of a tile
+// gets a lane, so the full pass can start each row's sum with alpha x_r.
+// row_base[i] receives the slot of row i's first entry (-1 when it has none).
+int slice_rows(pars3_handle *h, const std::vector<int32_t> &rows, const std::vector<int32_t> &slen,
+               std::vector<int32_t> &row_base) {
+    Layout &L = h->L;
+    const int32_t n = h->n, T = h->T, nt = h->ntiles;
+    L.sl_off.assign(static_cast<size_t>(nt) + 1, 0);
+    L.sl_ent.assign(1, 0);
+    L.sl_meta.clear();
+    L.sl_e.clear();
+    row_base.assign(n, -1);
+    for (int32_t t = 0; t < nt; ++t) {
+        const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+        int64_t tile_ent = 0;
+        for (int32_t g = r0; g < r1; g += kSlice) {
+            const int32_t width = slen[rows[g]];
+            const int64_t start = L.sl_ent.back();
+            const int64_t next = start + static_cast<int64_t>(kSlice) * width;
+            if (next > INT32_MAX - kSlice) return PARS3_EUNSUPPORTED;   // int32 slot offsets
+            L.sl_ent.push_back(static_cast<int32_t>(next));
+            for (int l = 0; l < kSlice; ++l) {
+                const int32_t k = g + l;
+                if (k < r1) {
+                    const int32_t i = rows[k];
+                    L.sl_meta.push_back(static_cast<uint32_t>(i - r0) | (static_cast<uint32_t>(slen[i]) << 16));
+                    if (slen[i] > 0) row_base[i] = static_cast<int32_t>(start + l);
+                } else {
+                    L.sl_meta.push_back(0xffffu);
+                }
+            }
+            tile_ent += static_cast<int64_t>(kSlice) * width;
+        }
+        L.sl_off[t + 1] = static_cast<int32_t>(L.sl_ent.size() - 1);
+        int32_t se = L.sl_off[t + 1];
+        while (se > L.sl_off[t] && L.sl_ent[se] == L.sl_ent[se - 1]) --se;
+        L.sl_e.push_back(se);
+        L.max_tile_full = static_cast<int32_t>(std::max<int64_t>(L.max_tile_full, tile_ent));
+        L.max_tile_slices = std::max(L.max_tile_slices, L.sl_off[t + 1] - L.sl_off[t]);
+    }
+    return PARS3_OK;
+}
+
+// Step 5: long rows in row order (lrow, lrp) and their pieces: full pieces
+// in row order, then the shorter last pieces, longest first (ties by row);
+// lp0, lrem, the long slices (ls_ent: a slice is as wide as its first, i.e.
+// longest, piece) and every piece's length.
+int long_pieces(pars3_handle *h, const std::vector<uint8_t> &is_long, const std::vector<int32_t> &flen,
+                std::vector<PieceRef> &pieces) {
+    Layout &L = h->L;
+    const int32_t n = h->n;
+    L.lrow.clear();
+    L.lrp.assign(1, 0);
+    for (int32_t i = 0; i < n; ++i)
+        if (is_long[i]) {
+            L.lrow.push_back(i);
+            L.lrp.push_back(static_cast<int32_t>(std::min<int64_t>(static_cast<int64_t>(L.lrp.back()) + flen[i],
+                                                                   INT32_MAX)));
+        }
+    const size_t nlong = L.lrow.size();
+    if (L.lrp.back() >= INT32_MAX / 2) return PARS3_EUNSUPPORTED;   // int32 entry offsets
+    const int32_t P = h->piece > 0 ? h->piece : kPieceLen;
+    L.piece_len = P;
+    std::vector<PieceRef> rest;
+    pieces.clear();
+    L.lp0.assign(nlong + 1, 0);
+    L.lrem.assign(nlong, -1);
+    for (size_t l = 0; l < nlong; ++l) {
+        const int32_t len = L.lrp[l + 1] - L.lrp[l];
+        int32_t q = 0;
+        for (; q + P <= len; q += P) pieces.push_back({static_cast<int32_t>(l), L.lrp[l] + q, P});
+        L.lp0[l + 1] = static_cast<int32_t>(pieces.size());
+        if (q < len) rest.push_back({static_cast<int32_t>(l), L.lrp[l] + q, len - q});
+    }
+    std::stable_sort(rest.begin(), rest.end(), [](const PieceRef &a, const PieceRef &b) { return a.len > b.len; });
+    for (const PieceRef &pc : rest) {
+        L.lrem[pc.l] = static_cast<int32_t>(pieces.size());
+        pieces.push_back(pc);
+    }
+    const int64_t npieces = static_cast<int64_t>(pieces.size());
+    const int64_t nls = (npieces + kSlice - 1) / kSlice;
+    if (nls * kSlice > INT32_MAX / 2) return PARS3_EUNSUPPORTED;
+    L.ls_ent.assign(1, 0);
+    L.ls_len.assign(static_cast<size_t>(nls) * kSlice, 0);
+    for (int64_t sl = 0; sl < nls; ++sl) {
+        const int64_t width = pieces[static_cast<size_t>(sl * kSlice)].len;   // the slice's longest piece
+        const int64_t next = L.ls_ent.back() + width * kSlice;
+        if (next > INT32_MAX - kSlice) return PARS3_EUNSUPPORTED;
+        L.ls_ent.push_back(static_cast<int32_t>(next));
+    }
+    for (int64_t p = 0; p < npieces; ++p) L.ls_len[p] = static_cast<uint16_t>(pieces[static_cast<size_t>(p)].len);
+    L.nslots = nls * kSlice;
+    L.ls_per_block = h->lsb > 0 ? h->lsb : kLongSlices;
+    return PARS3_OK;
+}
+
+// Step 6: fold items, each receiving row once, in row order.
+void fold_items(pars3_handle *h) {
+    Layout &L = h->L;
+    const int32_t n = h->n;
+    std::vector<int32_t> hidx(n, -1), lidx(n, -1);
+    for (size_t k = 0; k < L.hhrow.size(); ++k) hidx[L.hhrow[k]] = static_cast<int32_t>(k);
+    for (size_t l = 0; l < L.lrow.size(); ++l) lidx[L.lrow[l]] = static_cast<int32_t>(l);
+    L.fold_row.clear();
+    L.fold_halo.clear();
+    L.fold_p0.clear();
+    L.fold_np.clear();
+    L.fold_rem.clear();
+    L.fold_heavy.clear();
+    for (int32_t i = 0; i < n; ++i)
+        if (hidx[i] >= 0 || lidx[i] >= 0) {
+            const int32_t l = lidx[i];
+            L.fold_row.push_back(i);
+            L.fold_halo.push_back(hidx[i]);
+            L.fold_p0.push_back(l >= 0 ? L.lp0[l] : 0);
+            L.fold_np.push_back(l >= 0 ? L.lp0[l + 1] - L.lp0[l] : 0);
+            L.fold_rem.push_back(l >= 0 ? L.lrem[l] : -1);
+            if (L.fold_np.back() >= kFoldHeavy) L.fold_heavy.push_back(static_cast<int32_t>(L.fold_row.size()) - 1);
+        }
 }
 
 static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
@@ -230,45 +422,12 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
         for (int64_t e = 0; e < nnz; ++e) cent[fill[ci[e]]++] = static_cast<int32_t>(e);
     }
     // ---- 1. half path: middle entries, unless the tile would not fit
-    const int64_t mcap = mcap_in;
-    std::vector<uint8_t> half(nnz, 0);
     std::vector<int32_t> tcount(nt, 0);
-    for (int64_t e = 0; e < nnz; ++e) {
-        if (h->cls[e] != 2) {
-            half[e] = 1;
-            ++tcount[row_of[e] / T];
-        }
-    }
-    // a tile whose middle entries do not fit shared memory, or are too few
-    // to repay staging the x window (under 1/kHalfMinFrac of the tile's
-    // stored entries), takes them on the full path
-    for (int32_t t = 0; t < nt; ++t) {
-        const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
-        const int64_t stored = static_cast<int64_t>(rp[r1]) - rp[r0];
-        if (tcount[t] > mcap || static_cast<int64_t>(tcount[t]) * kHalfMinFrac < stored) {
-            for (int64_t e = rp[r0]; e < rp[r1]; ++e) half[e] = 0;
-            tcount[t] = 0;
-        }
-    }
-    // the launch reserves the largest tile's staging area for every block,
-    // which takes that shared memory away from L1 on every SM: when the half
-    // path would hold under 1/kHalfMinShare of all stored entries it is not
-    // used at all
-    {
-        int64_t hsum = 0;
-        for (int32_t t = 0; t < nt; ++t) hsum += tcount[t];
-        if (hsum * kHalfMinShare < nnz) {
-            std::fill(half.begin(), half.end(), 0);
-            std::fill(tcount.begin(), tcount.end(), 0);
-        }
-    }
-    L.hoff.assign(static_cast<size_t>(nt) + 1, 0);
-    L.hcnt.assign(nt, 0);
-    for (int32_t t = 0; t < nt; ++t) {
-        L.hcnt[t] = tcount[t];
-        L.hoff[t + 1] = static_cast<int32_t>(L.hoff[t] + round_up(tcount[t], kAlignHalf));
-        L.max_tile_half = std::max(L.max_tile_half, tcount[t]);
-    }
+    for (int64_t e = 0; e < nnz; ++e)
+        if (h->cls[e] != 2) ++tcount[row_of[e] / T];
+    half_tiles(h, mcap_in, tcount);
+    std::vector<uint8_t> half(nnz, 0);
+    for (int64_t e = 0; e < nnz; ++e) half[e] = h->cls[e] != 2 && tcount[row_of[e] / T] > 0;
     const int64_t hn = L.hoff[nt];
     L.hcol.assign(hn, 0);
     L.hcperm.assign(hn, 0);
@@ -335,39 +494,9 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
         flen[i] = c;
         ftotal += c;
     }
-    // ---- 3. long rows: longer than the cap, or the heaviest rows of a tile
-    // whose full entries exceed the cap (rows of at least kLongMin entries,
-    // longest first, ties by index)
-    const int64_t avg = nt > 0 ? (ftotal + nt - 1) / nt : 0;
-    const int64_t cap = cap_in > 0 ? cap_in : std::max<int64_t>(2048, round_up(2 * avg, kAlignFull));
-    L.cap_full = static_cast<int32_t>(std::min<int64_t>(cap, INT32_MAX));
-    const int64_t long_thr = std::min<int64_t>(h->long_row > 0 ? h->long_row : kSellMax, kSellMax);
-    std::vector<uint8_t> is_long(n, 0);
-    for (int32_t i = 0; i < n; ++i)
-        if (flen[i] > long_thr) is_long[i] = 1;
-    for (int32_t t = 0; t < nt; ++t) {
-        const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
-        int64_t f = 0;
-        for (int32_t i = r0; i < r1; ++i)
-            if (!is_long[i]) f += flen[i];
-        if (f <= cap) continue;
-        // balance: rows of at least kLongMin entries, longest first (ties by
-        // index); then, if the tile is still above the cap, any row
-        for (int pass = 0; pass < 2 && f > cap; ++pass) {
-            std::vector<int32_t> cand;
-            for (int32_t i = r0; i < r1; ++i)
-                if (!is_long[i] && flen[i] > 0 && (pass == 1 || flen[i] >= kLongMin)) cand.push_back(i);
-            std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
-                return flen[a] != flen[b] ? flen[a] > flen[b] : a < b;
-            });
-            const int64_t goal = cap;
-            for (int32_t i : cand) {
-                if (f <= goal) break;
-                is_long[i] = 1;
-                f -= flen[i];
-            }
-        }
-    }
+    // ---- 3. long rows
+    std::vector<uint8_t> is_long;
+    long_rows(h, flen, ftotal, cap_in, is_long);
     // ---- 4. full path per tile as sliced ELL (rows sorted by length, longest first)
     auto emit_row = [&](int32_t i, int32_t *colp, int32_t *srcp, int64_t stride) {
         int64_t q = 0;
@@ -379,44 +508,17 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
         }
         return q;
     };
-    L.sl_off.assign(static_cast<size_t>(nt) + 1, 0);
-    L.sl_ent.assign(1, 0);
-    L.sl_e.clear();
-    std::vector<std::vector<int32_t>> tile_rows(1);
-    {
-        std::vector<int32_t> rows;
-        for (int32_t t = 0; t < nt; ++t) {
-            const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
-            // every row of the tile gets a lane (long rows with length 0), so
-            // the full pass can start each row's sum with alpha x_r
-            rows.clear();
-            for (int32_t i = r0; i < r1; ++i) rows.push_back(i);
-            auto slen = [&](int32_t i) { return is_long[i] ? 0 : flen[i]; };
-            std::sort(rows.begin(), rows.end(), [&](int32_t a, int32_t b) {
-                return slen(a) != slen(b) ? slen(a) > slen(b) : a < b;
-            });
-            int64_t tile_ent = 0;
-            for (size_t g = 0; g < rows.size(); g += kSlice) {
-                const int32_t width = slen(rows[g]);
-                const int64_t next = L.sl_ent.back() + static_cast<int64_t>(kSlice) * width;
-                if (next > INT32_MAX - kSlice) return PARS3_EUNSUPPORTED;   // int32 slot offsets
-                L.sl_ent.push_back(static_cast<int32_t>(next));
-                for (int l = 0; l < kSlice; ++l) {
-                    const size_t k = g + l;
-                    L.sl_meta.push_back(k < rows.size()
-                                            ? static_cast<uint32_t>(rows[k] - r0) | (static_cast<uint32_t>(slen(rows[k])) << 16)
-                                            : 0xffffu);
-                }
-                tile_ent += static_cast<int64_t>(kSlice) * width;
-            }
-            L.sl_off[t + 1] = static_cast<int32_t>(L.sl_ent.size() - 1);
-            int32_t se = L.sl_off[t + 1];
-            while (se > L.sl_off[t] && L.sl_ent[se] == L.sl_ent[se - 1]) --se;
-            L.sl_e.push_back(se);
-            L.max_tile_full = static_cast<int32_t>(std::max<int64_t>(L.max_tile_full, tile_ent));
-            L.max_tile_slices = std::max(L.max_tile_slices, L.sl_off[t + 1] - L.sl_off[t]);
-        }
+    std::vector<int32_t> slen(n), rows(n);
+    for (int32_t i = 0; i < n; ++i) slen[i] = is_long[i] ? 0 : flen[i];
+    for (int32_t t = 0; t < nt; ++t) {
+        const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+        for (int32_t i = r0; i < r1; ++i) rows[i] = i;
+        std::sort(rows.begin() + r0, rows.begin() + r1, [&](int32_t a, int32_t b) {
+            return slen[a] != slen[b] ? slen[a] > slen[b] : a < b;
+        });
     }
+    std::vector<int32_t> row_base;
+    if (const int rc = slice_rows(h, rows, slen, row_base); rc != PARS3_OK) return rc;
     const int64_t fnp = L.sl_ent.back();
     L.fcol.assign(fnp, 0);
     std::vector<int32_t> fsrc(fnp, 0);  // +(e+1): lower entry, -(e+1): mirrored entry, 0: padding
@@ -431,78 +533,25 @@ static int build_layout_try(pars3_handle *h, int64_t mcap_in, int64_t cap_in) {
             }
     }
     // ---- 5. long rows, concatenated in row order and cut into pieces
-    L.lrp.assign(1, 0);
-    for (int32_t i = 0; i < n; ++i)
-        if (is_long[i]) {
-            L.lrow.push_back(i);
-            L.lrp.push_back(static_cast<int32_t>(std::min<int64_t>(static_cast<int64_t>(L.lrp.back()) + flen[i],
-                                                                   INT32_MAX)));
-        }
+    std::vector<PieceRef> pieces;
+    if (const int rc = long_pieces(h, is_long, flen, pieces); rc != PARS3_OK) return rc;
     const size_t nlong = L.lrow.size();
     const int64_t ltot = L.lrp.back();
-    if (ltot >= INT32_MAX / 2) return PARS3_EUNSUPPORTED;   // int32 entry offsets
     std::vector<int32_t> lflat(ltot), lsrc_flat(ltot);
     for (size_t l = 0; l < nlong; ++l) emit_row(L.lrow[l], &lflat[L.lrp[l]], &lsrc_flat[L.lrp[l]], 1);
-    const int32_t P = h->piece > 0 ? h->piece : kPieceLen;
-    L.piece_len = P;
-    // pieces: (long row, first entry, length); full pieces in row order, then
-    // the shorter last pieces, longest first (ties by row)
-    struct Piece { int32_t l, e0, len; };
-    std::vector<Piece> pieces, rest;
-    L.lp0.assign(nlong + 1, 0);
-    L.lrem.assign(nlong, -1);
-    for (size_t l = 0; l < nlong; ++l) {
-        const int32_t len = L.lrp[l + 1] - L.lrp[l];
-        int32_t q = 0;
-        for (; q + P <= len; q += P) pieces.push_back({static_cast<int32_t>(l), L.lrp[l] + q, P});
-        L.lp0[l + 1] = static_cast<int32_t>(pieces.size());
-        if (q < len) rest.push_back({static_cast<int32_t>(l), L.lrp[l] + q, len - q});
-    }
-    std::stable_sort(rest.begin(), rest.end(), [](const Piece &a, const Piece &b) { return a.len > b.len; });
-    for (const Piece &pc : rest) {
-        L.lrem[pc.l] = static_cast<int32_t>(pieces.size());
-        pieces.push_back(pc);
-    }
     const int64_t npieces = static_cast<int64_t>(pieces.size());
-    const int64_t nls = (npieces + kSlice - 1) / kSlice;
-    if (nls * kSlice > INT32_MAX / 2) return PARS3_EUNSUPPORTED;
-    L.ls_ent.assign(1, 0);
-    L.ls_len.assign(static_cast<size_t>(nls) * kSlice, 0);
-    for (int64_t sl = 0; sl < nls; ++sl) {
-        const int64_t width = pieces[static_cast<size_t>(sl * kSlice)].len;   // the slice's longest piece
-        const int64_t next = L.ls_ent.back() + width * kSlice;
-        if (next > INT32_MAX - kSlice) return PARS3_EUNSUPPORTED;
-        L.ls_ent.push_back(static_cast<int32_t>(next));
-    }
     L.lcol.assign(static_cast<size_t>(L.ls_ent.back()), 0);
     std::vector<int32_t> lsrc(L.lcol.size(), 0);
     for (int64_t p = 0; p < npieces; ++p) {
-        const Piece &pc = pieces[static_cast<size_t>(p)];
+        const PieceRef &pc = pieces[static_cast<size_t>(p)];
         const int64_t base = L.ls_ent[p / kSlice] + (p % kSlice);
-        L.ls_len[p] = static_cast<uint16_t>(pc.len);
         for (int32_t m = 0; m < pc.len; ++m) {
             L.lcol[base + static_cast<int64_t>(m) * kSlice] = lflat[pc.e0 + m];
             lsrc[base + static_cast<int64_t>(m) * kSlice] = lsrc_flat[pc.e0 + m];
         }
     }
-    L.nslots = nls * kSlice;
-    L.ls_per_block = h->lsb > 0 ? h->lsb : kLongSlices;
     // ---- 6. fold items: each receiving row once, in row order
-    {
-        std::vector<int32_t> hidx(n, -1), lidx(n, -1);
-        for (size_t k = 0; k < L.hhrow.size(); ++k) hidx[L.hhrow[k]] = static_cast<int32_t>(k);
-        for (size_t l = 0; l < L.lrow.size(); ++l) lidx[L.lrow[l]] = static_cast<int32_t>(l);
-        for (int32_t i = 0; i < n; ++i)
-            if (hidx[i] >= 0 || lidx[i] >= 0) {
-                const int32_t l = lidx[i];
-                L.fold_row.push_back(i);
-                L.fold_halo.push_back(hidx[i]);
-                L.fold_p0.push_back(l >= 0 ? L.lp0[l] : 0);
-                L.fold_np.push_back(l >= 0 ? L.lp0[l + 1] - L.lp0[l] : 0);
-                L.fold_rem.push_back(l >= 0 ? L.lrem[l] : -1);
-                if (L.fold_np.back() >= kFoldHeavy) L.fold_heavy.push_back(static_cast<int32_t>(L.fold_row.size()) - 1);
-            }
-    }
+    fold_items(h);
     // ---- 7. values per precision
     auto fill_vals = [&](const std::vector<int32_t> &src, std::vector<double> &v64, std::vector<float> &v32,
                          std::vector<uint16_t> &v16) {

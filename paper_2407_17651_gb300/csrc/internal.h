@@ -162,6 +162,20 @@ int check_layout_params(const pars3_split_params &p);
 int split_params_normalize(pars3_split_params *prm);
 int check_cut(int32_t T, int32_t W);
 int split_finish(pars3_handle *h, const pars3_split_params &p);
+// layout-build decisions shared by the host and GPU builders (host_split.cpp)
+struct PieceRef {
+    int32_t l, e0, len;   // long row, first entry in the concatenated long-row list, length
+};
+void half_tiles(pars3_handle *h, int64_t mcap, std::vector<int32_t> &tcount);
+void long_rows(pars3_handle *h, const std::vector<int32_t> &flen, int64_t ftotal, int64_t cap_in,
+               std::vector<uint8_t> &is_long);
+int slice_rows(pars3_handle *h, const std::vector<int32_t> &rows, const std::vector<int32_t> &slen,
+               std::vector<int32_t> &row_base);
+int long_pieces(pars3_handle *h, const std::vector<uint8_t> &is_long, const std::vector<int32_t> &flen,
+                std::vector<PieceRef> &pieces);
+void fold_items(pars3_handle *h);
+int max_smem_all(const pars3_handle *h);
+int64_t half_room(const pars3_handle *h);
 // bit of the calling thread's current CUDA device (kernel attributes are set
 // once per device and kernel)
 uint64_t device_bit();

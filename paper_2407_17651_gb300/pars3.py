@@ -105,6 +105,7 @@ def lib() -> C.CDLL:
         "pars3_reorder_device_batched": ([i32, P, P, P, i32, P, P, P, P], C.c_int),
         "pars3_split": ([i32, P, P, P, P, P, P], C.c_int),
         "pars3_split_device": ([i32, P, P, P, P, P, P, P], C.c_int),
+        "pars3_layout_digest": ([P, P], C.c_int),
         "pars3_split_export": ([P, P], C.c_int),
         "pars3_info_get": ([P, P], C.c_int),
         "pars3_layout_check": ([P], C.c_int),
@@ -136,7 +137,8 @@ def exported_symbols():
             "pars3_info_get", "pars3_layout_check", "pars3_upload", "pars3_spmv", "pars3_spmm",
             "pars3_spmm_batched", "pars3_mrs", "pars3_permute", "pars3_unpermute", "pars3_spmv_host",
             "pars3_check", "pars3_autotune", "pars3_free", "pars3_spmv_noalloc", "pars3_fp64_fma_rate",
-            "pars3_reorder_device", "pars3_reorder_device_batched", "pars3_split_device"]
+            "pars3_reorder_device", "pars3_reorder_device_batched", "pars3_split_device",
+            "pars3_layout_digest"]
 
 
 def _chk(rc: int, where: str):
@@ -330,6 +332,12 @@ def pars3_split_export(h: Handle) -> dict:
                 cls=arr(c.cls, nnz, np.uint8), tile_ptr=arr(c.tile_ptr, nt + 1, np.int32),
                 tile_list=arr(c.tile_list, nmid, np.int32), outer_csr=arr(c.outer_csr, nout, np.int32),
                 outer_csc=arr(c.outer_csc, nout, np.int32))
+
+
+def pars3_layout_digest(h: Handle) -> int:
+    d = C.c_uint64()
+    _chk(lib().pars3_layout_digest(h, C.byref(d)), "pars3_layout_digest")
+    return d.value
 
 
 def pars3_info_get(h: Handle) -> dict:
