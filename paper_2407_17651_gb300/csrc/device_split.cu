@@ -10,9 +10,11 @@
 //      cut (T, W); the middle entries of every tile are listed in (col, row)
 //      order and the outer entries in CSR and in CSC order (stable sorts of
 //      position lists).
-// The arrays are the same, element for element, as the host split's; they
-// are copied into the handle, and the device layout is then built from them
-// on the host exactly as pars3_split builds it.
+// The arrays are the same, element for element, as the host split's and are
+// copied into the handle.  The device layout is then built from them on the
+// GPU (layout_try_device): the per-entry steps run in kernels, the decisions
+// over rows and tiles are the host builder's own helpers, so the layout is
+// the one pars3_split builds.
 #include "device_prims.cuh"
 
 #include <cmath>
@@ -139,6 +141,218 @@ __global__ void list_key_kernel(int count, const int32_t *__restrict__ list, con
     }
 }
 
+// ------------------------------------------------------------ layout (GPU side)
+//
+// The device layout is built from the canonical split as the host builder
+// builds it: the decisions over rows and tiles (which tiles keep the half
+// path, long rows, slice order, pieces, fold items) are the host builder's
+// own helpers, run on per-row and per-tile counts from the device; every
+// per-entry step runs here.
+
+// cent = entry positions in column order (row order within a column, a
+// stable sort of positions by column); colcnt counts the entries of each column
+__global__ void col_count_kernel(int nnz, const int32_t *__restrict__ col, int32_t *colcnt) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += gridDim.x * blockDim.x)
+        atomicAdd(&colcnt[col[q]], 1);
+}
+
+// half[q]: a middle entry of a tile that keeps the half path
+__global__ void half_flag_kernel(int nnz, int T, const uint32_t *__restrict__ rs, const uint8_t *__restrict__ cls,
+                                 const uint8_t *__restrict__ tile_on, uint8_t *__restrict__ half,
+                                 int32_t *__restrict__ hflag) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += gridDim.x * blockDim.x) {
+        const int h = cls[q] != 2 && tile_on[rs[q] / static_cast<uint32_t>(T)];
+        half[q] = static_cast<uint8_t>(h);
+        hflag[q] = h;
+    }
+}
+
+// A half entry's slot in its tile's (row, col) list: hoff[t] + its rank
+// among the tile's half entries; its window column and source entry there.
+__global__ void half_place_kernel(int nnz, int T, int W, const uint32_t *__restrict__ rs,
+                                  const int32_t *__restrict__ col, const uint8_t *__restrict__ half,
+                                  const int32_t *__restrict__ hscan, const int32_t *__restrict__ rowptr,
+                                  const int32_t *__restrict__ hoff, uint16_t *__restrict__ hcol,
+                                  int32_t *__restrict__ hsrc, int32_t *__restrict__ hpos) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += gridDim.x * blockDim.x) {
+        if (!half[q]) continue;
+        const int t = static_cast<int>(rs[q]) / T, r0 = t * T;
+        const int pos = hoff[t] + hscan[q] - hscan[rowptr[r0]];
+        hpos[q] = pos;
+        hcol[pos] = static_cast<uint16_t>(col[q] - (r0 - W));
+        hsrc[pos] = q + 1;
+    }
+}
+
+// tile-local row pointers of the half entries (T + 8 per tile; rows past the
+// tile's end repeat its count)
+__global__ void half_rowptr_kernel(int n, int nt, int T, const int32_t *__restrict__ rowptr,
+                                   const int32_t *__restrict__ hscan, uint16_t *__restrict__ hrp) {
+    const int64_t total = static_cast<int64_t>(nt) * (T + 8);
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < total;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int t = static_cast<int>(x / (T + 8)), i = static_cast<int>(x % (T + 8));
+        const int r0 = t * T, r1 = min(n, r0 + T), r = min(r0 + i, r1);
+        hrp[x] = static_cast<uint16_t>(hscan[rowptr[r]] - hscan[rowptr[r0]]);
+    }
+}
+
+// Walk of each half tile's (col, row) list: the (col, row) order's slots
+// (hcperm), the window position of each entry's row (hrowc), and the first
+// entry of every distinct column (a segment; halo segments have a column
+// before the tile), counted per tile.
+__global__ void segment_kernel(int M, int T, int W, const int32_t *__restrict__ tlist,
+                               const int32_t *__restrict__ tile_ptr, const uint32_t *__restrict__ rs,
+                               const int32_t *__restrict__ col, const uint8_t *__restrict__ tile_on,
+                               const int32_t *__restrict__ hoff, const int32_t *__restrict__ hpos,
+                               uint16_t *__restrict__ hcperm, uint16_t *__restrict__ hrowc,
+                               int32_t *__restrict__ segflag, int32_t *nseg, int32_t *nhalo) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < M; s += gridDim.x * blockDim.x) {
+        const int e = tlist[s];
+        const int t = static_cast<int>(rs[e]) / T, r0 = t * T;
+        if (!tile_on[t]) {
+            segflag[s] = 0;
+            continue;
+        }
+        const int k = s - tile_ptr[t];
+        const int pos = hoff[t] + k;
+        hcperm[pos] = static_cast<uint16_t>(hpos[e] - hoff[t]);
+        hrowc[pos] = static_cast<uint16_t>(static_cast<int>(rs[e]) - (r0 - W));
+        const int j = col[e];
+        const bool first = k == 0 || col[tlist[s - 1]] != j;
+        segflag[s] = first;
+        if (first) {
+            atomicAdd(&nseg[t], 1);
+            if (j < r0) atomicAdd(&nhalo[t], 1);
+        }
+    }
+}
+
+// segment words (window position | first (col, row) index << 16) at the
+// segment's rank in its tile; halo segments come first, so a halo
+// segment's rank is also its halo target index
+__global__ void segment_write_kernel(int M, int T, int W, const int32_t *__restrict__ tlist,
+                                     const int32_t *__restrict__ tile_ptr, const uint32_t *__restrict__ rs,
+                                     const int32_t *__restrict__ col, const int32_t *__restrict__ segflag,
+                                     const int32_t *__restrict__ segscan, const int32_t *__restrict__ hcsoff,
+                                     const int32_t *__restrict__ hhoff, uint32_t *__restrict__ hcs,
+                                     int32_t *__restrict__ hhrow) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < M; s += gridDim.x * blockDim.x) {
+        if (!segflag[s]) continue;
+        const int e = tlist[s];
+        const int t = static_cast<int>(rs[e]) / T, r0 = t * T;
+        const int k = s - tile_ptr[t];
+        const int rank = segscan[s] - segscan[tile_ptr[t]];
+        const int j = col[e];
+        hcs[hcsoff[t] + rank] = static_cast<uint32_t>(j - (r0 - W)) | (static_cast<uint32_t>(k) << 16);
+        if (j < r0) hhrow[hhoff[t] + rank] = j;
+    }
+}
+
+// end words: every word of a tile after its segments is 0xffff | count << 16
+__global__ void segment_end_kernel(int nt, const int32_t *__restrict__ hcsoff, const int32_t *__restrict__ nseg,
+                                   const int32_t *__restrict__ hcnt, uint32_t *__restrict__ hcs) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x)
+        for (int w = hcsoff[t] + nseg[t]; w < hcsoff[t + 1]; ++w)
+            hcs[w] = 0xffffu | (static_cast<uint32_t>(hcnt[t]) << 16);
+}
+
+// full-path length of every row: its non-half lower entries and the
+// non-half entries of its column (mirrored)
+__global__ void full_len_kernel(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ cptr,
+                                const int32_t *__restrict__ cent, const uint8_t *__restrict__ half,
+                                int32_t *__restrict__ flen) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) c += !half[q];
+        for (int s = cptr[i]; s < cptr[i + 1]; ++s) c += !half[cent[s]];
+        flen[i] = c;
+    }
+}
+
+// Row i's full-path entries (lower ones in column order, then the mirrored
+// ones of its column in row order) at out[base + m * stride]: the column
+// and the source (+(q+1) lower, -(q+1) mirrored).  One thread per row.
+__device__ __forceinline__ void emit_full_row(int i, const int32_t *__restrict__ rowptr,
+                                              const int32_t *__restrict__ col, const int32_t *__restrict__ cptr,
+                                              const int32_t *__restrict__ cent, const uint32_t *__restrict__ rs,
+                                              const uint8_t *__restrict__ half, int64_t base, int stride,
+                                              int32_t *__restrict__ ocol, int32_t *__restrict__ osrc) {
+    int64_t o = base;
+    for (int q = rowptr[i]; q < rowptr[i + 1]; ++q)
+        if (!half[q]) {
+            ocol[o] = col[q];
+            osrc[o] = q + 1;
+            o += stride;
+        }
+    for (int s = cptr[i]; s < cptr[i + 1]; ++s) {
+        const int q = cent[s];
+        if (!half[q]) {
+            ocol[o] = static_cast<int32_t>(rs[q]);
+            osrc[o] = -(q + 1);
+            o += stride;
+        }
+    }
+}
+
+__global__ void emit_slices_kernel(int n, const int32_t *__restrict__ row_base, const int32_t *__restrict__ rowptr,
+                                   const int32_t *__restrict__ col, const int32_t *__restrict__ cptr,
+                                   const int32_t *__restrict__ cent, const uint32_t *__restrict__ rs,
+                                   const uint8_t *__restrict__ half, int32_t *__restrict__ fcol,
+                                   int32_t *__restrict__ fsrc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (row_base[i] >= 0) emit_full_row(i, rowptr, col, cptr, cent, rs, half, row_base[i], 32, fcol, fsrc);
+}
+
+__global__ void emit_long_kernel(int nlong, const int32_t *__restrict__ lrow, const int32_t *__restrict__ lrp,
+                                 const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                 const int32_t *__restrict__ cptr, const int32_t *__restrict__ cent,
+                                 const uint32_t *__restrict__ rs, const uint8_t *__restrict__ half,
+                                 int32_t *__restrict__ lflat, int32_t *__restrict__ lsflat) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlong; l += gridDim.x * blockDim.x)
+        emit_full_row(lrow[l], rowptr, col, cptr, cent, rs, half, lrp[l], 1, lflat, lsflat);
+}
+
+// piece p (first entry e0, length len) goes to lane p % 32 of long slice p / 32
+__global__ void piece_scatter_kernel(int npieces, const int2 *__restrict__ pieces, const int32_t *__restrict__ ls_ent,
+                                     const int32_t *__restrict__ lflat, const int32_t *__restrict__ lsflat,
+                                     int32_t *__restrict__ lcol, int32_t *__restrict__ lsrc) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npieces; p += gridDim.x * blockDim.x) {
+        const int2 pc = pieces[p];
+        const int64_t base = static_cast<int64_t>(ls_ent[p / 32]) + (p % 32);
+        for (int m = 0; m < pc.y; ++m) {
+            lcol[base + 32LL * m] = lflat[pc.x + m];
+            lsrc[base + 32LL * m] = lsflat[pc.x + m];
+        }
+    }
+}
+
+// bf16 bits of an fp32 value, round to nearest even (quiet NaNs keep a payload bit)
+__device__ __forceinline__ uint16_t bf16_rne_bits(float f) {
+    uint32_t u = __float_as_uint(f);
+    if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) return static_cast<uint16_t>((u >> 16) | 0x40u);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return static_cast<uint16_t>(u >> 16);
+}
+
+// values of every slot from its source (+(q+1) lower, -(q+1) mirrored with
+// the mirror sign, 0 padding), in each packed precision
+__global__ void fill_values_kernel(int64_t m, const int32_t *__restrict__ src, const double *__restrict__ val,
+                                   int symmetric, double *__restrict__ v64, float *__restrict__ v32,
+                                   uint16_t *__restrict__ v16) {
+    for (int64_t x = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; x < m;
+         x += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int s = src[x];
+        double a = 0.0;
+        if (s > 0) a = val[s - 1];
+        else if (s < 0) a = symmetric ? val[-s - 1] : -val[-s - 1];
+        const float f = static_cast<float>(a);
+        if (v64) v64[x] = a;
+        if (v32) v32[x] = f;
+        if (v16) v16[x] = s == 0 ? 0 : bf16_rne_bits(f);
+    }
+}
+
 }  // namespace
 }  // namespace pars3
 
@@ -150,6 +364,200 @@ int download(std::vector<T> &dst, const T *src, size_t count, cudaStream_t st) {
     dst.resize(count);
     if (count == 0) return PARS3_OK;
     return cuda_status(cudaMemcpyAsync(dst.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost, st));
+}
+
+template <typename T>
+int upload(T *dst, const std::vector<T> &src, cudaStream_t st) {
+    if (src.empty()) return PARS3_OK;
+    return cuda_status(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, st));
+}
+
+// the canonical split in device memory
+struct DevCanon {
+    const uint32_t *rs;       // row of every sorted entry
+    const int32_t *col, *rowptr, *tile_ptr, *tlist;
+    const double *val;
+    const uint8_t *cls;
+    const int32_t *cptr, *cent;   // column view
+};
+
+// One attempt of the layout build at half-path capacity mcap (as
+// build_layout_try on the host).  Every host vector of h->L is filled.
+int layout_try_device(pars3_handle *h, const DevCanon &C, int64_t mcap, cudaStream_t st) {
+    Layout &L = h->L;
+    L = Layout();
+    const int32_t n = h->n, T = h->T, W = h->W, nt = h->ntiles;
+    const int nnz = static_cast<int>(h->nnz);
+    const int M = h->tile_ptr.empty() ? 0 : h->tile_ptr[nt];
+    const int G = kThreads;
+    Scratch S;
+    int rc;
+    // ---- 1. half path
+    std::vector<int32_t> tcount(nt);
+    for (int32_t t = 0; t < nt; ++t) tcount[t] = h->tile_ptr[t + 1] - h->tile_ptr[t];
+    half_tiles(h, mcap, tcount);
+    std::vector<uint8_t> on(nt);
+    for (int32_t t = 0; t < nt; ++t) on[t] = tcount[t] > 0;
+    const int64_t hn = L.hoff[nt];
+    const int64_t nrp = static_cast<int64_t>(nt) * (T + 8);
+    uint8_t *tile_on = S.get<uint8_t>(nt), *half = S.get<uint8_t>(nnz);
+    int32_t *hoff = S.get<int32_t>(nt + 1), *hcnt = S.get<int32_t>(nt), *hflag = S.get<int32_t>(nnz);
+    int32_t *hscan = S.get<int32_t>(static_cast<size_t>(nnz) + 1), *hpos = S.get<int32_t>(nnz);
+    uint16_t *hcol = S.get<uint16_t>(hn), *hcperm = S.get<uint16_t>(hn), *hrowc = S.get<uint16_t>(hn);
+    uint16_t *hrp = S.get<uint16_t>(nrp);
+    int32_t *hsrc = S.get<int32_t>(hn);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    if ((rc = upload(tile_on, on, st)) != PARS3_OK || (rc = upload(hoff, L.hoff, st)) != PARS3_OK ||
+        (rc = upload(hcnt, L.hcnt, st)) != PARS3_OK)
+        return rc;
+    cudaMemsetAsync(hcol, 0, sizeof(uint16_t) * hn, st);
+    cudaMemsetAsync(hcperm, 0, sizeof(uint16_t) * hn, st);
+    cudaMemsetAsync(hrowc, 0, sizeof(uint16_t) * hn, st);
+    cudaMemsetAsync(hsrc, 0, sizeof(int32_t) * hn, st);
+    half_flag_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, T, C.rs, C.cls, tile_on, half, hflag);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(hflag, hscan, nullptr, nnz);
+    half_place_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, T, W, C.rs, C.col, half, hscan, C.rowptr, hoff, hcol,
+                                                      hsrc, hpos);
+    half_rowptr_kernel<<<grid_for(nrp, G), G, 0, st>>>(n, nt, T, C.rowptr, hscan, hrp);
+    // column segments
+    int32_t *segflag = S.get<int32_t>(M), *segscan = S.get<int32_t>(static_cast<size_t>(M) + 1);
+    int32_t *nseg = S.get<int32_t>(nt), *nhalo = S.get<int32_t>(nt);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    cudaMemsetAsync(nseg, 0, sizeof(int32_t) * nt, st);
+    cudaMemsetAsync(nhalo, 0, sizeof(int32_t) * nt, st);
+    segment_kernel<<<grid_for(M, G), G, 0, st>>>(M, T, W, C.tlist, C.tile_ptr, C.rs, C.col, tile_on, hoff, hpos,
+                                                 hcperm, hrowc, segflag, nseg, nhalo);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(segflag, segscan, nullptr, M);
+    std::vector<int32_t> nseg_h, nhalo_h;
+    if ((rc = download(nseg_h, nseg, nt, st)) != PARS3_OK || (rc = download(nhalo_h, nhalo, nt, st)) != PARS3_OK ||
+        (rc = cuda_status(cudaStreamSynchronize(st))) != PARS3_OK)
+        return rc;
+    L.hcsoff.assign(static_cast<size_t>(nt) + 1, 0);
+    L.hhoff.assign(static_cast<size_t>(nt) + 1, 0);
+    L.hcsn.assign(nt, 0);
+    L.max_tile_cs = 0;
+    for (int32_t t = 0; t < nt; ++t) {
+        L.hcsn[t] = nseg_h[t];
+        L.hcsoff[t + 1] = static_cast<int32_t>(L.hcsoff[t] + round_up(nseg_h[t] + 1, 4));
+        L.hhoff[t + 1] = L.hhoff[t] + nhalo_h[t];
+        L.max_tile_cs = std::max(L.max_tile_cs, L.hcsoff[t + 1] - L.hcsoff[t]);
+    }
+    int32_t *hcsoff = S.get<int32_t>(nt + 1), *hhoff = S.get<int32_t>(nt + 1);
+    uint32_t *hcs = S.get<uint32_t>(L.hcsoff[nt]);
+    int32_t *hhrow = S.get<int32_t>(L.hhoff[nt]);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    if ((rc = upload(hcsoff, L.hcsoff, st)) != PARS3_OK || (rc = upload(hhoff, L.hhoff, st)) != PARS3_OK) return rc;
+    segment_write_kernel<<<grid_for(M, G), G, 0, st>>>(M, T, W, C.tlist, C.tile_ptr, C.rs, C.col, segflag, segscan,
+                                                       hcsoff, hhoff, hcs, hhrow);
+    segment_end_kernel<<<grid_for(nt, G), G, 0, st>>>(nt, hcsoff, nseg, hcnt, hcs);
+    // ---- 2. full-path lengths
+    int32_t *flen = S.get<int32_t>(n);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    full_len_kernel<<<grid_for(n, G), G, 0, st>>>(n, C.rowptr, C.cptr, C.cent, half, flen);
+    std::vector<int32_t> flen_h;
+    if ((rc = download(flen_h, flen, n, st)) != PARS3_OK || (rc = download(L.hhrow, hhrow, L.hhoff[nt], st)) != PARS3_OK ||
+        (rc = cuda_status(cudaStreamSynchronize(st))) != PARS3_OK)
+        return rc;
+    int64_t ftotal = 0;
+    for (int32_t i = 0; i < n; ++i) ftotal += flen_h[i];
+    // ---- 3. long rows
+    std::vector<uint8_t> is_long;
+    long_rows(h, flen_h, ftotal, 0, is_long);
+    // ---- 4. slices: each tile's rows by full length, longest first, ties by
+    // row (a counting sort per tile: short rows have at most kSellMax entries)
+    std::vector<int32_t> slen(n), rows(n), row_base;
+    for (int32_t i = 0; i < n; ++i) slen[i] = is_long[i] ? 0 : flen_h[i];
+    {
+        std::vector<int32_t> bucket(kSellMax + 2);
+        for (int32_t t = 0; t < nt; ++t) {
+            const int32_t r0 = t * T, r1 = std::min(n, r0 + T);
+            std::fill(bucket.begin(), bucket.end(), 0);
+            for (int32_t i = r0; i < r1; ++i) ++bucket[kSellMax - slen[i] + 1];
+            for (int b = 0; b <= kSellMax; ++b) bucket[b + 1] += bucket[b];
+            for (int32_t i = r0; i < r1; ++i) rows[r0 + bucket[kSellMax - slen[i]]++] = i;
+        }
+    }
+    if ((rc = slice_rows(h, rows, slen, row_base)) != PARS3_OK) return rc;
+    const int64_t fnp = L.sl_ent.back();
+    int32_t *rbase = S.get<int32_t>(n), *fcol = S.get<int32_t>(fnp), *fsrc = S.get<int32_t>(fnp);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    if ((rc = upload(rbase, row_base, st)) != PARS3_OK) return rc;
+    cudaMemsetAsync(fcol, 0, sizeof(int32_t) * fnp, st);
+    cudaMemsetAsync(fsrc, 0, sizeof(int32_t) * fnp, st);
+    emit_slices_kernel<<<grid_for(n, G), G, 0, st>>>(n, rbase, C.rowptr, C.col, C.cptr, C.cent, C.rs, half, fcol,
+                                                     fsrc);
+    // ---- 5. long rows in pieces
+    std::vector<PieceRef> pieces;
+    if ((rc = long_pieces(h, is_long, flen_h, pieces)) != PARS3_OK) return rc;
+    const int nlong = static_cast<int>(L.lrow.size());
+    const int64_t ltot = L.lrp.back(), lslots = L.ls_ent.back();
+    const int npieces = static_cast<int>(pieces.size());
+    std::vector<int2> pc(npieces);
+    for (int p = 0; p < npieces; ++p) pc[p] = make_int2(pieces[p].e0, pieces[p].len);
+    int32_t *lrow = S.get<int32_t>(nlong), *lrp = S.get<int32_t>(static_cast<size_t>(nlong) + 1);
+    int32_t *lflat = S.get<int32_t>(ltot), *lsflat = S.get<int32_t>(ltot), *ls_ent = S.get<int32_t>(L.ls_ent.size());
+    int32_t *lcol = S.get<int32_t>(lslots), *lsrc = S.get<int32_t>(lslots);
+    int2 *pcs = S.get<int2>(npieces);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    if ((rc = upload(lrow, L.lrow, st)) != PARS3_OK || (rc = upload(lrp, L.lrp, st)) != PARS3_OK ||
+        (rc = upload(ls_ent, L.ls_ent, st)) != PARS3_OK || (rc = upload(pcs, pc, st)) != PARS3_OK)
+        return rc;
+    cudaMemsetAsync(lcol, 0, sizeof(int32_t) * lslots, st);
+    cudaMemsetAsync(lsrc, 0, sizeof(int32_t) * lslots, st);
+    emit_long_kernel<<<grid_for(nlong, G), G, 0, st>>>(nlong, lrow, lrp, C.rowptr, C.col, C.cptr, C.cent, C.rs, half,
+                                                       lflat, lsflat);
+    piece_scatter_kernel<<<grid_for(npieces, G), G, 0, st>>>(npieces, pcs, ls_ent, lflat, lsflat, lcol, lsrc);
+    // ---- 6. fold items
+    fold_items(h);
+    // ---- 7. values per precision, then everything to the host
+    const bool d64 = h->dtypes & PARS3_DTYPE_BIT(PARS3_F64), d32 = h->dtypes & PARS3_DTYPE_BIT(PARS3_F32),
+               d16 = h->dtypes & PARS3_DTYPE_BIT(PARS3_BF16);
+    struct Part {
+        const int32_t *src;
+        int64_t m;
+        std::vector<double> *v64;
+        std::vector<float> *v32;
+        std::vector<uint16_t> *v16;
+    } parts[3] = {{hsrc, hn, &L.hval64, &L.hval32, &L.hval16},
+                  {fsrc, fnp, &L.fval64, &L.fval32, &L.fval16},
+                  {lsrc, lslots, &L.lval64, &L.lval32, &L.lval16}};
+    for (const Part &pt : parts) {
+        Scratch V;
+        double *v64 = d64 ? V.get<double>(pt.m) : nullptr;
+        float *v32 = d32 ? V.get<float>(pt.m) : nullptr;
+        uint16_t *v16 = d16 ? V.get<uint16_t>(pt.m) : nullptr;
+        if (V.err() != cudaSuccess) return PARS3_ENOMEM;
+        fill_values_kernel<<<grid_for(pt.m, G), G, 0, st>>>(pt.m, pt.src, C.val, h->symmetric, v64, v32, v16);
+        if (d64 && (rc = download(*pt.v64, static_cast<const double *>(v64), pt.m, st)) != PARS3_OK) return rc;
+        if (d32 && (rc = download(*pt.v32, static_cast<const float *>(v32), pt.m, st)) != PARS3_OK) return rc;
+        if (d16 && (rc = download(*pt.v16, static_cast<const uint16_t *>(v16), pt.m, st)) != PARS3_OK) return rc;
+        if ((rc = cuda_status(cudaStreamSynchronize(st))) != PARS3_OK) return rc;   // V is freed next
+    }
+    if ((rc = download(L.hcol, static_cast<const uint16_t *>(hcol), hn, st)) != PARS3_OK ||
+        (rc = download(L.hcperm, static_cast<const uint16_t *>(hcperm), hn, st)) != PARS3_OK ||
+        (rc = download(L.hrowc, static_cast<const uint16_t *>(hrowc), hn, st)) != PARS3_OK ||
+        (rc = download(L.hrp, static_cast<const uint16_t *>(hrp), nrp, st)) != PARS3_OK ||
+        (rc = download(L.hcs, static_cast<const uint32_t *>(hcs), L.hcsoff[nt], st)) != PARS3_OK ||
+        (rc = download(L.fcol, static_cast<const int32_t *>(fcol), fnp, st)) != PARS3_OK ||
+        (rc = download(L.lcol, static_cast<const int32_t *>(lcol), lslots, st)) != PARS3_OK)
+        return rc;
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+// The layout search of build_layout with the GPU attempt: start with every
+// middle entry of a fitting tile on the half path; while the tile block does
+// not fit shared memory, halve the largest half-path tile.
+int build_layout_device(pars3_handle *h, const DevCanon &C, cudaStream_t st) {
+    int64_t mcap = half_room(h);
+    if (mcap < 0) return PARS3_EUNSUPPORTED;
+    for (int iter = 0; iter < 40; ++iter) {
+        const int rc = layout_try_device(h, C, mcap, st);
+        if (rc != PARS3_OK) return rc;
+        if (max_smem_all(h) <= kSmemLimit) return PARS3_OK;
+        if (h->L.max_tile_half == 0) return PARS3_EUNSUPPORTED;
+        mcap = h->L.max_tile_half / 2;
+    }
+    return PARS3_EUNSUPPORTED;
 }
 
 int split_device(int32_t n, const int32_t *rp, const int32_t *ci, const double *val, const int32_t *perm,
@@ -263,7 +671,25 @@ int split_device(int32_t n, const int32_t *rp, const int32_t *ci, const double *
     vx = vo == va ? vb : va;
     list_key_kernel<<<grid_for(M, G), G, 0, st>>>(M, vo, col_s, rsorted, T, 1, kx);
     radix_sort(kx, vo, ko, vx, M, bits_for(ntiles), hist, hoff, st, &k2, &v2);
-    int32_t *tile_list = v2;
+    // the tile lists get their own buffer: the sort buffers are reused below
+    int32_t *tile_list = S.get<int32_t>(M), *outer_csc = S.get<int32_t>(O);
+    int32_t *colcnt = S.get<int32_t>(n), *cptr = S.get<int32_t>(static_cast<size_t>(n) + 1);
+    int32_t *cent = S.get<int32_t>(nnz);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    cudaMemcpyAsync(tile_list, v2, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st);
+    // outer lists: in position order (CSR), and stably by column (CSC)
+    cudaMemcpyAsync(va, olist, sizeof(int32_t) * O, cudaMemcpyDeviceToDevice, st);
+    list_key_kernel<<<grid_for(O, G), G, 0, st>>>(O, va, col_s, rsorted, T, 0, ka);
+    radix_sort(ka, va, kb, vb, O, nbits, hist, hoff, st, &ko, &vo);
+    cudaMemcpyAsync(outer_csc, vo, sizeof(int32_t) * O, cudaMemcpyDeviceToDevice, st);
+    // column view for the layout: entries of every column in row order
+    cudaMemsetAsync(colcnt, 0, sizeof(int32_t) * n, st);
+    col_count_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, col_s, colcnt);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(colcnt, cptr, nullptr, n);
+    iota_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, va);
+    list_key_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, va, col_s, rsorted, T, 0, ka);
+    radix_sort(ka, va, kb, vb, nnz, nbits, hist, hoff, st, &ko, &vo);
+    cudaMemcpyAsync(cent, vo, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st);
     pars3_handle *h = nullptr;
     try {
         h = new pars3_handle();
@@ -271,13 +697,6 @@ int split_device(int32_t n, const int32_t *rp, const int32_t *ci, const double *
         return PARS3_ENOMEM;
     }
     std::unique_ptr<pars3_handle> hold(h);
-    rc = download(h->tile_list, tile_list, M, st);
-    if (rc == PARS3_OK) rc = cuda_status(cudaStreamSynchronize(st));   // va / vb are reused below
-    if (rc != PARS3_OK) return rc;
-    // outer lists: in position order (CSR), and stably by column (CSC)
-    cudaMemcpyAsync(va, olist, sizeof(int32_t) * O, cudaMemcpyDeviceToDevice, st);
-    list_key_kernel<<<grid_for(O, G), G, 0, st>>>(O, va, col_s, rsorted, T, 0, ka);
-    radix_sort(ka, va, kb, vb, O, nbits, hist, hoff, st, &ko, &vo);
 
     // the handle: canonical arrays from the device, then the host layout
     try {
@@ -302,13 +721,17 @@ int split_device(int32_t n, const int32_t *rp, const int32_t *ci, const double *
         if (rc == PARS3_OK) rc = download(h->cls, cls, nnz, st);
         if (rc == PARS3_OK) rc = download(h->tile_ptr, tile_ptr, static_cast<size_t>(ntiles) + 1, st);
         if (rc == PARS3_OK) rc = download(h->outer_csr, olist, O, st);
-        if (rc == PARS3_OK) rc = download(h->outer_csc, vo, O, st);
+        if (rc == PARS3_OK) rc = download(h->outer_csc, static_cast<const int32_t *>(outer_csc), O, st);
+        if (rc == PARS3_OK) rc = download(h->tile_list, static_cast<const int32_t *>(tile_list), M, st);
         if (rc == PARS3_OK) rc = cuda_status(cudaStreamSynchronize(st));
         if (rc != PARS3_OK) return rc;
     } catch (const std::bad_alloc &) {
         return PARS3_ENOMEM;
     }
-    rc = split_finish(h, prm);
+    // the device layout, built on the GPU from the arrays still on it
+    set_layout_params(h, prm);
+    const DevCanon C{rsorted, col_s, rowptr, tile_ptr, tile_list, val_s, cls, cptr, cent};
+    rc = build_layout_device(h, C, st);
     if (rc != PARS3_OK) return rc;
     *out = hold.release();
     return PARS3_OK;

@@ -622,7 +622,7 @@ int check_layout_params(const pars3_split_params &p) {
     return PARS3_OK;
 }
 
-static void set_layout_params(pars3_handle *h, const pars3_split_params &p) {
+void set_layout_params(pars3_handle *h, const pars3_split_params &p) {
     h->long_row = p.long_row > 0 ? p.long_row : 0;
     h->piece = p.piece;
     h->lsb = p.long_slices;
@@ -642,18 +642,6 @@ int split_params_normalize(pars3_split_params *prm) {
 
 int check_cut(int32_t T, int32_t W) {
     return (!is_pow2(T) || !is_pow2(W) || W < 32 || W > T || T > 32768) ? PARS3_EINVAL : PARS3_OK;
-}
-
-// Completes a handle whose canonical split (perm, rowptr, col, val, cls,
-// tile and outer lists, counts, bw, T, W, ntiles) was filled elsewhere (the
-// GPU split): the layout parameters of p and the device layout.
-int split_finish(pars3_handle *h, const pars3_split_params &p) {
-    set_layout_params(h, p);
-    try {
-        return build_layout(h);
-    } catch (const std::bad_alloc &) {
-        return PARS3_ENOMEM;
-    }
 }
 
 // A handle with the same reordered matrix as src (perm, band CSR, packed

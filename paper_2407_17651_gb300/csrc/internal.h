@@ -161,7 +161,7 @@ int split_recut(const pars3_handle *src, const pars3_split_params &p, pars3_hand
 int check_layout_params(const pars3_split_params &p);
 int split_params_normalize(pars3_split_params *prm);
 int check_cut(int32_t T, int32_t W);
-int split_finish(pars3_handle *h, const pars3_split_params &p);
+void set_layout_params(pars3_handle *h, const pars3_split_params &p);
 // layout-build decisions shared by the host and GPU builders (host_split.cpp)
 struct PieceRef {
     int32_t l, e0, len;   // long row, first entry in the concatenated long-row list, length

@@ -2,8 +2,9 @@
 and the oracle (Sec. 3.1.2, Eq. 2, Figs. 7-8): every exported array --
 reordered CSR with the re-triangularization sign flip, classes, per-tile
 middle lists in (col, row) order, outer lists in CSR and CSC order, counts,
-cut points -- must be identical, element for element; the layouts built
-from them must be identical too (same products, bit for bit)."""
+cut points -- must be identical, element for element; the device layout,
+built on the GPU, must equal the host-built one (same digest over every
+layout array, same products bit for bit)."""
 import numpy as np
 import pytest
 
@@ -40,6 +41,7 @@ def _compare(A, perm, oracle=True, **kw):
     for k in KEYS + ("T", "W", "ntiles", "nnz"):
         assert np.array_equal(np.asarray(ed[k]), np.asarray(eh[k])), (A.name, k, kw)
     assert P.pars3_info_get(hd) == P.pars3_info_get(hh), A.name
+    assert P.pars3_layout_digest(hd) == P.pars3_layout_digest(hh), (A.name, kw)   # the layout built on the GPU
     assert P.pars3_layout_check(hd) == 0
     if oracle:
         so = O.split(A, perm if perm is not None else np.arange(A.n, dtype=np.int32), ed["T"], ed["W"],
