@@ -373,8 +373,10 @@ int pars3_check(const pars3_handle *h, void *stream);
  * over powers of two), then, for matrices with long rows, the long-row
  * threshold, piece length and long slices per block, then the tile kernel
  * variant (fp32 / bf16, k = 1) or the lane width of the multi-vector
- * product (k > 1).  The matrix arguments are those of pars3_split.  Leaves
- * no device state behind.  Errors: as pars3_split and pars3_upload. */
+ * product (k > 1).  The matrix arguments are those of pars3_split (host
+ * arrays); they are copied to the device, reordered there once, and every
+ * candidate is split on the GPU as pars3_split_device splits it.  Leaves no
+ * device state behind.  Errors: as pars3_split_device and pars3_upload. */
 int pars3_autotune(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
                    const int32_t *perm, const pars3_split_params *base, int32_t dtype, int32_t k,
                    pars3_split_params *best, double *best_us);

@@ -19,10 +19,11 @@
 // than the matrix's band holds no more entries.  A candidate replaces the
 // incumbent only when it is at least 2 % faster, so near-ties keep the
 // earlier (simpler) choice.  Candidates the layout cannot hold (shared
-// memory) are skipped.  The matrix is reordered and sorted once; each
-// candidate re-runs only the cut-dependent stages of the split, is uploaded,
-// timed (3 warm-up products, then the median of 3 groups of 8 products
-// measured with CUDA events) and freed.
+// memory) are skipped.  The matrix is reordered and sorted once, on the GPU
+// (the cut-independent stages of pars3_split_device); each candidate re-runs
+// only the cut-dependent stages, also on the GPU, is uploaded, timed (3
+// warm-up products, then the median of 3 groups of 8 products measured with
+// CUDA events) and freed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,7 +38,7 @@ namespace {
 
 struct Timer {
     int32_t n = 0, dtype = 0, k = 1;
-    const pars3_handle *tmpl = nullptr;   // reordered matrix; candidates re-cut it
+    DevBase *base = nullptr;   // reordered matrix on the device; candidates re-cut it
     void *X = nullptr, *Y = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -46,7 +47,7 @@ struct Timer {
     int time(const pars3_split_params &p, double *us) {
         *us = INFINITY;
         pars3_handle *h = nullptr;
-        int rc = split_recut(tmpl, p, &h);
+        int rc = devbase_cut(base, p, &h, st);
         if (rc == PARS3_EUNSUPPORTED) return PARS3_OK;
         if (rc != PARS3_OK) return rc;
         rc = pars3_upload(h, st);
@@ -79,16 +80,41 @@ struct Timer {
     }
 };
 
-// longest row of the full-storage (both triangles) pattern
-int64_t max_full_row(const pars3_handle *h) {
-    std::vector<int32_t> deg(static_cast<size_t>(h->n), 0);
-    for (int32_t i = 0; i < h->n; ++i) {
-        deg[i] += h->rowptr[i + 1] - h->rowptr[i];
-        for (int32_t e = h->rowptr[i]; e < h->rowptr[i + 1]; ++e) ++deg[h->col[e]];
+// longest row of the full-storage (both triangles) pattern: the largest
+// vertex degree, which no reordering changes
+int64_t max_full_row(int32_t n, const int32_t *rowptr, const int32_t *col) {
+    std::vector<int32_t> deg(static_cast<size_t>(n), 0);
+    for (int32_t i = 0; i < n; ++i) {
+        deg[i] += rowptr[i + 1] - rowptr[i];
+        for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) ++deg[col[e]];
     }
     int64_t m = 0;
     for (int32_t d : deg) m = std::max<int64_t>(m, d);
     return m;
+}
+
+// the inputs on the device, for building the reordered matrix there
+int device_base(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const int32_t *perm,
+                int symmetric, cudaStream_t st, DevBase **out) {
+    const int64_t nnz = rowptr[n];
+    int32_t *d_rp = nullptr, *d_ci = nullptr, *d_perm = nullptr;
+    double *d_val = nullptr;
+    cudaError_t e = cudaMalloc(&d_rp, sizeof(int32_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_ci, sizeof(int32_t) * std::max<int64_t>(1, nnz));
+    if (e == cudaSuccess) e = cudaMalloc(&d_val, sizeof(double) * std::max<int64_t>(1, nnz));
+    if (e == cudaSuccess && perm) e = cudaMalloc(&d_perm, sizeof(int32_t) * std::max(1, n));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_ci, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_val, val, sizeof(double) * nnz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && perm) e = cudaMemcpyAsync(d_perm, perm, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+    int rc = cuda_status(e);
+    if (rc == PARS3_OK) rc = devbase_create(n, d_rp, d_ci, d_val, d_perm, symmetric, out, st);
+    cudaStreamSynchronize(st);
+    cudaFree(d_rp);
+    cudaFree(d_ci);
+    cudaFree(d_val);
+    if (d_perm) cudaFree(d_perm);
+    return rc;
 }
 
 int32_t pow2_ceil(int64_t v) {
@@ -124,22 +150,21 @@ extern "C" int pars3_autotune(int32_t n, const int32_t *rowptr, const int32_t *c
         return PARS3_OK;
     }
 
+    if (rowptr[n] > 0 && !val) return PARS3_EINVAL;
+    if ((b0.flags & ~PARS3_SPLIT_SYMMETRIC) || (b0.dtypes & ~7)) return PARS3_EINVAL;
     const int32_t wcap = (b0.dtypes & PARS3_DTYPE_BIT(PARS3_F64)) ? 1024 : 2048;
-    pars3_handle *tmpl = nullptr;
-    {
-        pars3_split_params p0 = b0;
-        p0.T = 1024;
-        p0.W = 32;
-        rc = pars3_split(n, rowptr, col, val, perm, &p0, &tmpl);
-        if (rc != PARS3_OK) return rc;
+    cudaError_t e = cudaStreamCreateWithFlags(&tm.st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status(e);
+    rc = device_base(n, rowptr, col, val, perm, (b0.flags & PARS3_SPLIT_SYMMETRIC) ? 1 : 0, tm.st, &tm.base);
+    if (rc != PARS3_OK) {
+        cudaStreamDestroy(tm.st);
+        return rc;
     }
-    tm.tmpl = tmpl;
-    const int32_t wmax = std::min(pow2_ceil(tmpl->bw), wcap);
+    const int32_t wmax = std::min(pow2_ceil(devbase_bandwidth(tm.base)), wcap);
 
     const size_t vsz = dtype == PARS3_F64 ? 8 : 4;
     const size_t bytes = std::max<size_t>(16, static_cast<size_t>(n) * k * vsz);
-    cudaError_t e = cudaStreamCreateWithFlags(&tm.st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&tm.X, bytes);
+    e = cudaMalloc(&tm.X, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&tm.Y, bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(tm.X, 0, bytes, tm.st);
     if (e == cudaSuccess) e = cudaEventCreate(&tm.e0);
@@ -183,7 +208,7 @@ extern "C" int pars3_autotune(int32_t n, const int32_t *rowptr, const int32_t *c
     }
     // 4. long rows: (threshold, piece, slices per block) against the incumbent's
     // defaults (128, 192, 32)
-    if (bp.T > 0 && base_layout_default && max_full_row(tmpl) > 32) {
+    if (bp.T > 0 && base_layout_default && max_full_row(n, rowptr, col) > 32) {
         const int32_t T4 = bp.T;
         struct L3 { int32_t long_row, piece, slices; };
         for (const L3 &l : {L3{32, 255, 16}, L3{128, 255, 16}, L3{32, 192, 32}, L3{64, 128, 32}}) {
@@ -218,7 +243,7 @@ extern "C" int pars3_autotune(int32_t n, const int32_t *rowptr, const int32_t *c
     if (tm.X) cudaFree(tm.X);
     if (tm.Y) cudaFree(tm.Y);
     if (tm.st) cudaStreamDestroy(tm.st);
-    pars3_free(tmpl);
+    devbase_free(tm.base);
     if (rc != PARS3_OK) return rc;
     if (bp.T == 0) return PARS3_EUNSUPPORTED;
     *best = bp;

@@ -560,26 +560,44 @@ int build_layout_device(pars3_handle *h, const DevCanon &C, cudaStream_t st) {
     return PARS3_EUNSUPPORTED;
 }
 
-int split_device(int32_t n, const int32_t *rp, const int32_t *ci, const double *val, const int32_t *perm,
-                 const pars3_split_params *p, pars3_handle **out, cudaStream_t st) {
-    if (!out || n < 0 || !rp) return PARS3_EINVAL;
-    *out = nullptr;
-    pars3_split_params prm{};
-    if (p) prm = *p;
-    if (split_params_normalize(&prm) != PARS3_OK) return PARS3_EINVAL;
+}  // namespace
+
+// The reordered matrix on the device: the stages of the split that do not
+// depend on the cut (checks, re-triangularization, (row, col) order, column
+// view), kept for any number of cuts (pars3_split_device makes one, the
+// autotuner one per candidate).  It owns its device memory.
+struct DevBase {
+    Scratch S;
+    int32_t n = 0, nnz = 0, sym = 0;
+    int64_t bw = 0;
+    uint32_t *rs = nullptr;   // row of every sorted entry
+    int32_t *col = nullptr, *rowptr = nullptr, *cptr = nullptr, *cent = nullptr;
+    double *val = nullptr;
+    uint32_t *ka = nullptr, *kb = nullptr;   // sort buffers
+    int32_t *va = nullptr, *vb = nullptr, *hist = nullptr, *hoff = nullptr;
+    std::vector<int32_t> perm_h, rowptr_h, col_h;   // host copies for the handles
+    std::vector<double> val_h;
+};
+
+namespace {
+
+int base_build(DevBase &B, int32_t n, const int32_t *rp, const int32_t *ci, const double *val, const int32_t *perm,
+               int sym, cudaStream_t st) {
     int32_t nnz = 0;
     int rc = fetch(&nnz, rp + n, sizeof(int32_t), st);
     if (rc != PARS3_OK) return rc;
     if (nnz < 0 || (n == 0 && nnz != 0)) return PARS3_ENOTSKEW;
     if (nnz > 0 && (!ci || !val)) return PARS3_EINVAL;
     const int G = kThreads;
-    const int sym = (prm.flags & PARS3_SPLIT_SYMMETRIC) ? 1 : 0;
-
-    Scratch S;
-    int *err = S.get<int>(1);
-    int32_t *off = S.get<int32_t>(4), *rowof = S.get<int32_t>(nnz), *deg = S.get<int32_t>(n + 1);
-    int32_t *pinv = S.get<int32_t>(n), *seen = S.get<int32_t>(n);
-    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    B.n = n;
+    B.nnz = nnz;
+    B.sym = sym;
+    Scratch T;   // temporaries of this stage
+    Scratch &S = B.S;
+    int *err = T.get<int>(1);
+    int32_t *off = T.get<int32_t>(4), *rowof = T.get<int32_t>(nnz), *deg = T.get<int32_t>(n + 1);
+    int32_t *pinv = T.get<int32_t>(n), *seen = T.get<int32_t>(n);
+    if (T.err() != cudaSuccess) return PARS3_ENOMEM;
     const int32_t off_h[4] = {0, n, 0, nnz};   // one block: vertices [0, n), entries [0, nnz)
     cudaError_t ce = cudaMemcpyAsync(off, off_h, sizeof(off_h), cudaMemcpyHostToDevice, st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(err, 0, sizeof(int), st);
@@ -604,55 +622,92 @@ int split_device(int32_t n, const int32_t *rp, const int32_t *ci, const double *
     }
 
     // 2-3. re-triangularize, then sort by (row, col): by column, then stably by row
-    uint32_t *ckey = S.get<uint32_t>(nnz), *rkey = S.get<uint32_t>(nnz);
-    uint32_t *ka = S.get<uint32_t>(nnz), *kb = S.get<uint32_t>(nnz);
-    int32_t *va = S.get<int32_t>(nnz), *vb = S.get<int32_t>(nnz);
-    double *vv = S.get<double>(nnz), *val_s = S.get<double>(nnz);
-    int32_t *col_s = S.get<int32_t>(nnz), *rowcnt = S.get<int32_t>(n), *rowptr = S.get<int32_t>(n + 1);
+    uint32_t *ckey = T.get<uint32_t>(nnz);
+    double *vv = T.get<double>(nnz);
+    int32_t *rowcnt = T.get<int32_t>(n), *colcnt = T.get<int32_t>(n);
+    unsigned long long *acc = T.get<unsigned long long>(1);
+    B.rs = S.get<uint32_t>(nnz);
+    B.ka = S.get<uint32_t>(nnz);
+    B.kb = S.get<uint32_t>(nnz);
+    B.va = S.get<int32_t>(nnz);
+    B.vb = S.get<int32_t>(nnz);
+    B.val = S.get<double>(nnz);
+    B.col = S.get<int32_t>(nnz);
+    B.rowptr = S.get<int32_t>(static_cast<size_t>(n) + 1);
+    B.cptr = S.get<int32_t>(static_cast<size_t>(n) + 1);
+    B.cent = S.get<int32_t>(nnz);
     const int stiles = (nnz + kSortTile - 1) / kSortTile;
-    int32_t *hist = S.get<int32_t>(256 * static_cast<size_t>(stiles) + 1);
-    int32_t *hoff = S.get<int32_t>(256 * static_cast<size_t>(stiles) + 1);
-    unsigned long long *acc = S.get<unsigned long long>(4);   // bandwidth, then the three class counts
-    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    B.hist = S.get<int32_t>(256 * static_cast<size_t>(stiles) + 1);
+    B.hoff = S.get<int32_t>(256 * static_cast<size_t>(stiles) + 1);
+    if (T.err() != cudaSuccess || S.err() != cudaSuccess) return PARS3_ENOMEM;
+    uint32_t *ka = B.ka, *kb = B.kb, *rkey = B.rs;
+    int32_t *va = B.va, *vb = B.vb;
     const int nbits = bits_for(n);
     retriangularize_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, ci, val, pinv, sym, ckey, rkey, va, vv);
     cudaMemcpyAsync(ka, ckey, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToDevice, st);
     uint32_t *ko, *k2;
     int32_t *vo, *v2;
-    radix_sort(ka, va, kb, vb, nnz, nbits, hist, hoff, st, &ko, &vo);
+    radix_sort(ka, va, kb, vb, nnz, nbits, B.hist, B.hoff, st, &ko, &vo);
     uint32_t *kx = ko == ka ? kb : ka;
     int32_t *vx = vo == va ? vb : va;
     gather_key_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, vo, rkey, kx);
-    radix_sort(kx, vo, ko, vx, nnz, nbits, hist, hoff, st, &k2, &v2);
+    radix_sort(kx, vo, ko, vx, nnz, nbits, B.hist, B.hoff, st, &k2, &v2);
     // the row of every sorted entry gets its own buffer: the sort buffers are reused below
-    uint32_t *rsorted = rkey;
-    cudaMemcpyAsync(rsorted, k2, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(B.rs, k2, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToDevice, st);
     const int32_t *order = v2;   // source entry of every sorted position (read by emit_kernel only)
     cudaMemsetAsync(rowcnt, 0, sizeof(int32_t) * n, st);
-    cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 4, st);
-    emit_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, order, rsorted, ckey, vv, col_s, val_s, rowcnt, acc);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(rowcnt, rowptr, nullptr, n);
+    cudaMemsetAsync(acc, 0, sizeof(unsigned long long), st);
+    emit_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, order, B.rs, ckey, vv, B.col, B.val, rowcnt, acc);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(rowcnt, B.rowptr, nullptr, n);
+    // column view for the layout: entries of every column in row order
+    cudaMemsetAsync(colcnt, 0, sizeof(int32_t) * n, st);
+    col_count_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, B.col, colcnt);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(colcnt, B.cptr, nullptr, n);
+    iota_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, va);
+    list_key_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, va, B.col, B.rs, 1, 0, ka);
+    radix_sort(ka, va, kb, vb, nnz, nbits, B.hist, B.hoff, st, &ko, &vo);
+    cudaMemcpyAsync(B.cent, vo, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st);
     unsigned long long bw = 0;
-    if ((rc = fetch(&bw, acc, sizeof(bw), st)) != PARS3_OK) return rc;
-
-    // the cut: given, or the default rule on the reordered bandwidth
-    if (prm.T == 0) {
-        const int32_t wcap = (prm.dtypes & PARS3_DTYPE_BIT(PARS3_F64)) ? 1024 : 2048;
-        auto_cut(static_cast<int64_t>(bw), 32, wcap, 1024, &prm.T, &prm.W);
+    cudaMemcpyAsync(&bw, acc, sizeof(bw), cudaMemcpyDeviceToHost, st);
+    // host copies
+    try {
+        if (perm) {
+            rc = download(B.perm_h, perm, n, st);
+        } else {
+            B.perm_h.resize(n);
+            for (int32_t k = 0; k < n; ++k) B.perm_h[k] = k;
+        }
+        if (rc == PARS3_OK) rc = download(B.rowptr_h, static_cast<const int32_t *>(B.rowptr), static_cast<size_t>(n) + 1, st);
+        if (rc == PARS3_OK) rc = download(B.col_h, static_cast<const int32_t *>(B.col), nnz, st);
+        if (rc == PARS3_OK) rc = download(B.val_h, static_cast<const double *>(B.val), nnz, st);
+        if (rc == PARS3_OK) rc = cuda_status(cudaStreamSynchronize(st));   // T is freed next
+    } catch (const std::bad_alloc &) {
+        return PARS3_ENOMEM;
     }
-    if (check_cut(prm.T, prm.W) != PARS3_OK) return PARS3_EINVAL;
-    const int T = prm.T, W = prm.W;
-    const int ntiles = n > 0 ? (n + T - 1) / T : 0;
+    B.bw = static_cast<int64_t>(bw);
+    return rc;
+}
 
-    // 4. classes, tile lists in (tile, col, position) order, outer lists
+// The cut-dependent stages for the cut (prm.T, prm.W): classes, tile lists
+// in (tile, col, position) order, outer lists, then the device layout on the
+// GPU.  prm is normalized and its cut valid.
+int base_cut(DevBase &B, const pars3_split_params &prm, pars3_handle **out, cudaStream_t st) {
+    const int n = B.n, nnz = B.nnz, T = prm.T, W = prm.W;
+    const int ntiles = n > 0 ? (n + T - 1) / T : 0;
+    const int G = kThreads;
+    const int nbits = bits_for(n);
+    int rc;
+    Scratch S;
     uint8_t *cls = S.get<uint8_t>(nnz);
     int32_t *mflag = S.get<int32_t>(nnz), *oflag = S.get<int32_t>(nnz);
-    int32_t *mpre = S.get<int32_t>(nnz + 1), *opre = S.get<int32_t>(nnz + 1);
-    int32_t *tcnt = S.get<int32_t>(ntiles), *tile_ptr = S.get<int32_t>(ntiles + 1);
+    int32_t *mpre = S.get<int32_t>(static_cast<size_t>(nnz) + 1), *opre = S.get<int32_t>(static_cast<size_t>(nnz) + 1);
+    int32_t *tcnt = S.get<int32_t>(ntiles), *tile_ptr = S.get<int32_t>(static_cast<size_t>(ntiles) + 1);
     int32_t *mlist = S.get<int32_t>(nnz), *olist = S.get<int32_t>(nnz);
+    unsigned long long *acc = S.get<unsigned long long>(3);
     if (S.err() != cudaSuccess) return PARS3_ENOMEM;
     cudaMemsetAsync(tcnt, 0, sizeof(int32_t) * ntiles, st);
-    classify_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, T, W, rsorted, col_s, cls, mflag, oflag, tcnt, acc + 1);
+    cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 3, st);
+    classify_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, T, W, B.rs, B.col, cls, mflag, oflag, tcnt, acc);
     scan_kernel<<<1, kScanThreads, 0, st>>>(mflag, mpre, nullptr, nnz);
     scan_kernel<<<1, kScanThreads, 0, st>>>(oflag, opre, nullptr, nnz);
     scan_kernel<<<1, kScanThreads, 0, st>>>(tcnt, tile_ptr, nullptr, ntiles);
@@ -662,34 +717,26 @@ int split_device(int32_t n, const int32_t *rp, const int32_t *ci, const double *
     unsigned long long cnt3[3] = {0, 0, 0};
     cudaMemcpyAsync(&M, mpre + nnz, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(&O, opre + nnz, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-    if ((rc = fetch(cnt3, acc + 1, sizeof(cnt3), st)) != PARS3_OK) return rc;
+    if ((rc = fetch(cnt3, acc, sizeof(cnt3), st)) != PARS3_OK) return rc;
     // middle list: positions (in order), stably by column, then stably by tile
+    uint32_t *ka = B.ka, *kb = B.kb, *ko, *k2;
+    int32_t *va = B.va, *vb = B.vb, *vo, *v2;
     cudaMemcpyAsync(va, mlist, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st);
-    list_key_kernel<<<grid_for(M, G), G, 0, st>>>(M, va, col_s, rsorted, T, 0, ka);
-    radix_sort(ka, va, kb, vb, M, nbits, hist, hoff, st, &ko, &vo);
-    kx = ko == ka ? kb : ka;
-    vx = vo == va ? vb : va;
-    list_key_kernel<<<grid_for(M, G), G, 0, st>>>(M, vo, col_s, rsorted, T, 1, kx);
-    radix_sort(kx, vo, ko, vx, M, bits_for(ntiles), hist, hoff, st, &k2, &v2);
+    list_key_kernel<<<grid_for(M, G), G, 0, st>>>(M, va, B.col, B.rs, T, 0, ka);
+    radix_sort(ka, va, kb, vb, M, nbits, B.hist, B.hoff, st, &ko, &vo);
+    uint32_t *kx = ko == ka ? kb : ka;
+    int32_t *vx = vo == va ? vb : va;
+    list_key_kernel<<<grid_for(M, G), G, 0, st>>>(M, vo, B.col, B.rs, T, 1, kx);
+    radix_sort(kx, vo, ko, vx, M, bits_for(ntiles), B.hist, B.hoff, st, &k2, &v2);
     // the tile lists get their own buffer: the sort buffers are reused below
     int32_t *tile_list = S.get<int32_t>(M), *outer_csc = S.get<int32_t>(O);
-    int32_t *colcnt = S.get<int32_t>(n), *cptr = S.get<int32_t>(static_cast<size_t>(n) + 1);
-    int32_t *cent = S.get<int32_t>(nnz);
     if (S.err() != cudaSuccess) return PARS3_ENOMEM;
     cudaMemcpyAsync(tile_list, v2, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st);
     // outer lists: in position order (CSR), and stably by column (CSC)
     cudaMemcpyAsync(va, olist, sizeof(int32_t) * O, cudaMemcpyDeviceToDevice, st);
-    list_key_kernel<<<grid_for(O, G), G, 0, st>>>(O, va, col_s, rsorted, T, 0, ka);
-    radix_sort(ka, va, kb, vb, O, nbits, hist, hoff, st, &ko, &vo);
+    list_key_kernel<<<grid_for(O, G), G, 0, st>>>(O, va, B.col, B.rs, T, 0, ka);
+    radix_sort(ka, va, kb, vb, O, nbits, B.hist, B.hoff, st, &ko, &vo);
     cudaMemcpyAsync(outer_csc, vo, sizeof(int32_t) * O, cudaMemcpyDeviceToDevice, st);
-    // column view for the layout: entries of every column in row order
-    cudaMemsetAsync(colcnt, 0, sizeof(int32_t) * n, st);
-    col_count_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, col_s, colcnt);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(colcnt, cptr, nullptr, n);
-    iota_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, va);
-    list_key_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, va, col_s, rsorted, T, 0, ka);
-    radix_sort(ka, va, kb, vb, nnz, nbits, hist, hoff, st, &ko, &vo);
-    cudaMemcpyAsync(cent, vo, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st);
     pars3_handle *h = nullptr;
     try {
         h = new pars3_handle();
@@ -697,30 +744,24 @@ int split_device(int32_t n, const int32_t *rp, const int32_t *ci, const double *
         return PARS3_ENOMEM;
     }
     std::unique_ptr<pars3_handle> hold(h);
-
-    // the handle: canonical arrays from the device, then the host layout
+    // the handle: canonical arrays, then the layout built on the GPU
     try {
         h->n = n;
         h->nnz = nnz;
         h->dtypes = prm.dtypes;
-        h->symmetric = sym;
+        h->symmetric = B.sym;
         h->T = T;
         h->W = W;
         h->ntiles = ntiles;
-        h->bw = static_cast<int64_t>(bw);
+        h->bw = B.bw;
         for (int k = 0; k < 3; ++k) h->counts[k] = static_cast<int64_t>(cnt3[k]);
-        if (perm) {
-            rc = download(h->perm, perm, n, st);
-        } else {
-            h->perm.resize(n);
-            for (int32_t k = 0; k < n; ++k) h->perm[k] = k;
-        }
-        if (rc == PARS3_OK) rc = download(h->rowptr, rowptr, static_cast<size_t>(n) + 1, st);
-        if (rc == PARS3_OK) rc = download(h->col, col_s, nnz, st);
-        if (rc == PARS3_OK) rc = download(h->val, val_s, nnz, st);
-        if (rc == PARS3_OK) rc = download(h->cls, cls, nnz, st);
-        if (rc == PARS3_OK) rc = download(h->tile_ptr, tile_ptr, static_cast<size_t>(ntiles) + 1, st);
-        if (rc == PARS3_OK) rc = download(h->outer_csr, olist, O, st);
+        h->perm = B.perm_h;
+        h->rowptr = B.rowptr_h;
+        h->col = B.col_h;
+        h->val = B.val_h;
+        rc = download(h->cls, static_cast<const uint8_t *>(cls), nnz, st);
+        if (rc == PARS3_OK) rc = download(h->tile_ptr, static_cast<const int32_t *>(tile_ptr), static_cast<size_t>(ntiles) + 1, st);
+        if (rc == PARS3_OK) rc = download(h->outer_csr, static_cast<const int32_t *>(olist), O, st);
         if (rc == PARS3_OK) rc = download(h->outer_csc, static_cast<const int32_t *>(outer_csc), O, st);
         if (rc == PARS3_OK) rc = download(h->tile_list, static_cast<const int32_t *>(tile_list), M, st);
         if (rc == PARS3_OK) rc = cuda_status(cudaStreamSynchronize(st));
@@ -728,13 +769,31 @@ int split_device(int32_t n, const int32_t *rp, const int32_t *ci, const double *
     } catch (const std::bad_alloc &) {
         return PARS3_ENOMEM;
     }
-    // the device layout, built on the GPU from the arrays still on it
     set_layout_params(h, prm);
-    const DevCanon C{rsorted, col_s, rowptr, tile_ptr, tile_list, val_s, cls, cptr, cent};
+    const DevCanon C{B.rs, B.col, B.rowptr, tile_ptr, tile_list, B.val, cls, B.cptr, B.cent};
     rc = build_layout_device(h, C, st);
     if (rc != PARS3_OK) return rc;
     *out = hold.release();
     return PARS3_OK;
+}
+
+int split_device(int32_t n, const int32_t *rp, const int32_t *ci, const double *val, const int32_t *perm,
+                 const pars3_split_params *p, pars3_handle **out, cudaStream_t st) {
+    if (!out || n < 0 || !rp) return PARS3_EINVAL;
+    *out = nullptr;
+    pars3_split_params prm{};
+    if (p) prm = *p;
+    if (split_params_normalize(&prm) != PARS3_OK) return PARS3_EINVAL;
+    DevBase B;
+    int rc = base_build(B, n, rp, ci, val, perm, (prm.flags & PARS3_SPLIT_SYMMETRIC) ? 1 : 0, st);
+    if (rc != PARS3_OK) return rc;
+    // the cut: given, or the default rule on the reordered bandwidth
+    if (prm.T == 0) {
+        const int32_t wcap = (prm.dtypes & PARS3_DTYPE_BIT(PARS3_F64)) ? 1024 : 2048;
+        auto_cut(B.bw, 32, wcap, 1024, &prm.T, &prm.W);
+    }
+    if (check_cut(prm.T, prm.W) != PARS3_OK) return PARS3_EINVAL;
+    return base_cut(B, prm, out, st);
 }
 
 }  // namespace
@@ -745,3 +804,37 @@ extern "C" int pars3_split_device(int32_t n, const int32_t *rowptr, const int32_
                                   void *stream) {
     return pars3::split_device(n, rowptr, col, val, perm, p, out, static_cast<cudaStream_t>(stream));
 }
+
+namespace pars3 {
+
+int devbase_create(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const int32_t *perm,
+                   int symmetric, DevBase **out, void *stream) {
+    *out = nullptr;
+    DevBase *b = nullptr;
+    try {
+        b = new DevBase();
+    } catch (const std::bad_alloc &) {
+        return PARS3_ENOMEM;
+    }
+    const int rc = base_build(*b, n, rowptr, col, val, perm, symmetric, static_cast<cudaStream_t>(stream));
+    if (rc != PARS3_OK) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return PARS3_OK;
+}
+
+int devbase_cut(DevBase *b, const pars3_split_params &p, pars3_handle **out, void *stream) {
+    *out = nullptr;
+    pars3_split_params prm = p;
+    if (split_params_normalize(&prm) != PARS3_OK || check_cut(prm.T, prm.W) != PARS3_OK) return PARS3_EINVAL;
+    if (!!(prm.flags & PARS3_SPLIT_SYMMETRIC) != !!b->sym) return PARS3_EINVAL;
+    return base_cut(*b, prm, out, static_cast<cudaStream_t>(stream));
+}
+
+int64_t devbase_bandwidth(const DevBase *b) { return b->bw; }
+
+void devbase_free(DevBase *b) { delete b; }
+
+}  // namespace pars3

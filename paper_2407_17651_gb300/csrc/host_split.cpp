@@ -644,40 +644,6 @@ int check_cut(int32_t T, int32_t W) {
     return (!is_pow2(T) || !is_pow2(W) || W < 32 || W > T || T > 32768) ? PARS3_EINVAL : PARS3_OK;
 }
 
-// A handle with the same reordered matrix as src (perm, band CSR, packed
-// precisions, mirror sign) and the cut points and layout parameters of p:
-// only the cut-dependent stages run.  Used by the autotuner.
-int split_recut(const pars3_handle *src, const pars3_split_params &p, pars3_handle **out) {
-    *out = nullptr;
-    const int32_t T = p.T, W = p.W;
-    if (!is_pow2(T) || !is_pow2(W) || W < 32 || W > T || T > 32768) return PARS3_EINVAL;
-    if (check_layout_params(p) != PARS3_OK) return PARS3_EINVAL;
-    pars3_handle *h = nullptr;
-    try {
-        h = new pars3_handle();
-        h->n = src->n;
-        h->nnz = src->nnz;
-        h->dtypes = src->dtypes;
-        set_layout_params(h, p);
-        h->symmetric = src->symmetric;
-        h->perm = src->perm;
-        h->rowptr = src->rowptr;
-        h->col = src->col;
-        h->val = src->val;
-        h->T = T;
-        h->W = W;
-        h->ntiles = h->n > 0 ? (h->n + T - 1) / T : 0;
-        canonical_classify(h);
-        const int rc = build_layout(h);
-        if (rc != PARS3_OK) { delete h; return rc; }
-    } catch (const std::bad_alloc &) {
-        delete h;
-        return PARS3_ENOMEM;
-    }
-    *out = h;
-    return PARS3_OK;
-}
-
 }  // namespace pars3
 
 using namespace pars3;

@@ -157,7 +157,6 @@ int validate_lower(int32_t n, const int32_t *rowptr, const int32_t *col);
 int64_t bandwidth(int32_t n, const int32_t *rowptr, const int32_t *col, const int32_t *pinv);
 
 // host_split.cpp
-int split_recut(const pars3_handle *src, const pars3_split_params &p, pars3_handle **out);
 int check_layout_params(const pars3_split_params &p);
 int split_params_normalize(pars3_split_params *prm);
 int check_cut(int32_t T, int32_t W);
@@ -175,6 +174,14 @@ int long_pieces(pars3_handle *h, const std::vector<uint8_t> &is_long, const std:
                 std::vector<PieceRef> &pieces);
 void fold_items(pars3_handle *h);
 int max_smem_all(const pars3_handle *h);
+// device_split.cu: the reordered matrix on the device (the cut-independent
+// split stages), re-cut on the GPU for any cut (pars3_split_device, the autotuner)
+struct DevBase;
+int devbase_create(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const int32_t *perm,
+                   int symmetric, DevBase **out, void *stream);
+int devbase_cut(DevBase *b, const pars3_split_params &p, pars3_handle **out, void *stream);
+int64_t devbase_bandwidth(const DevBase *b);
+void devbase_free(DevBase *b);
 int64_t half_room(const pars3_handle *h);
 // bit of the calling thread's current CUDA device (kernel attributes are set
 // once per device and kernel)
