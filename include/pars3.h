@@ -243,12 +243,14 @@ int pars3_split(int32_t n, const int32_t *rowptr, const int32_t *col, const doub
  * the device the pattern, values and permutation are checked, the entries
  * are permuted and re-triangularized (sign flip, Eq. 2), sorted by
  * (row, col), classified for (T, W) and listed per tile and in CSR / CSC
- * order; those arrays are copied into the new handle and its layout is then
- * built on the host as pars3_split builds it.  The result -- every array
- * pars3_split_export shows, and the layout -- is identical to pars3_split
- * with the same inputs and parameters.  Runs on `stream` and returns after
- * the handle is complete.  Allocates temporary device memory (about 80 bytes
- * per stored entry).  Errors as for pars3_split, plus ECUDA. */
+ * order, and the device layout is built from them (the decisions over rows
+ * and tiles by the host builder's own rules); the new handle holds host
+ * copies of all of it, as a pars3_split handle does.  The result -- every
+ * array pars3_split_export shows, and the layout (pars3_layout_digest) --
+ * is identical to pars3_split with the same inputs and parameters.  Runs on
+ * `stream` and returns after the handle is complete.  Allocates temporary
+ * device memory (about 100 bytes per stored entry).  Errors as for
+ * pars3_split, plus ECUDA. */
 int pars3_split_device(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
                        const int32_t *perm, const pars3_split_params *p, pars3_handle **out, void *stream);
 
