@@ -198,8 +198,8 @@ int pars3_reorder(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t 
  * components are placed in the order of their (degree, index)-smallest
  * vertex, searched level by level with every vertex appended by the first
  * vertex of the previous level adjacent to it, in (degree, index) order.
- * Flags: PARS3_RCM_GUARD and PARS3_RCM_PERIPHERAL (PARS3_RCM_LOCAL returns
- * EUNSUPPORTED).  bw_before/bw_after (host, may be NULL) as for
+ * Flags: PARS3_RCM_GUARD, PARS3_RCM_PERIPHERAL and PARS3_RCM_LOCAL, as for
+ * pars3_reorder.  bw_before/bw_after (host, may be NULL) as for
  * pars3_reorder.  Runs on `stream` and returns after the result is
  * complete (it synchronizes the stream a few times to size its work).
  * Allocates device scratch of about 52 bytes per stored entry plus 130 per

@@ -461,6 +461,70 @@ __global__ void union_cols_kernel(int nnz, int count, const int32_t *const *__re
     }
 }
 
+// ------------------------------------------------------------ local edges
+
+constexpr int64_t kLocalDeg = 4096;   // edges between vertices whose degree product exceeds this stay untested
+
+// 1 when v is in the sorted list adj[lo .. hi)
+__device__ __forceinline__ bool in_sorted(const int32_t *__restrict__ adj, int lo, int hi, int v) {
+    const int end = hi;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (adj[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < end && adj[lo] == v;
+}
+
+// flag[k] = 1 when stored entry k = (u, v) is a local edge: deg u * deg v
+// above kLocalDeg, or a neighbour a != v of u adjacent to v (a triangle), or
+// a neighbour a != v of u adjacent to a neighbour b of v other than u and a
+// (a 4-cycle).  sadj holds the adjacency lists sorted by index.
+__global__ void local_edge_kernel(int nnz, const int32_t *__restrict__ rowof, const int32_t *__restrict__ ci,
+                                  const int32_t *__restrict__ arp, const int32_t *__restrict__ sadj,
+                                  int32_t *__restrict__ flag) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
+        const int u = rowof[k], v = ci[k];
+        const int u0 = arp[u], u1 = arp[u + 1], v0 = arp[v], v1 = arp[v + 1];
+        bool local = static_cast<int64_t>(u1 - u0) * (v1 - v0) > kLocalDeg;
+        for (int x = u0; !local && x < u1; ++x) {
+            const int a = sadj[x];
+            if (a == v) continue;
+            if (in_sorted(sadj, v0, v1, a)) {
+                local = true;
+                break;
+            }
+            const int a0 = arp[a], a1 = arp[a + 1];
+            for (int y = v0; y < v1; ++y) {
+                const int b = sadj[y];
+                if (b == u || b == a) continue;
+                if (in_sorted(sadj, a0, a1, b)) {
+                    local = true;
+                    break;
+                }
+            }
+        }
+        flag[k] = local ? 1 : 0;
+    }
+}
+
+// the filtered pattern: rp2[i] = fscan[rp[i]], the kept entries in order
+__global__ void filter_kernel(int n, int nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const int32_t *__restrict__ flag, const int32_t *__restrict__ fscan,
+                              int32_t *__restrict__ rp2, int32_t *__restrict__ ci2) {
+    const int span = max(n + 1, nnz);
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < span; x += gridDim.x * blockDim.x) {
+        if (x <= n) rp2[x] = fscan[rp[x]];
+        if (x < nnz && flag[x]) ci2[fscan[x]] = ci[x];
+    }
+}
+
+// dst[i] = src[idx[i]]
+__global__ void row_gather_kernel(int count, const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
+                                  int32_t *__restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];
+}
+
 // ------------------------------------------------------------ host side
 
 
@@ -476,7 +540,11 @@ struct Problem {
     std::vector<int32_t *> perms_h;
 };
 
-int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaStream_t st) {
+// The RCM of P's pattern into P.perms, with its bandwidths and guard per
+// matrix; pos_out (device, n, may be null) receives every vertex's position
+// in the unreversed order (before the guard).
+int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaStream_t st,
+             int32_t *pos_out = nullptr) {
     const int n = P.n, nnz = P.nnz, m2 = 2 * P.nnz;
     const int G = kThreads;
     Scratch S;
@@ -617,6 +685,7 @@ int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaSt
     cudaMemsetAsync(bw, 0, sizeof(unsigned long long) * 2 * P.count, st);
     perm_kernel<<<grid_for(n, G), G, 0, st>>>(n, P.B, cm, pos, P.perms, ctl);
     bandwidth_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, P.B.mid, rowof, P.ci, pos, bw);
+    if (pos_out) cudaMemcpyAsync(pos_out, pos, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
     std::vector<unsigned long long> bw_h(2 * static_cast<size_t>(P.count));
     cudaMemcpyAsync(bw_h.data(), bw, sizeof(unsigned long long) * bw_h.size(), cudaMemcpyDeviceToHost, st);
     if ((rc = fetch(&hc, ctl, sizeof(Ctl), st)) != PARS3_OK) return rc;
@@ -639,8 +708,84 @@ int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaSt
 
 int check_flags(int32_t flags) {
     if (flags & ~(PARS3_RCM_GUARD | PARS3_RCM_PERIPHERAL | PARS3_RCM_LOCAL)) return PARS3_EINVAL;
-    if (flags & PARS3_RCM_LOCAL) return PARS3_EUNSUPPORTED;
     return PARS3_OK;
+}
+
+// The local-edge RCM (PARS3_RCM_LOCAL): the RCM, with the caller's start
+// rule, of the pattern restricted to its local edges -- those on a triangle
+// or a 4-cycle, or between two vertices whose degree product exceeds
+// kLocalDeg (kept untested) -- so that random long-range edges do not steer
+// the order; they stay in the matrix, and the bandwidths and the guard
+// count every stored entry.
+int rcm_local(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaStream_t st) {
+    const int n = P.n, nnz = P.nnz, m2 = 2 * P.nnz;
+    const int G = kThreads;
+    Scratch S;
+    int *err = S.get<int>(1);
+    int32_t *rowof = S.get<int32_t>(nnz), *deg = S.get<int32_t>(n + 1), *arp = S.get<int32_t>(n + 1);
+    int32_t *cur = S.get<int32_t>(n), *aun = S.get<int32_t>(m2), *iota = S.get<int32_t>(n);
+    uint32_t *ka = S.get<uint32_t>(m2), *kb = S.get<uint32_t>(m2);
+    int32_t *va = S.get<int32_t>(m2), *vb = S.get<int32_t>(m2);
+    const int ntiles = (m2 + kSortTile - 1) / kSortTile;
+    int32_t *hist = S.get<int32_t>(256 * static_cast<size_t>(ntiles) + 1);
+    int32_t *hoff = S.get<int32_t>(256 * static_cast<size_t>(ntiles) + 1);
+    int32_t *flag = S.get<int32_t>(nnz), *fscan = S.get<int32_t>(static_cast<size_t>(nnz) + 1);
+    int32_t *rp2 = S.get<int32_t>(n + 1), *ci2 = S.get<int32_t>(nnz), *pos = S.get<int32_t>(n);
+    int32_t *eoff2 = S.get<int32_t>(static_cast<size_t>(P.count) + 1);
+    unsigned long long *bw = S.get<unsigned long long>(2 * static_cast<size_t>(P.count));
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    validate_kernel<<<grid_for(n, G), G, 0, st>>>(n, P.B, P.rp, P.ci, rowof, deg, err);
+    int herr = 0;
+    int rc = fetch(&herr, err, sizeof(int), st);
+    if (rc != PARS3_OK) return rc;
+    if (herr) return PARS3_ENOTSKEW;
+    degree_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, P.ci, deg);
+    // adjacency lists sorted by index: the directed edges listed source by
+    // source in index order, then sorted stably by target
+    scan_kernel<<<1, kScanThreads, 0, st>>>(deg, arp, nullptr, n);
+    cudaMemsetAsync(cur, 0, sizeof(int32_t) * n, st);
+    scatter_adj_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, P.ci, arp, cur, aun);
+    iota_kernel<<<grid_for(n, G), G, 0, st>>>(n, iota);
+    edges_by_rank_kernel<<<grid_for(static_cast<int64_t>(n) * 32, G), G, 0, st>>>(n, iota, arp, aun, arp, ka, va);
+    uint32_t *ko;
+    int32_t *sadj;
+    radix_sort(ka, va, kb, vb, m2, bits_for(n), hist, hoff, st, &ko, &sadj);
+    // the local entries, kept in their order: the filtered pattern
+    local_edge_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, P.ci, arp, sadj, flag);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(flag, fscan, nullptr, nnz);
+    filter_kernel<<<grid_for(std::max(n + 1, nnz), G), G, 0, st>>>(n, nnz, P.rp, P.ci, flag, fscan, rp2, ci2);
+    row_gather_kernel<<<grid_for(P.count + 1, G), G, 0, st>>>(P.count + 1, P.B.moff, rp2, eoff2);
+    int32_t nnz2 = 0;
+    if ((rc = fetch(&nnz2, fscan + nnz, sizeof(int32_t), st)) != PARS3_OK) return rc;
+    Problem P2{n, nnz2, P.count, rp2, ci2, Blocks{P.B.mid, P.B.moff, eoff2}, P.perms, P.moff_h, P.perms_h};
+    if ((rc = rcm_core(P2, flags & PARS3_RCM_PERIPHERAL, nullptr, nullptr, st, pos)) != PARS3_OK) return rc;
+    // bandwidths over every stored entry, and the guard
+    cudaMemsetAsync(bw, 0, sizeof(unsigned long long) * 2 * P.count, st);
+    bandwidth_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, P.B.mid, rowof, P.ci, pos, bw);
+    std::vector<unsigned long long> bw_h(2 * static_cast<size_t>(P.count));
+    if ((rc = fetch(bw_h.data(), bw, sizeof(unsigned long long) * bw_h.size(), st)) != PARS3_OK) return rc;
+    bool reset = false;
+    for (int m = 0; m < P.count; ++m) {
+        int64_t b0 = static_cast<int64_t>(bw_h[2 * m]), b1 = static_cast<int64_t>(bw_h[2 * m + 1]);
+        const int nm = P.moff_h[m + 1] - P.moff_h[m];
+        if ((flags & PARS3_RCM_GUARD) && b1 > b0) {
+            if (nm > 0) iota_kernel<<<grid_for(nm, G), G, 0, st>>>(nm, P.perms_h[m]);
+            b1 = b0;
+            reset = true;
+        }
+        if (bw0) bw0[m] = b0;
+        if (bw1) bw1[m] = b1;
+    }
+    if (reset) {
+        const cudaError_t ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) return cuda_status(ce);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+int rcm_entry(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaStream_t st) {
+    return (flags & PARS3_RCM_LOCAL) ? rcm_local(P, flags, bw0, bw1, st) : rcm_core(P, flags, bw0, bw1, st);
 }
 
 int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flags, int32_t *perm,
@@ -667,7 +812,7 @@ int reorder_device(int32_t n, const int32_t *rp, const int32_t *ci, int32_t flag
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);   // the host sources above are stack memory
     if (ce != cudaSuccess) return cuda_status(ce);
     Problem P{n, nnz, 1, rp, ci, Blocks{nullptr, off, off + 2}, perms, {0, n}, {perm}};
-    return rcm_core(P, flags, bw_before, bw_after, st);
+    return rcm_entry(P, flags, bw_before, bw_after, st);
 }
 
 int reorder_device_batched(int32_t count, const int32_t *ns, const int32_t *const *rps,
@@ -718,7 +863,7 @@ int reorder_device_batched(int32_t count, const int32_t *ns, const int32_t *cons
     union_cols_kernel<<<grid_for(nnz, kThreads), kThreads, 0, st>>>(nnz, count, cis_d, moff_d, eoff_d, ci);
     Problem P{n, nnz, count, rp, ci, Blocks{mid, moff_d, eoff_d}, perms_d, moff,
               std::vector<int32_t *>(perms, perms + count)};
-    rc = rcm_core(P, flags, bw_before, bw_after, st);
+    rc = rcm_entry(P, flags, bw_before, bw_after, st);
     // the host vectors copied from above must outlive the copies
     const cudaError_t se = cudaStreamSynchronize(st);
     return rc != PARS3_OK ? rc : cuda_status(se);

@@ -14,6 +14,7 @@ from paper_2407_17651_gb300 import pars3 as P
 pytestmark = pytest.mark.gpu
 
 FLAGS = [0, P.RCM_GUARD, P.RCM_GUARD | P.RCM_PERIPHERAL, P.RCM_PERIPHERAL]
+LOCAL_FLAGS = [P.RCM_LOCAL, P.RCM_GUARD | P.RCM_LOCAL, P.RCM_GUARD | P.RCM_PERIPHERAL | P.RCM_LOCAL]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -33,11 +34,16 @@ def _dev(A):
 def _check(A, flags):
     rp, ci = _dev(A)
     perm, b0, b1 = P.pars3_reorder_device(A.n, rp, ci, flags)
-    po, ob0, ob1 = O.rcm(A, guard=bool(flags & P.RCM_GUARD), peripheral=bool(flags & P.RCM_PERIPHERAL))
+    po, ob0, ob1 = _oracle(A, flags)
     got = perm.cpu().numpy()
     assert np.array_equal(got, po), (A.name, flags)
     assert (b0, b1) == (ob0, ob1), (A.name, flags)
     return got
+
+
+def _oracle(A, flags):
+    return O.rcm(A, guard=bool(flags & P.RCM_GUARD), peripheral=bool(flags & P.RCM_PERIPHERAL),
+                 local=bool(flags & P.RCM_LOCAL))
 
 
 def _from_pairs(n, pairs, name=""):
@@ -134,9 +140,6 @@ def test_empty_and_errors():
     rp = torch.tensor([0, 0, 1], dtype=torch.int32, device="cuda")
     ci = torch.tensor([0], dtype=torch.int32, device="cuda")
     with pytest.raises(P.Pars3Error) as ei:
-        P.pars3_reorder_device(2, rp, ci, P.RCM_LOCAL)
-    assert ei.value.code == P.EUNSUPPORTED
-    with pytest.raises(P.Pars3Error) as ei:
         P.pars3_reorder_device(2, rp, ci, 64)
     assert ei.value.code == P.EINVAL
     # the library still works after the rejected calls
@@ -176,14 +179,14 @@ def _batch_cases():
     return cases
 
 
-@pytest.mark.parametrize("flags", FLAGS)
+@pytest.mark.parametrize("flags", FLAGS + LOCAL_FLAGS)
 def test_batched_matches_oracle_per_matrix(flags):
     cases = _batch_cases()
     pats = [(A.n,) + _dev(A) for A in cases]
     out = P.pars3_reorder_device_batched(pats, flags)
     assert len(out) == len(cases)
     for A, (perm, b0, b1) in zip(cases, out):
-        po, ob0, ob1 = O.rcm(A, guard=bool(flags & P.RCM_GUARD), peripheral=bool(flags & P.RCM_PERIPHERAL))
+        po, ob0, ob1 = _oracle(A, flags)
         assert np.array_equal(perm.cpu().numpy(), po), (A.name, flags)
         assert (b0, b1) == (ob0, ob1), (A.name, flags)
 
@@ -217,3 +220,23 @@ def test_batched_all_64_matrices_in_one_call():
         for A, (perm, b0, b1) in zip(mats, out):
             po, ob0, ob1 = O.rcm(A, guard=True, peripheral=bool(flags & P.RCM_PERIPHERAL))
             assert np.array_equal(perm.cpu().numpy(), po) and (b0, b1) == (ob0, ob1), A.name
+
+
+@pytest.mark.parametrize("flags", LOCAL_FLAGS)
+def test_local_edge_rcm(flags):
+    """PARS3_RCM_LOCAL on the GPU: the RCM of the edges on a triangle or a
+    4-cycle (degree products above 4096 kept untested), bandwidths and guard
+    over every edge, against orc_rcm with the local flag."""
+    rng = np.random.default_rng(21)
+    cases = [_random_graph(int(n), int(3 * n), s) for s, n in enumerate(rng.integers(5, 300, 12))]
+    cases += [W.grid_plus_random((40, 30), 0.02, "normal", 22), W.grid_plus_random((12, 10, 9), 0.01, "normal", 23),
+              W.grid((33, 17), "normal", 24), W.rmat(11, 12000, seed=25),
+              _from_pairs(100, [(0, i) for i in range(1, 100)] + [(i, i + 1) for i in range(1, 99)], "wheel"),
+              _from_pairs(7, [], "no edges")]
+    for A in cases:
+        _check(A, flags)
+
+
+@pytest.mark.slow
+def test_local_edge_rcm_full_size():
+    _check(W.config1()[0], P.RCM_GUARD | P.RCM_LOCAL)
