@@ -89,6 +89,52 @@ __device__ void block_scan_array(const int32_t *in, int32_t *out, int len, int *
     if (threadIdx.x == 0) out[len] = carry;
 }
 
+// One chunk of kScanThreads * kScanItems values: out[base ..] = carry +
+// exclusive prefix sums of in[base ..], up to len; returns the chunk's sum.
+__device__ int block_scan_chunk(const int32_t *in, int32_t *out, int base, int len, int carry, int *ws) {
+    const int i0 = base + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        v[t] = i0 + t < len ? in[i0 + t] : 0;
+        s += v[t];
+    }
+    int total;
+    int run = carry + block_excl_scan<int>(s, ws, &total);
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        if (i0 + t < len) out[i0 + t] = run;
+        run += v[t];
+    }
+    return total;
+}
+
+constexpr int kScanChunk = kScanThreads * kScanItems;   // values per block of the multi-block scan
+
+// multi-block scan, pass 1: bsum[b] = sum of chunk b
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int32_t *__restrict__ in, int len,
+                                                                   int32_t *__restrict__ bsum) {
+    __shared__ int ws[32];
+    const int i0 = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) s += i0 + t < len ? in[i0 + t] : 0;
+    int total;
+    block_excl_scan<int>(s, ws, &total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// multi-block scan, pass 3: every chunk from its offset boff[b]; the last
+// block writes the total to out[len]
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int32_t *__restrict__ in,
+                                                                  int32_t *__restrict__ out, int len,
+                                                                  const int32_t *__restrict__ boff) {
+    __shared__ int ws[32];
+    block_scan_chunk(in, out, blockIdx.x * kScanChunk, len, boff[blockIdx.x], ws);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[len] = boff[gridDim.x];
+}
+
 // Single-block exclusive scan; the length is *len_dev when len_dev is not
 // null (a size the host does not know), else len.
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(const int32_t *__restrict__ in,
@@ -257,15 +303,35 @@ int bits_for(int64_t n) {   // bits needed for the values 0 .. n-1
     return b;
 }
 
+// Scratch words scan_exclusive needs for arrays of up to len values.
+inline size_t scan_ws_size(int64_t len) { return 2 * static_cast<size_t>(len / kScanChunk + 2); }
+
+// out[0 .. len) = exclusive prefix sums of in, out[len] = the total (len
+// known to the host).  Long arrays take three passes over many blocks
+// (chunk sums, their prefix sums, chunk scans from those offsets); ws holds
+// scan_ws_size(len) words.
+inline void scan_exclusive(const int32_t *in, int32_t *out, int len, int32_t *ws, cudaStream_t st) {
+    if (len <= 4 * kScanChunk) {
+        scan_kernel<<<1, kScanThreads, 0, st>>>(in, out, nullptr, len);
+        return;
+    }
+    const int nb = (len + kScanChunk - 1) / kScanChunk;
+    int32_t *bsum = ws, *boff = ws + nb + 1;
+    scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, len, bsum);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(bsum, boff, nullptr, nb);
+    scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(in, out, len, boff);
+}
+
 // Stable sort of (key, val) pairs by the low `bits` bits of key.  The pairs
 // start in (k0, v0); on return *ko/*vo point at whichever buffer holds the
 // sorted pairs.
+// hist and hoff hold 256 * tiles + 1 words, ws scan_ws_size of that.
 void radix_sort(uint32_t *k0, int32_t *v0, uint32_t *k1, int32_t *v1, int count, int bits, int32_t *hist,
-                int32_t *hoff, cudaStream_t st, uint32_t **ko, int32_t **vo) {
+                int32_t *hoff, int32_t *ws, cudaStream_t st, uint32_t **ko, int32_t **vo) {
     const int ntiles = (count + kSortTile - 1) / kSortTile;
     for (int shift = 0; shift < bits && count > 0; shift += 8) {
         sort_hist_kernel<<<ntiles, kThreads, 0, st>>>(k0, count, shift, ntiles, hist);
-        scan_kernel<<<1, kScanThreads, 0, st>>>(hist, hoff, nullptr, 256 * ntiles);
+        scan_exclusive(hist, hoff, 256 * ntiles, ws, st);
         sort_scatter_kernel<<<ntiles, kThreads, 0, st>>>(k0, v0, count, shift, ntiles, hoff, k1, v1);
         std::swap(k0, k1);
         std::swap(v0, v1);

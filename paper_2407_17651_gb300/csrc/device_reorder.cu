@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kHookRounds = 1 << 22;                // bound on the union-find retries of one edge
 constexpr int kLevelsPerCheck = 8;                  // level steps between two host checks
+constexpr int kSmallComp = 1 << 19;                 // components up to this size are searched by one block each
 
 // error bits of Ctl::err (bit kErrPattern is the pattern check's)
 constexpr int kErrHook = 2;       // union-find retries ran out
@@ -162,6 +163,13 @@ __global__ void scatter_adj_kernel(int nnz, const int32_t *__restrict__ rowof, c
     }
 }
 
+// out[pre[c]] = c for every c with flag[c] set
+__global__ void compact_list_kernel(int count, const int32_t *__restrict__ flag, const int32_t *__restrict__ pre,
+                                    int32_t *__restrict__ out) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x)
+        if (flag[c]) out[pre[c]] = c;
+}
+
 // ------------------------------------------------------------ level steps
 //
 // The current level is a list of frontier entries act[0 .. nact) (nact =
@@ -179,22 +187,156 @@ __device__ __forceinline__ int entry_of(const int32_t *__restrict__ fpre, int na
     return lo;
 }
 
-// start positions: component c begins its queue segment at cbase[c] with root[c]
+// start positions: component c begins its queue segment at cbase[c] with
+// root[c]; the large components (bigpos: their exclusive prefix count) form
+// the first frontier of the grid-wide level steps
 __global__ void bfs_init_kernel(int ncomp, const int32_t *__restrict__ root, const int32_t *__restrict__ cbase,
+                                const int32_t *__restrict__ csz, const int32_t *__restrict__ bigpos,
                                 int32_t *__restrict__ cm, int32_t *__restrict__ pos, Front *__restrict__ act,
                                 int32_t *__restrict__ fpre, Ctl *ctl) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp; c += gridDim.x * blockDim.x) {
         const int v = root[c], q = cbase[c];
         cm[q] = v;
         pos[v] = q;
-        act[c] = Front{q, q + 1, c, 0};
-        fpre[c] = c;
+        if (csz[c] > kSmallComp) {
+            const int k = bigpos[c];
+            act[k] = Front{q, q + 1, c, 0};
+            fpre[k] = k;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        fpre[ncomp] = ncomp;
-        ctl->nact[0] = ncomp;
+        const int nbig = bigpos[ncomp];
+        fpre[nbig] = nbig;
+        ctl->nact[0] = nbig;
         ctl->nact[1] = 0;
         ctl->level = 0;
+    }
+}
+
+// size classes of the components: large ones take the grid-wide level
+// steps, the others (more than one vertex) a block each
+__global__ void comp_class_kernel(int ncomp, const int32_t *__restrict__ csz, int32_t *__restrict__ big,
+                                  int32_t *__restrict__ small) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp; c += gridDim.x * blockDim.x) {
+        big[c] = csz[c] > kSmallComp;
+        small[c] = csz[c] > 1 && csz[c] <= kSmallComp;
+    }
+}
+
+// single-vertex components: eccentricity 0, the last level is the vertex
+__global__ void single_comp_kernel(int ncomp, const int32_t *__restrict__ csz, const int32_t *__restrict__ cbase,
+                                   int32_t *__restrict__ ecc, int2 *__restrict__ last) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp; c += gridDim.x * blockDim.x)
+        if (csz[c] == 1) {
+            ecc[c] = 0;
+            last[c] = make_int2(cbase[c], cbase[c] + 1);
+        }
+}
+
+// One block searches one component of at most kSmallComp vertices through
+// all its levels, with block barriers between the steps of a level (claim,
+// count, prefix sum, write: the same steps as the grid-wide kernels), so a
+// deep, narrow search costs no launch per level.  A frontier vertex of
+// degree up to 32 is handled by one thread (its few neighbours in a loop),
+// a larger one by a warp (lanes over its adjacency, ballots keeping the
+// children in adjacency order).  Components go to blocks in turn; with ecc /
+// last set, each one's eccentricity and last level are recorded.
+__global__ void __launch_bounds__(kScanThreads) component_search_kernel(
+    int nsmall, const int32_t *__restrict__ list, const int32_t *__restrict__ cbase, const int32_t *__restrict__ csz,
+    const int32_t *__restrict__ arp, const int32_t *__restrict__ adj, int32_t *cm, int32_t *pos, int32_t *claim,
+    int32_t *cnt, int32_t *coff, int32_t *__restrict__ ecc, int2 *__restrict__ last) {
+    __shared__ int ws[32];
+    const int tid = threadIdx.x, P = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = P >> 5;
+    const unsigned lt = static_cast<unsigned>(lanemask_lt());
+    for (int i = blockIdx.x; i < nsmall; i += gridDim.x) {
+        const int c = list[i];
+        const int end = cbase[c] + csz[c];
+        int fb = cbase[c], fe = fb + 1, level = 0;
+        for (;;) {
+            // claim: every unvisited neighbour takes the smallest frontier position
+            for (int q = fb + tid; q < fe; q += P) {
+                const int v = cm[q], e1 = arp[v + 1];
+                if (e1 - arp[v] > 32) continue;
+                for (int e = arp[v]; e < e1; ++e) {
+                    const int u = adj[e];
+                    if (pos[u] < 0) atomicMin(&claim[u], q);
+                }
+            }
+            for (int q = fb + warp; q < fe; q += nw) {
+                const int v = cm[q], e1 = arp[v + 1];
+                if (e1 - arp[v] <= 32) continue;
+                for (int e = arp[v] + lane; e < e1; e += 32) {
+                    const int u = adj[e];
+                    if (pos[u] < 0) atomicMin(&claim[u], q);
+                }
+            }
+            __syncthreads();
+            // count: the children of every frontier vertex
+            for (int q = fb + tid; q < fe; q += P) {
+                const int v = cm[q], e1 = arp[v + 1];
+                if (e1 - arp[v] > 32) continue;
+                int k = 0;
+                for (int e = arp[v]; e < e1; ++e) k += claim[adj[e]] == q;
+                cnt[q] = k;
+            }
+            for (int q = fb + warp; q < fe; q += nw) {
+                const int v = cm[q], e1 = arp[v + 1];
+                if (e1 - arp[v] <= 32) continue;
+                int k = 0;
+                for (int e0 = arp[v]; e0 < e1; e0 += 32) {
+                    const int e = e0 + lane;
+                    k += __popc(__ballot_sync(0xffffffffu, e < e1 && claim[adj[e]] == q));
+                }
+                if (lane == 0) cnt[q] = k;
+            }
+            __syncthreads();
+            block_scan_array(cnt + fb, coff + fb, fe - fb, ws);   // coff[fe] receives the level's total
+            __syncthreads();
+            const int total = coff[fe];
+            // write: the children at their slots, in adjacency order
+            for (int q = fb + tid; q < fe; q += P) {
+                const int v = cm[q], e1 = arp[v + 1];
+                if (e1 - arp[v] > 32) continue;
+                int slot = fe + coff[q];
+                for (int e = arp[v]; e < e1; ++e) {
+                    const int u = adj[e];
+                    if (claim[u] == q) {
+                        cm[slot] = u;
+                        pos[u] = slot;
+                        ++slot;
+                    }
+                }
+            }
+            for (int q = fb + warp; q < fe; q += nw) {
+                const int v = cm[q], e1 = arp[v + 1];
+                if (e1 - arp[v] <= 32) continue;
+                int slot = fe + coff[q];
+                for (int e0 = arp[v]; e0 < e1; e0 += 32) {
+                    const int e = e0 + lane;
+                    const int u = e < e1 ? adj[e] : -1;
+                    const bool hit = u >= 0 && claim[u] == q;
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (hit) {
+                        const int p = slot + __popc(m & lt);
+                        cm[p] = u;
+                        pos[u] = p;
+                    }
+                    slot += __popc(m);
+                }
+            }
+            __syncthreads();
+            if (total == 0 || fe + total > end) {   // done (the second test guards the segment)
+                if (ecc && tid == 0) {
+                    ecc[c] = level;
+                    last[c] = make_int2(fb, fe);
+                }
+                break;
+            }
+            fb = fe;
+            fe += total;
+            ++level;
+        }
     }
 }
 
@@ -571,6 +713,7 @@ int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaSt
     int32_t *va = S.get<int32_t>(sort_max), *vb = S.get<int32_t>(sort_max);
     int32_t *hist = S.get<int32_t>(256 * static_cast<size_t>(ntiles) + 1);
     int32_t *hoff = S.get<int32_t>(256 * static_cast<size_t>(ntiles) + 1);
+    int32_t *sws = S.get<int32_t>(scan_ws_size(std::max(sort_max, 256 * ntiles + 1)));
     int32_t *by_deg = S.get<int32_t>(n), *rank = S.get<int32_t>(n);
     int32_t *arp = S.get<int32_t>(n + 1), *cur = S.get<int32_t>(n), *aun = S.get<int32_t>(m2);
     int32_t *sdeg = S.get<int32_t>(n), *epos = S.get<int32_t>(n + 1), *adj = S.get<int32_t>(m2);
@@ -579,14 +722,14 @@ int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaSt
     int32_t *vo;
     cudaMemcpyAsync(ka, deg, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
     iota_kernel<<<grid_for(n, G), G, 0, st>>>(n, va);
-    radix_sort(ka, va, kb, vb, n, nbits, hist, hoff, st, &ko, &vo);
+    radix_sort(ka, va, kb, vb, n, nbits, hist, hoff, sws, st, &ko, &vo);
     if (P.B.mid) {
         uint32_t *kx = ko == ka ? kb : ka;
         int32_t *vx = vo == va ? vb : va;
         gather_kernel<<<grid_for(n, G), G, 0, st>>>(n, vo, P.B.mid, reinterpret_cast<int32_t *>(kx));
         uint32_t *k2;
         int32_t *v2;
-        radix_sort(kx, vo, ko, vx, n, bits_for(P.count), hist, hoff, st, &k2, &v2);
+        radix_sort(kx, vo, ko, vx, n, bits_for(P.count), hist, hoff, sws, st, &k2, &v2);
         vo = v2;
     }
     cudaMemcpyAsync(by_deg, vo, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st);
@@ -594,13 +737,13 @@ int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaSt
 
     // adjacency lists sorted by the neighbours' rank: the directed edges are
     // listed source by source in rank order, then sorted stably by target
-    scan_kernel<<<1, kScanThreads, 0, st>>>(deg, arp, nullptr, n);
+    scan_exclusive(deg, arp, n, sws, st);
     cudaMemsetAsync(cur, 0, sizeof(int32_t) * n, st);
     scatter_adj_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, P.ci, arp, cur, aun);
     gather_kernel<<<grid_for(n, G), G, 0, st>>>(n, by_deg, deg, sdeg);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(sdeg, epos, nullptr, n);
+    scan_exclusive(sdeg, epos, n, sws, st);
     edges_by_rank_kernel<<<grid_for(static_cast<int64_t>(n) * 32, G), G, 0, st>>>(n, by_deg, arp, aun, epos, ka, va);
-    radix_sort(ka, va, kb, vb, m2, nbits, hist, hoff, st, &ko, &vo);
+    radix_sort(ka, va, kb, vb, m2, nbits, hist, hoff, sws, st, &ko, &vo);
     cudaMemcpyAsync(adj, vo, sizeof(int32_t) * m2, cudaMemcpyDeviceToDevice, st);
 
     // connected components, their start candidates (in start order) and sizes
@@ -613,7 +756,7 @@ int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaSt
     cudaMemsetAsync(csize, 0, sizeof(int32_t) * n, st);
     comp_kernel<<<grid_for(n, G), G, 0, st>>>(n, parent, rank, comp, cmin, csize);
     start_flag_kernel<<<grid_for(n, G), G, 0, st>>>(n, by_deg, comp, cmin, flag);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(flag, sidx, nullptr, n);
+    scan_exclusive(flag, sidx, n, sws, st);
     int32_t ncomp = 0;
     cudaMemcpyAsync(&ncomp, sidx + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if ((rc = fetch(&hc, ctl, sizeof(Ctl), st)) != PARS3_OK) return rc;
@@ -626,14 +769,33 @@ int rcm_core(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaSt
     int32_t *fpre[2] = {S.get<int32_t>(ncomp + 1), S.get<int32_t>(ncomp + 1)};
     if (S.err() != cudaSuccess) return PARS3_ENOMEM;
     start_list_kernel<<<grid_for(n, G), G, 0, st>>>(n, by_deg, comp, csize, flag, sidx, cstart, csz);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(csz, cbase, nullptr, ncomp);
+    scan_exclusive(csz, cbase, ncomp, sws, st);
+    // components by size: large ones take the grid-wide level steps, the
+    // others one block each
+    int32_t *bigf = S.get<int32_t>(ncomp), *bigpos = S.get<int32_t>(ncomp + 1);
+    int32_t *smallf = S.get<int32_t>(ncomp), *smallpos = S.get<int32_t>(ncomp + 1);
+    int32_t *smalllist = S.get<int32_t>(ncomp);
+    if (S.err() != cudaSuccess) return PARS3_ENOMEM;
+    comp_class_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, csz, bigf, smallf);
+    scan_exclusive(bigf, bigpos, ncomp, sws, st);
+    scan_exclusive(smallf, smallpos, ncomp, sws, st);
+    compact_list_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, smallf, smallpos, smalllist);
+    int32_t nbig = 0, nsmall = 0;
+    cudaMemcpyAsync(&nbig, bigpos + ncomp, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if ((rc = fetch(&nsmall, smallpos + ncomp, sizeof(int32_t), st)) != PARS3_OK) return rc;
 
     // one breadth-first search of every component from root[c]; with ecc and
     // last set, each component's eccentricity and last level are recorded
     auto search = [&](const int32_t *root, int32_t *ecc, int2 *last) -> int {
         cudaMemsetAsync(pos, 0xff, sizeof(int32_t) * n, st);
         fill_kernel<<<grid_for(n, G), G, 0, st>>>(n, INT_MAX, claim);
-        bfs_init_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, root, cbase, cm, pos, act[0], fpre[0], ctl);
+        bfs_init_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, root, cbase, csz, bigpos, cm, pos, act[0], fpre[0],
+                                                          ctl);
+        if (ecc) single_comp_kernel<<<grid_for(ncomp, G), G, 0, st>>>(ncomp, csz, cbase, ecc, last);
+        if (nsmall > 0)
+            component_search_kernel<<<std::min(nsmall, 2 * sm_count()), kScanThreads, 0, st>>>(
+                nsmall, smalllist, cbase, csz, arp, adj, cm, pos, claim, cnt, coff, ecc, last);
+        if (nbig == 0) return cuda_status(cudaGetLastError());
         const int wg = 4 * sm_count();   // warp-per-vertex kernels: grid-stride over the level
         int b = 0;
         for (int64_t steps = 0;; steps += kLevelsPerCheck) {
@@ -729,6 +891,7 @@ int rcm_local(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaS
     const int ntiles = (m2 + kSortTile - 1) / kSortTile;
     int32_t *hist = S.get<int32_t>(256 * static_cast<size_t>(ntiles) + 1);
     int32_t *hoff = S.get<int32_t>(256 * static_cast<size_t>(ntiles) + 1);
+    int32_t *sws = S.get<int32_t>(scan_ws_size(std::max(std::max(n, m2), 256 * ntiles + 1)));
     int32_t *flag = S.get<int32_t>(nnz), *fscan = S.get<int32_t>(static_cast<size_t>(nnz) + 1);
     int32_t *rp2 = S.get<int32_t>(n + 1), *ci2 = S.get<int32_t>(nnz), *pos = S.get<int32_t>(n);
     int32_t *eoff2 = S.get<int32_t>(static_cast<size_t>(P.count) + 1);
@@ -743,17 +906,17 @@ int rcm_local(const Problem &P, int32_t flags, int64_t *bw0, int64_t *bw1, cudaS
     degree_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, P.ci, deg);
     // adjacency lists sorted by index: the directed edges listed source by
     // source in index order, then sorted stably by target
-    scan_kernel<<<1, kScanThreads, 0, st>>>(deg, arp, nullptr, n);
+    scan_exclusive(deg, arp, n, sws, st);
     cudaMemsetAsync(cur, 0, sizeof(int32_t) * n, st);
     scatter_adj_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, P.ci, arp, cur, aun);
     iota_kernel<<<grid_for(n, G), G, 0, st>>>(n, iota);
     edges_by_rank_kernel<<<grid_for(static_cast<int64_t>(n) * 32, G), G, 0, st>>>(n, iota, arp, aun, arp, ka, va);
     uint32_t *ko;
     int32_t *sadj;
-    radix_sort(ka, va, kb, vb, m2, bits_for(n), hist, hoff, st, &ko, &sadj);
+    radix_sort(ka, va, kb, vb, m2, bits_for(n), hist, hoff, sws, st, &ko, &sadj);
     // the local entries, kept in their order: the filtered pattern
     local_edge_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, rowof, P.ci, arp, sadj, flag);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(flag, fscan, nullptr, nnz);
+    scan_exclusive(flag, fscan, nnz, sws, st);
     filter_kernel<<<grid_for(std::max(n + 1, nnz), G), G, 0, st>>>(n, nnz, P.rp, P.ci, flag, fscan, rp2, ci2);
     row_gather_kernel<<<grid_for(P.count + 1, G), G, 0, st>>>(P.count + 1, P.B.moff, rp2, eoff2);
     int32_t nnz2 = 0;

@@ -406,6 +406,7 @@ int layout_try_device(pars3_handle *h, const DevCanon &C, int64_t mcap, cudaStre
     uint16_t *hcol = S.get<uint16_t>(hn), *hcperm = S.get<uint16_t>(hn), *hrowc = S.get<uint16_t>(hn);
     uint16_t *hrp = S.get<uint16_t>(nrp);
     int32_t *hsrc = S.get<int32_t>(hn);
+    int32_t *sws = S.get<int32_t>(scan_ws_size(std::max(nnz, M)));
     if (S.err() != cudaSuccess) return PARS3_ENOMEM;
     if ((rc = upload(tile_on, on, st)) != PARS3_OK || (rc = upload(hoff, L.hoff, st)) != PARS3_OK ||
         (rc = upload(hcnt, L.hcnt, st)) != PARS3_OK)
@@ -415,7 +416,7 @@ int layout_try_device(pars3_handle *h, const DevCanon &C, int64_t mcap, cudaStre
     cudaMemsetAsync(hrowc, 0, sizeof(uint16_t) * hn, st);
     cudaMemsetAsync(hsrc, 0, sizeof(int32_t) * hn, st);
     half_flag_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, T, C.rs, C.cls, tile_on, half, hflag);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(hflag, hscan, nullptr, nnz);
+    scan_exclusive(hflag, hscan, nnz, sws, st);
     half_place_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, T, W, C.rs, C.col, half, hscan, C.rowptr, hoff, hcol,
                                                       hsrc, hpos);
     half_rowptr_kernel<<<grid_for(nrp, G), G, 0, st>>>(n, nt, T, C.rowptr, hscan, hrp);
@@ -427,7 +428,7 @@ int layout_try_device(pars3_handle *h, const DevCanon &C, int64_t mcap, cudaStre
     cudaMemsetAsync(nhalo, 0, sizeof(int32_t) * nt, st);
     segment_kernel<<<grid_for(M, G), G, 0, st>>>(M, T, W, C.tlist, C.tile_ptr, C.rs, C.col, tile_on, hoff, hpos,
                                                  hcperm, hrowc, segflag, nseg, nhalo);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(segflag, segscan, nullptr, M);
+    scan_exclusive(segflag, segscan, M, sws, st);
     std::vector<int32_t> nseg_h, nhalo_h;
     if ((rc = download(nseg_h, nseg, nt, st)) != PARS3_OK || (rc = download(nhalo_h, nhalo, nt, st)) != PARS3_OK ||
         (rc = cuda_status(cudaStreamSynchronize(st))) != PARS3_OK)
@@ -575,6 +576,7 @@ struct DevBase {
     double *val = nullptr;
     uint32_t *ka = nullptr, *kb = nullptr;   // sort buffers
     int32_t *va = nullptr, *vb = nullptr, *hist = nullptr, *hoff = nullptr;
+    int32_t *sws = nullptr;   // prefix-sum workspace
     std::vector<int32_t> perm_h, rowptr_h, col_h;   // host copies for the handles
     std::vector<double> val_h;
 };
@@ -639,6 +641,7 @@ int base_build(DevBase &B, int32_t n, const int32_t *rp, const int32_t *ci, cons
     const int stiles = (nnz + kSortTile - 1) / kSortTile;
     B.hist = S.get<int32_t>(256 * static_cast<size_t>(stiles) + 1);
     B.hoff = S.get<int32_t>(256 * static_cast<size_t>(stiles) + 1);
+    B.sws = S.get<int32_t>(scan_ws_size(std::max(std::max(n, nnz), 256 * stiles + 1)));
     if (T.err() != cudaSuccess || S.err() != cudaSuccess) return PARS3_ENOMEM;
     uint32_t *ka = B.ka, *kb = B.kb, *rkey = B.rs;
     int32_t *va = B.va, *vb = B.vb;
@@ -647,25 +650,25 @@ int base_build(DevBase &B, int32_t n, const int32_t *rp, const int32_t *ci, cons
     cudaMemcpyAsync(ka, ckey, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToDevice, st);
     uint32_t *ko, *k2;
     int32_t *vo, *v2;
-    radix_sort(ka, va, kb, vb, nnz, nbits, B.hist, B.hoff, st, &ko, &vo);
+    radix_sort(ka, va, kb, vb, nnz, nbits, B.hist, B.hoff, B.sws, st, &ko, &vo);
     uint32_t *kx = ko == ka ? kb : ka;
     int32_t *vx = vo == va ? vb : va;
     gather_key_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, vo, rkey, kx);
-    radix_sort(kx, vo, ko, vx, nnz, nbits, B.hist, B.hoff, st, &k2, &v2);
+    radix_sort(kx, vo, ko, vx, nnz, nbits, B.hist, B.hoff, B.sws, st, &k2, &v2);
     // the row of every sorted entry gets its own buffer: the sort buffers are reused below
     cudaMemcpyAsync(B.rs, k2, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToDevice, st);
     const int32_t *order = v2;   // source entry of every sorted position (read by emit_kernel only)
     cudaMemsetAsync(rowcnt, 0, sizeof(int32_t) * n, st);
     cudaMemsetAsync(acc, 0, sizeof(unsigned long long), st);
     emit_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, order, B.rs, ckey, vv, B.col, B.val, rowcnt, acc);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(rowcnt, B.rowptr, nullptr, n);
+    scan_exclusive(rowcnt, B.rowptr, n, B.sws, st);
     // column view for the layout: entries of every column in row order
     cudaMemsetAsync(colcnt, 0, sizeof(int32_t) * n, st);
     col_count_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, B.col, colcnt);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(colcnt, B.cptr, nullptr, n);
+    scan_exclusive(colcnt, B.cptr, n, B.sws, st);
     iota_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, va);
     list_key_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, va, B.col, B.rs, 1, 0, ka);
-    radix_sort(ka, va, kb, vb, nnz, nbits, B.hist, B.hoff, st, &ko, &vo);
+    radix_sort(ka, va, kb, vb, nnz, nbits, B.hist, B.hoff, B.sws, st, &ko, &vo);
     cudaMemcpyAsync(B.cent, vo, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st);
     unsigned long long bw = 0;
     cudaMemcpyAsync(&bw, acc, sizeof(bw), cudaMemcpyDeviceToHost, st);
@@ -708,9 +711,9 @@ int base_cut(DevBase &B, const pars3_split_params &prm, pars3_handle **out, cuda
     cudaMemsetAsync(tcnt, 0, sizeof(int32_t) * ntiles, st);
     cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 3, st);
     classify_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, T, W, B.rs, B.col, cls, mflag, oflag, tcnt, acc);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(mflag, mpre, nullptr, nnz);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(oflag, opre, nullptr, nnz);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(tcnt, tile_ptr, nullptr, ntiles);
+    scan_exclusive(mflag, mpre, nnz, B.sws, st);
+    scan_exclusive(oflag, opre, nnz, B.sws, st);
+    scan_exclusive(tcnt, tile_ptr, ntiles, B.sws, st);
     compact_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, mflag, mpre, mlist);
     compact_kernel<<<grid_for(nnz, G), G, 0, st>>>(nnz, oflag, opre, olist);
     int32_t M = 0, O = 0;
@@ -723,11 +726,11 @@ int base_cut(DevBase &B, const pars3_split_params &prm, pars3_handle **out, cuda
     int32_t *va = B.va, *vb = B.vb, *vo, *v2;
     cudaMemcpyAsync(va, mlist, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st);
     list_key_kernel<<<grid_for(M, G), G, 0, st>>>(M, va, B.col, B.rs, T, 0, ka);
-    radix_sort(ka, va, kb, vb, M, nbits, B.hist, B.hoff, st, &ko, &vo);
+    radix_sort(ka, va, kb, vb, M, nbits, B.hist, B.hoff, B.sws, st, &ko, &vo);
     uint32_t *kx = ko == ka ? kb : ka;
     int32_t *vx = vo == va ? vb : va;
     list_key_kernel<<<grid_for(M, G), G, 0, st>>>(M, vo, B.col, B.rs, T, 1, kx);
-    radix_sort(kx, vo, ko, vx, M, bits_for(ntiles), B.hist, B.hoff, st, &k2, &v2);
+    radix_sort(kx, vo, ko, vx, M, bits_for(ntiles), B.hist, B.hoff, B.sws, st, &k2, &v2);
     // the tile lists get their own buffer: the sort buffers are reused below
     int32_t *tile_list = S.get<int32_t>(M), *outer_csc = S.get<int32_t>(O);
     if (S.err() != cudaSuccess) return PARS3_ENOMEM;
@@ -735,7 +738,7 @@ int base_cut(DevBase &B, const pars3_split_params &prm, pars3_handle **out, cuda
     // outer lists: in position order (CSR), and stably by column (CSC)
     cudaMemcpyAsync(va, olist, sizeof(int32_t) * O, cudaMemcpyDeviceToDevice, st);
     list_key_kernel<<<grid_for(O, G), G, 0, st>>>(O, va, B.col, B.rs, T, 0, ka);
-    radix_sort(ka, va, kb, vb, O, nbits, B.hist, B.hoff, st, &ko, &vo);
+    radix_sort(ka, va, kb, vb, O, nbits, B.hist, B.hoff, B.sws, st, &ko, &vo);
     cudaMemcpyAsync(outer_csc, vo, sizeof(int32_t) * O, cudaMemcpyDeviceToDevice, st);
     pars3_handle *h = nullptr;
     try {
