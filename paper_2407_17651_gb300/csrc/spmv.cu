@@ -69,8 +69,22 @@ static int launch_typed(const pars3_handle *h, int dtype, double alpha, const vo
     const int nf = static_cast<int>(L.fold_row.size());
     if (nf > 0) {
         const int blocks = static_cast<int>(std::min<int64_t>((nf + 255) / 256, 8LL * sm_count()));
-        fold_kernel<XT, AT><<<blocks, 256, 0, st>>>(nf, fold_lists(D, L), static_cast<const AT *>(halo),
-                                                    static_cast<const AT *>(lpart), static_cast<XT *>(y));
+        // a programmatic dependent launch: the fold's blocks are scheduled
+        // during the tile kernel's tail and wait for its results on the device
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, fold_kernel<XT, AT>, nf, fold_lists(D, L),
+                                                 static_cast<const AT *>(halo), static_cast<const AT *>(lpart),
+                                                 static_cast<XT *>(y));
+        if (e != cudaSuccess) return cuda_status(e);
     }
     return cuda_status(cudaGetLastError());
 }

@@ -829,6 +829,9 @@ constexpr int tile_min_blocks() { return sizeof(AT) == 8 ? 2 : 3; }
 template <typename VT, typename XT, typename AT, bool LA = false>
 __global__ void __launch_bounds__(kBlock, LA ? 2 : tile_min_blocks<AT>()) tile_kernel(const SpmvArgs<VT, XT, AT> a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    // the fold may be scheduled once every block of this grid has started
+    // (it waits for this grid's results before reading them)
+    asm volatile("griddepcontrol.launch_dependents;");
     if (static_cast<int>(blockIdx.x) < a.nlb) {
         long_pieces_block<VT, XT, AT>(a, blockIdx.x, a.x);
     } else {
@@ -928,6 +931,9 @@ struct FoldLists {
 template <typename XT, typename AT>
 __global__ void __launch_bounds__(256) fold_kernel(int nitems, const FoldLists F, const AT *__restrict__ halo,
                                                    const AT *__restrict__ lpart, XT *__restrict__ y) {
+    // launched as a programmatic dependent of the tile kernel: wait for its
+    // completion (and its writes) before reading y, halo and lpart
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int w = gw; w < F.nheavy; w += nw) {   // heavy rows, a warp each
