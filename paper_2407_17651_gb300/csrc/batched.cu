@@ -178,9 +178,14 @@ static int enqueue(BatchCache &C, int count, int64_t total_units, int64_t total_
         if (e != cudaSuccess) return cuda_status(e);
         configured.fetch_or(dbit);
     }
-    const int grid = static_cast<int>(std::min<int64_t>(total_units, 2LL * sm_count()));
+    // k = 1: a unit is short and latency-bound, so half-size blocks, four per
+    // SM, keep twice as many units in flight (the registers the kernel is
+    // compiled for, 64 a thread, still fit); k > 1: 512 threads, two per SM
+    const int block = k == 1 ? kBlock / 2 : kBlock;
+    const int per_sm = k == 1 ? 4 : 2;
+    const int grid = static_cast<int>(std::min<int64_t>(total_units, static_cast<int64_t>(per_sm) * sm_count()));
     if (grid > 0)
-        batched_kernel<VT, XT, AT, LPR, NV><<<grid, kBlock, smem, st>>>(
+        batched_kernel<VT, XT, AT, LPR, NV><<<grid, block, smem, st>>>(
             static_cast<const SpmvArgs<VT, XT, AT> *>(C.args), static_cast<const int32_t *>(C.upre), count,
             static_cast<int>(total_units), k);
     if (total_fold > 0) {
