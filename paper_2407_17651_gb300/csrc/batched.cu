@@ -178,11 +178,14 @@ static int enqueue(BatchCache &C, int count, int64_t total_units, int64_t total_
         if (e != cudaSuccess) return cuda_status(e);
         configured.fetch_or(dbit);
     }
-    // k = 1: a unit is short and latency-bound, so half-size blocks, four per
-    // SM, keep twice as many units in flight (the registers the kernel is
-    // compiled for, 64 a thread, still fit); k > 1: 512 threads, two per SM
-    const int block = k == 1 ? kBlock / 2 : kBlock;
-    const int per_sm = k == 1 ? 4 : 2;
+    // Half-size blocks, four per SM: a unit (one tile or one block of
+    // long-row slices) is short and mostly waits on memory, so twice as many
+    // units in flight pay at every k (the kernel's 64 registers a thread
+    // still fit four blocks of 256 threads).  On the 64-matrix set against
+    // 512-thread blocks, two per SM: fp32 k = 1 / 4 / 32 362 / 344 / 965 ->
+    // 238 / 259 / 873 us.
+    const int block = kBlock / 2;
+    const int per_sm = 4;
     const int grid = static_cast<int>(std::min<int64_t>(total_units, static_cast<int64_t>(per_sm) * sm_count()));
     if (grid > 0)
         batched_kernel<VT, XT, AT, LPR, NV><<<grid, block, smem, st>>>(
