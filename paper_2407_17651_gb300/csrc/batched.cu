@@ -178,14 +178,18 @@ static int enqueue(BatchCache &C, int count, int64_t total_units, int64_t total_
         if (e != cudaSuccess) return cuda_status(e);
         configured.fetch_or(dbit);
     }
-    // Half-size blocks, four per SM: a unit (one tile or one block of
-    // long-row slices) is short and mostly waits on memory, so twice as many
-    // units in flight pay at every k (the kernel's 64 registers a thread
-    // still fit four blocks of 256 threads).  On the 64-matrix set against
-    // 512-thread blocks, two per SM: fp32 k = 1 / 4 / 32 362 / 344 / 965 ->
-    // 238 / 259 / 873 us.
-    const int block = kBlock / 2;
-    const int per_sm = 4;
+    // Smaller blocks, more of them per SM: a unit (one tile or one block of
+    // long-row slices) is short and mostly waits on memory, so more units in
+    // flight pay (the kernel's 64 registers a thread fit 1,024 threads an SM
+    // however they are split).  Measured on the 64-matrix set against
+    // 512-thread blocks, two per SM: 256-thread blocks, four per SM, are
+    // faster at every k (fp32 k = 1 / 4 / 32: 362 / 344 / 965 -> 238 / 259 /
+    // 873 us); 128-thread blocks, eight per SM, are faster still for fp32 /
+    // bf16 up to k = 16 (k = 1: 198 us) and fp64 from k = 4, and slower for
+    // fp32 at k = 32 and fp64 at k = 1, where the 256-thread blocks stay.
+    const bool quarter = sizeof(AT) == 4 ? k <= 16 : k >= 4;
+    const int block = quarter ? kBlock / 4 : kBlock / 2;
+    const int per_sm = quarter ? 8 : 4;
     const int grid = static_cast<int>(std::min<int64_t>(total_units, static_cast<int64_t>(per_sm) * sm_count()));
     if (grid > 0)
         batched_kernel<VT, XT, AT, LPR, NV><<<grid, block, smem, st>>>(
